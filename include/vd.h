@@ -1,0 +1,175 @@
+/*
+ * vd.h -- C ABI of the GB300 (sm_103a) variable-density spectral elliptic solver.
+ *
+ * Method: Reynier, Di Pierro, Alizard, Cadiou, Le Penven, Buffat, "A preconditioning for
+ * the spectral solution of incompressible variable-density flows" (arXiv 2403.06654).
+ * The library solves the elliptic systems of each semi-implicit second-order time step on
+ * a fully periodic (Fourier x Fourier x Fourier) grid:
+ *   pressure  L_rho(phi) = div(rho^-1 grad phi) = f             (Eq. VDINSE.Lrho / Lrho.num)
+ *   velocity  V_rho(u)   = u - (dt/2) zeta(rho, u) = b            (Eq. VDINSE.zeta, num.momentum.proj;
+ *                                                                   1D form Eq. VDINSE.Vrho)
+ * by preconditioned CG, GMRES or Richardson Minimal Residual (Sec. 3.1), with the inverse
+ * of the constant-density operator as preconditioner (Eq. VDINSE.V for the velocity; the
+ * inverse Laplacian with the k = 0 mode removed for the pressure, Sec. 3.2 and the text
+ * before Table 2).
+ *
+ * Conventions shared by every call
+ *  - Every call returns a vd_status; VD_OK is 0.  On failure vd_last_error() returns a
+ *    message for the calling thread.  No C++ exception crosses the ABI.
+ *  - Device buffers are owned by the caller: the library reads and writes them and never
+ *    frees them.  Only vd_grid_create allocates device memory of its own (the twiddle
+ *    tables, a few KB), released by vd_grid_destroy.
+ *  - Calls that take a stream are stream-ordered on it: they enqueue kernels and return;
+ *    vd_solve and vd_density_set also synchronise the stream to read convergence flags and
+ *    density bounds.  Pass 0 for the legacy default stream.
+ *  - Fields are row-major with x fastest: a physical scalar field holds n0*n1*n2 doubles
+ *    laid out [n2][n1][n0] (1D: n1 = n2 = 1; 2D: n2 = 1).  A vector field stores its ndim
+ *    components back to back.  Every axis length must be even and factor into 2, 3 and 5,
+ *    with 4 <= n <= 1024.
+ *  - Discretisation: Fourier differentiation D_j = F^-1 diag(i k~_j) F with the Nyquist
+ *    wavenumber set to zero, and the Laplacian sum_j D_j D_j (symbol -|k~|^2).  The pressure
+ *    operator then has a null space of dimension 2^ndim (the modes whose every index is 0
+ *    or n/2); pressure solves return the solution orthogonal to it.
+ */
+#ifndef VD_H_
+#define VD_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vd_grid vd_grid;
+typedef struct CUstream_st* vd_stream; /* same type as cudaStream_t */
+
+typedef enum {
+  VD_OK = 0,
+  VD_ERR_INVALID_ARG = 1,    /* bad size, null pointer, rho <= 0 or non-finite, CG on V_rho */
+  VD_ERR_OOM = 2,            /* workspace smaller than the query says, or allocation failed */
+  VD_ERR_CUDA = 3,           /* a CUDA runtime call failed; message has the CUDA error */
+  VD_ERR_NOT_CONVERGED = 4,  /* max_it reached above tol (x holds the last iterate) */
+  VD_ERR_BREAKDOWN = 5,      /* Krylov breakdown (zero curvature / zero search direction) */
+  VD_ERR_DIVERGED = 6,       /* monitored residual grew above 1e3 x the best value */
+  VD_ERR_NONFINITE = 7,      /* NaN or Inf met in a reduction */
+  VD_ERR_NO_DENSITY = 8      /* an operator was used before vd_density_set */
+} vd_status;
+
+typedef enum { VD_OP_PRESSURE = 0, VD_OP_VELOCITY = 1 } vd_op;
+typedef enum { VD_SOLVER_CG = 0, VD_SOLVER_GMRES = 1, VD_SOLVER_RMR = 2 } vd_solver;
+typedef enum {
+  VD_PREC_FP64 = 0,  /* every transform, product and reduction in IEEE double */
+  VD_PREC_MIXED = 1  /* inner Krylov solve with float transforms and preconditioner, double
+                        dot products, inside a double iterative-refinement loop whose true
+                        residual uses the double operator (spec precision form) */
+} vd_precision;
+
+/* Parameters of the velocity operator: a = dt/(2 Re) (Eq. VDINSE.Vrho), inv_sc = 1/Sc. */
+typedef struct {
+  double a;
+  double inv_sc;
+} vd_op_params;
+
+typedef struct {
+  double tol;        /* stop when the monitored relative residual <= tol */
+  int max_it;        /* limit on operator applications inside the Krylov loop(s) */
+  int restart;       /* GMRES restart length m (1..64), default 30 when <= 0 */
+  int use_x0;        /* 1: x holds the initial guess (warm start, Sec. 3.1); 0: start from 0 */
+  int precision;     /* vd_precision */
+  double inner_tol;  /* VD_PREC_MIXED: relative tolerance of each inner solve (default 1e-5) */
+  int check_every;   /* iterations enqueued between host convergence checks (default 1) */
+} vd_solve_params;
+
+typedef struct {
+  int iters;           /* operator applications in the Krylov loop(s) */
+  int outer_iters;     /* VD_PREC_MIXED: refinement sweeps (0 otherwise) */
+  int status;          /* vd_status of the solve */
+  double relres;       /* last monitored relative residual */
+  double relres_true;  /* ||b - A x|| / ||b|| of the returned x, with the double operator */
+  double* hist;        /* optional host array: monitored relres per iteration (hist[0] = initial) */
+  int hist_cap;        /* capacity of hist */
+  int hist_len;        /* entries written */
+} vd_solve_info;
+
+/* Last error message of the calling thread (static storage, never null). */
+const char* vd_last_error(void);
+
+/* Library version string. */
+const char* vd_version(void);
+
+/*
+ * Create a periodic grid: ndim in {1,2,3}; n[j] points over length L[j] along axis j
+ * (j = 0 is x).  Entries beyond ndim are ignored.  Builds the FFT plans and uploads the
+ * twiddle tables (library-owned device memory) on the current device.
+ * Errors: VD_ERR_INVALID_ARG for an unsupported size, VD_ERR_CUDA/OOM on allocation.
+ */
+vd_status vd_grid_create(int ndim, const int n[3], const double L[3], vd_grid** out);
+vd_status vd_grid_destroy(vd_grid* grid);
+
+/* Number of points (n0 n1 n2) and of half-spectrum coefficients ((n0/2+1) n1 n2). */
+size_t vd_grid_points(const vd_grid* grid);
+size_t vd_grid_modes(const vd_grid* grid);
+
+/*
+ * Density data: bytes of the caller-owned device buffer that vd_density_set fills with
+ * rho, 1/(N rho) (double and float) and, when `op` is VD_OP_VELOCITY, the spectral first
+ * and second derivatives D_j rho and D_i D_j rho (reading: the paper does not say how
+ * they are formed; they are the Fourier derivatives of the grid density).
+ */
+size_t vd_density_bytes(const vd_grid* grid, vd_op op);
+
+/*
+ * Attach the density rho (device, n0 n1 n2 doubles, caller-owned, not retained) to the
+ * grid, precomputing into dens_ws (device, vd_density_bytes(grid, op) bytes, caller-owned,
+ * must stay alive while the grid uses it).  Checks rho > 0 and finite
+ * (VD_ERR_INVALID_ARG otherwise; this synchronises `stream`).  The grid keeps pointers
+ * into dens_ws until the next vd_density_set.
+ */
+vd_status vd_density_set(vd_grid* grid, vd_op op, const double* rho, void* dens_ws, size_t dens_bytes,
+                         vd_stream stream);
+
+/* Workspace bytes needed by vd_apply_op / vd_apply_precond / vd_solve (caller-owned). */
+size_t vd_workspace_bytes(const vd_grid* grid, vd_op op, vd_solver solver, const vd_solve_params* params);
+
+/*
+ * out = A(in) on physical fields, A = L~_rho (pressure, scalar field) or V~_rho (velocity,
+ * ndim-component field, params required).  in and out may not alias.  Forward transform,
+ * spectral apply, inverse transform, all on `stream`.
+ */
+vd_status vd_apply_op(const vd_grid* grid, vd_op op, const vd_op_params* params, const double* in, double* out,
+                      void* ws, size_t ws_bytes, vd_stream stream);
+
+/*
+ * out = M(in): the constant-density inverse, diagonal in Fourier space.
+ * Pressure: multiply by -1/|k~|^2, 0 on the null-space modes (pseudo-inverse of the
+ * Laplacian).  Velocity: multiply every component by 1/(1 + a |k~|^2) (Eq. VDINSE.V).
+ */
+vd_status vd_apply_precond(const vd_grid* grid, vd_op op, const vd_op_params* params, const double* in, double* out,
+                           void* ws, size_t ws_bytes, vd_stream stream);
+
+/*
+ * Solve A x = b (physical fields) with the chosen Krylov method, right-preconditioned by
+ * M (GMRES, RMR) or split-preconditioned (CG).  Pressure right-hand sides are first
+ * projected onto the range of L~ (their null-space modes are removed); x is returned
+ * orthogonal to the null space.  CG with VD_OP_VELOCITY is rejected (VD_ERR_INVALID_ARG:
+ * V_rho is not symmetric, Sec. 3.1).  x is input (initial guess if use_x0) and output.
+ * info (optional, host) receives iteration counts, residuals and history.  Returns the
+ * solve status (VD_OK when converged).
+ */
+vd_status vd_solve(const vd_grid* grid, vd_op op, vd_solver solver, const vd_op_params* op_params,
+                   const vd_solve_params* params, const double* b, double* x, vd_solve_info* info, void* ws,
+                   size_t ws_bytes, vd_stream stream);
+
+/* out = sum_j D_j u_j (spectral divergence of an ndim-component physical field). */
+vd_status vd_divergence(const vd_grid* grid, const double* u, double* out, void* ws, size_t ws_bytes,
+                        vd_stream stream);
+
+/* out_j = D_j phi (spectral gradient; out holds ndim components). */
+vd_status vd_gradient(const vd_grid* grid, const double* phi, double* out, void* ws, size_t ws_bytes,
+                      vd_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VD_H_ */

@@ -1,0 +1,310 @@
+"""GB300 (sm_103a) variable-density spectral elliptic solver: Python binding of libvd.so.
+
+The binding only marshals arguments: every step of an operator apply or a solve runs in
+the CUDA kernels of ``libvd.so`` (declared in ``include/vd.h``).  PyTorch supplies device
+memory (tensors passed as raw pointers) and the current CUDA stream.
+
+Module-level functions carry the C names (``vd_grid_create``, ``vd_density_set``,
+``vd_apply_op``, ``vd_apply_precond``, ``vd_solve``, ...).  ``Grid`` is a convenience
+wrapper that allocates the workspaces with torch and calls them.
+
+If the shared library is missing, every call raises ``VDError``: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libvd.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "vd.h")
+
+VD_OK, VD_ERR_INVALID_ARG, VD_ERR_OOM, VD_ERR_CUDA = 0, 1, 2, 3
+VD_ERR_NOT_CONVERGED, VD_ERR_BREAKDOWN, VD_ERR_DIVERGED, VD_ERR_NONFINITE, VD_ERR_NO_DENSITY = 4, 5, 6, 7, 8
+STATUS_NAMES = {0: "converged", 1: "invalid_arg", 2: "oom", 3: "cuda", 4: "max_iter", 5: "breakdown",
+                6: "diverged", 7: "nonfinite", 8: "no_density"}
+VD_OP_PRESSURE, VD_OP_VELOCITY = 0, 1
+VD_SOLVER_CG, VD_SOLVER_GMRES, VD_SOLVER_RMR = 0, 1, 2
+VD_PREC_FP64, VD_PREC_MIXED = 0, 1
+OPS = {"pressure": VD_OP_PRESSURE, "velocity": VD_OP_VELOCITY}
+SOLVERS = {"cg": VD_SOLVER_CG, "gmres": VD_SOLVER_GMRES, "rmr": VD_SOLVER_RMR}
+PRECISIONS = {"fp64": VD_PREC_FP64, "mixed": VD_PREC_MIXED}
+
+
+class VDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vd_op_params(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("inv_sc", ctypes.c_double)]
+
+
+class vd_solve_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_it", ctypes.c_int), ("restart", ctypes.c_int),
+                ("use_x0", ctypes.c_int), ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("check_every", ctypes.c_int)]
+
+
+class vd_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("status", ctypes.c_int),
+                ("relres", ctypes.c_double), ("relres_true", ctypes.c_double),
+                ("hist", ctypes.POINTER(ctypes.c_double)), ("hist_cap", ctypes.c_int), ("hist_len", ctypes.c_int)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+_I = ctypes.c_int
+
+_SIGS = {
+    "vd_last_error": (ctypes.c_char_p, []),
+    "vd_version": (ctypes.c_char_p, []),
+    "vd_grid_create": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_P)]),
+    "vd_grid_destroy": (_I, [_P]),
+    "vd_grid_points": (_SZ, [_P]),
+    "vd_grid_modes": (_SZ, [_P]),
+    "vd_density_bytes": (_SZ, [_P, _I]),
+    "vd_density_set": (_I, [_P, _I, _P, _P, _SZ, _P]),
+    "vd_workspace_bytes": (_SZ, [_P, _I, _I, ctypes.POINTER(vd_solve_params)]),
+    "vd_apply_op": (_I, [_P, _I, ctypes.POINTER(vd_op_params), _P, _P, _P, _SZ, _P]),
+    "vd_apply_precond": (_I, [_P, _I, ctypes.POINTER(vd_op_params), _P, _P, _P, _SZ, _P]),
+    "vd_solve": (_I, [_P, _I, _I, ctypes.POINTER(vd_op_params), ctypes.POINTER(vd_solve_params), _P, _P,
+                      ctypes.POINTER(vd_solve_info), _P, _SZ, _P]),
+    "vd_divergence": (_I, [_P, _P, _P, _P, _SZ, _P]),
+    "vd_gradient": (_I, [_P, _P, _P, _P, _SZ, _P]),
+}
+
+
+def lib():
+    """Load libvd.so (raises VDError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise VDError(VD_ERR_CUDA, f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_functions(path: str = HEADER) -> list:
+    """Names of the functions declared in include/vd.h."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(vd_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _check(st):
+    if st != VD_OK:
+        raise VDError(st, lib().vd_last_error().decode())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------------------------------
+# thin wrappers with the C names
+# ------------------------------------------------------------------------------------------
+
+def vd_grid_create(n, L):
+    nd = len(n)
+    nn = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - nd)))
+    ll = (ctypes.c_double * 3)(*(list(L) + [1.0] * (3 - nd)))
+    h = ctypes.c_void_p()
+    _check(lib().vd_grid_create(nd, nn, ll, ctypes.byref(h)))
+    return h
+
+
+def vd_grid_destroy(h):
+    _check(lib().vd_grid_destroy(h))
+
+
+def vd_density_bytes(h, op):
+    return int(lib().vd_density_bytes(h, op))
+
+
+def vd_workspace_bytes(h, op, solver, params: vd_solve_params | None):
+    return int(lib().vd_workspace_bytes(h, op, solver, ctypes.byref(params) if params is not None else None))
+
+
+def vd_density_set(h, op, rho, ws, stream=None):
+    _check(lib().vd_density_set(h, op, _ptr(rho), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def vd_apply_op(h, op, params, x, out, ws, stream=None):
+    _check(lib().vd_apply_op(h, op, ctypes.byref(params) if params is not None else None, _ptr(x), _ptr(out),
+                             _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def vd_apply_precond(h, op, params, x, out, ws, stream=None):
+    _check(lib().vd_apply_precond(h, op, ctypes.byref(params) if params is not None else None, _ptr(x), _ptr(out),
+                                  _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def vd_solve(h, op, solver, op_params, params, b, x, info, ws, stream=None):
+    """Returns the raw status (not raised: non-convergence is a result, not an error)."""
+    st = lib().vd_solve(h, op, solver, ctypes.byref(op_params) if op_params is not None else None,
+                        ctypes.byref(params), _ptr(b), _ptr(x), ctypes.byref(info), _ptr(ws), ws.numel(),
+                        _stream(stream))
+    if st in (VD_ERR_INVALID_ARG, VD_ERR_OOM, VD_ERR_CUDA, VD_ERR_NO_DENSITY):
+        _check(st)
+    return st
+
+
+def vd_divergence(h, u, out, ws, stream=None):
+    _check(lib().vd_divergence(h, _ptr(u), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def vd_gradient(h, phi, out, ws, stream=None):
+    _check(lib().vd_gradient(h, _ptr(phi), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+# ------------------------------------------------------------------------------------------
+# convenience object
+# ------------------------------------------------------------------------------------------
+
+class Grid:
+    """A periodic grid with its density; fields are float64 CUDA tensors shaped (n2, n1, n0)
+    (trailing axes dropped for 2D/1D), vector fields (ndim, ...)."""
+
+    def __init__(self, n, L, device="cuda"):
+        import torch
+        self.n = tuple(int(v) for v in n)
+        self.L = tuple(float(v) for v in L)
+        self.ndim = len(self.n)
+        self.shape = tuple(reversed(self.n))
+        self.device = torch.device(device)
+        self.h = vd_grid_create(self.n, self.L)
+        self._dens = None
+        self._ws = {}
+        self._op_set = None
+
+    def close(self):
+        if self.h:
+            vd_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def modes(self):
+        return int(lib().vd_grid_modes(self.h))
+
+    def _field(self, t, ncomp=0, name="field"):
+        """float64 contiguous device copy of t, checked against the grid shape; ncomp = 0 for
+        a scalar field, else the number of components of a vector field (ncomp, *shape)."""
+        import torch
+        t = t.to(device=self.device, dtype=torch.float64).contiguous()
+        want = ((ncomp,) if ncomp > 0 else ()) + self.shape
+        if tuple(t.shape) != want:
+            raise VDError(VD_ERR_INVALID_ARG, f"{name} has shape {tuple(t.shape)}, expected {want}")
+        return t
+
+    def _ncomp(self, op):
+        return self.ndim if OPS[op] == VD_OP_VELOCITY else 0
+
+    def _workspace(self, nbytes):
+        import torch
+        key = "ws"
+        t = self._ws.get(key)
+        if t is None or t.numel() < nbytes:
+            t = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+            self._ws[key] = t
+        return t
+
+    def set_density(self, rho, op="pressure", stream=None):
+        import torch
+        opc = OPS[op]
+        rho = self._field(rho, 0, "rho")
+        nb = vd_density_bytes(self.h, opc)
+        self._dens = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        vd_density_set(self.h, opc, rho, self._dens, stream)
+        self._op_set = op
+
+    def apply(self, op, x, a=0.0, inv_sc=1.0, stream=None):
+        import torch
+        opc = OPS[op]
+        x = self._field(x, self._ncomp(op), "x")
+        out = torch.empty_like(x)
+        p = vd_solve_params(tol=0.0, max_it=1, restart=1, use_x0=0, precision=0, inner_tol=0.0, check_every=1)
+        ws = self._workspace(vd_workspace_bytes(self.h, opc, VD_SOLVER_RMR, p))
+        vd_apply_op(self.h, opc, vd_op_params(a, inv_sc) if opc == VD_OP_VELOCITY else None, x, out, ws, stream)
+        return out
+
+    def precond(self, op, x, a=0.0, stream=None):
+        import torch
+        opc = OPS[op]
+        x = self._field(x, self._ncomp(op), "x")
+        out = torch.empty_like(x)
+        p = vd_solve_params(tol=0.0, max_it=1, restart=1, use_x0=0, precision=0, inner_tol=0.0, check_every=1)
+        ws = self._workspace(vd_workspace_bytes(self.h, opc, VD_SOLVER_RMR, p))
+        vd_apply_precond(self.h, opc, vd_op_params(a, 1.0) if opc == VD_OP_VELOCITY else None, x, out, ws, stream)
+        return out
+
+    def solve_params(self, tol=1e-10, max_it=500, restart=30, use_x0=False, precision="fp64", inner_tol=1e-5,
+                     check_every=1):
+        return vd_solve_params(tol=tol, max_it=max_it, restart=restart, use_x0=int(bool(use_x0)),
+                               precision=PRECISIONS[precision], inner_tol=inner_tol, check_every=check_every)
+
+    def workspace_bytes(self, op, solver, **kw):
+        return vd_workspace_bytes(self.h, OPS[op], SOLVERS[solver], self.solve_params(**kw))
+
+    def solve(self, op, solver, b, x0=None, a=0.0, inv_sc=1.0, stream=None, hist_cap=0, out=None, **kw):
+        """Solve A x = b; returns (x, info dict)."""
+        import torch
+        opc, sc = OPS[op], SOLVERS[solver]
+        b = self._field(b, self._ncomp(op), "b")
+        if out is None:
+            out = torch.zeros_like(b)
+        if x0 is not None:
+            out.copy_(x0)
+            kw["use_x0"] = True
+        p = self.solve_params(**kw)
+        ws = self._workspace(vd_workspace_bytes(self.h, opc, sc, p))
+        info = vd_solve_info()
+        hist = None
+        if hist_cap > 0:
+            hist = (ctypes.c_double * hist_cap)()
+            info.hist = hist
+            info.hist_cap = hist_cap
+        st = vd_solve(self.h, opc, sc, vd_op_params(a, inv_sc) if opc == VD_OP_VELOCITY else None, p, b, out, info,
+                      ws, stream)
+        res = {"status": STATUS_NAMES.get(st, st), "iters": info.iters, "outer_iters": info.outer_iters,
+               "relres": info.relres, "relres_true": info.relres_true}
+        if hist is not None:
+            res["hist"] = [hist[i] for i in range(info.hist_len)]
+        return out, res
+
+    def divergence(self, u, stream=None):
+        import torch
+        u = self._field(u, self.ndim, "u")
+        out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        ws = self._workspace(16 * self.modes * 3 + 256)
+        vd_divergence(self.h, u, out, ws, stream)
+        return out
+
+    def gradient(self, phi, stream=None):
+        import torch
+        phi = self._field(phi, 0, "phi")
+        out = torch.empty((self.ndim,) + self.shape, dtype=torch.float64, device=self.device)
+        ws = self._workspace(16 * self.modes * 3 + 256)
+        vd_gradient(self.h, phi, out, ws, stream)
+        return out

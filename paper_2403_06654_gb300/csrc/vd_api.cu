@@ -1,0 +1,672 @@
+// C ABI of the library: grids, density data, operator/preconditioner application and
+// the preconditioned solves (double and mixed precision).
+#include "vd_krylov.cuh"
+#include "vd_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+namespace vd {
+
+static thread_local std::string g_err = "no error";
+
+vd_status fail(vd_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+vd_status cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  return (e == cudaErrorMemoryAllocation) ? VD_ERR_OOM : VD_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------------------
+// plans and twiddles
+// ---------------------------------------------------------------------------------------
+
+static bool make_plan(int n, FftPlan* p) {
+  if (n < 2 || n > 4096) return false;
+  int a = 0, b = 0, c = 0, r = n;
+  while (r % 2 == 0) { r /= 2; ++a; }
+  while (r % 3 == 0) { r /= 3; ++b; }
+  while (r % 5 == 0) { r /= 5; ++c; }
+  if (r != 1) return false;
+  p->n = n;
+  p->nst = 0;
+  auto push = [&](int R) { p->rad[p->nst++] = R; };
+  while (a >= 3) { push(8); a -= 3; }
+  if (a == 2) push(4);
+  if (a == 1) push(2);
+  while (b-- > 0) push(3);
+  while (c-- > 0) push(5);
+  return p->nst <= kMaxStages;
+}
+
+// exp(-2 pi i j / n) evaluated in extended precision, rounded once to double
+static void twiddle(long long j, long long n, double* re, double* im) {
+  j %= n;
+  const long double th = 2.0L * 3.14159265358979323846264338327950288L * (long double)j / (long double)n;
+  *re = (double)cosl(th);
+  *im = (double)(-sinl(th));
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  size_t cap;
+  template <typename P>
+  P* take(size_t bytes) {
+    P* p = reinterpret_cast<P*>(base ? base + off : nullptr);
+    off = align256(off + bytes);
+    return p;
+  }
+  bool ok() const { return off <= cap; }
+};
+
+}  // namespace vd
+
+using namespace vd;
+
+extern "C" {
+
+const char* vd_last_error(void) { return g_err.c_str(); }
+const char* vd_version(void) { return "vdspectral 0.1 (sm_103a)"; }
+
+vd_status vd_grid_create(int ndim, const int n[3], const double L[3], vd_grid** out) {
+  if (!out || !n || !L) return fail(VD_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (ndim < 1 || ndim > 3) return fail(VD_ERR_INVALID_ARG, "ndim must be 1, 2 or 3");
+  int nn[3] = {1, 1, 1};
+  for (int j = 0; j < ndim; ++j) {
+    nn[j] = n[j];
+    if (n[j] < 4 || n[j] > 1024 || (n[j] % 2) != 0)
+      return fail(VD_ERR_INVALID_ARG, "axis lengths must be even and in [4, 1024]");
+    if (!(L[j] > 0.0) || !std::isfinite(L[j])) return fail(VD_ERR_INVALID_ARG, "box lengths must be positive");
+  }
+  vd_grid* G = new vd_grid();
+  GridDesc& g = G->g;
+  g.ndim = ndim;
+  g.n0 = nn[0];
+  g.n1 = nn[1];
+  g.n2 = nn[2];
+  g.h0 = nn[0] / 2 + 1;
+  g.nreal = (long long)nn[0] * nn[1] * nn[2];
+  g.ncplx = (long long)g.h0 * nn[1] * nn[2];
+  for (int j = 0; j < 3; ++j) {
+    G->L[j] = (j < ndim) ? L[j] : 1.0;
+    g.kfac[j] = 2.0 * 3.14159265358979323846 / G->L[j];
+  }
+  bool ok = make_plan(nn[0] / 2, &g.px);
+  if (ndim >= 2) ok = ok && make_plan(nn[1], &g.py);
+  else g.py = g.px;
+  if (ndim == 3) ok = ok && make_plan(nn[2], &g.pz);
+  else g.pz = g.py;
+  if (!ok) {
+    delete G;
+    return fail(VD_ERR_INVALID_ARG, "axis lengths must factor into 2, 3 and 5");
+  }
+  // twiddle tables: px (m), py (n1), pz (n2), packing (m + 1)
+  std::vector<double> tw;
+  auto add = [&](FftPlan& p) {
+    p.tw_off = (int)(tw.size() / 2);
+    for (int j = 0; j < p.n; ++j) {
+      double re, im;
+      twiddle(j, p.n, &re, &im);
+      tw.push_back(re);
+      tw.push_back(im);
+    }
+  };
+  add(g.px);
+  if (ndim >= 2) add(g.py);
+  else g.py.tw_off = g.px.tw_off;
+  if (ndim == 3) add(g.pz);
+  else g.pz.tw_off = g.py.tw_off;
+  g.pk_off = (int)(tw.size() / 2);
+  for (int k = 0; k <= nn[0] / 2; ++k) {
+    double re, im;
+    twiddle(k, nn[0], &re, &im);
+    tw.push_back(re);
+    tw.push_back(im);
+  }
+  std::vector<float> twf(tw.size());
+  for (size_t i = 0; i < tw.size(); ++i) twf[i] = (float)tw[i];
+  cudaError_t e = cudaMalloc(&G->tw_d, tw.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&G->tw_f, twf.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(G->tw_d, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(G->tw_f, twf.data(), twf.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (G->tw_d) cudaFree(G->tw_d);
+    if (G->tw_f) cudaFree(G->tw_f);
+    delete G;
+    return cuda_fail(e, "vd_grid_create");
+  }
+  *out = G;
+  return VD_OK;
+}
+
+vd_status vd_grid_destroy(vd_grid* G) {
+  if (!G) return VD_OK;
+  if (G->tw_d) cudaFree(G->tw_d);
+  if (G->tw_f) cudaFree(G->tw_f);
+  delete G;
+  return VD_OK;
+}
+
+size_t vd_grid_points(const vd_grid* G) { return G ? (size_t)G->g.nreal : 0; }
+size_t vd_grid_modes(const vd_grid* G) { return G ? (size_t)G->g.ncplx : 0; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// density
+// ---------------------------------------------------------------------------------------
+
+namespace vd {
+
+__global__ void k_density_prep(long long n, const double* __restrict__ rho, double* __restrict__ rcopy,
+                               double* __restrict__ rinv_s, float* __restrict__ rinv_f, double invN,
+                               double* __restrict__ stats /* [min, max, bad] via block partials */) {
+  __shared__ double smin[256], smax[256], sbad[256];
+  double mn = 1e308, mx = -1e308, bd = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double r = rho[e];
+    rcopy[e] = r;
+    const double ri = invN / r;
+    rinv_s[e] = ri;
+    rinv_f[e] = (float)ri;
+    if (!(r > 0.0) || !isfinite(r)) bd = 1.0;
+    mn = fmin(mn, r);
+    mx = fmax(mx, r);
+  }
+  smin[threadIdx.x] = mn;
+  smax[threadIdx.x] = mx;
+  sbad[threadIdx.x] = bd;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + s]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + s]);
+      sbad[threadIdx.x] = fmax(sbad[threadIdx.x], sbad[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    stats[3 * blockIdx.x + 0] = smin[0];
+    stats[3 * blockIdx.x + 1] = smax[0];
+    stats[3 * blockIdx.x + 2] = sbad[0];
+  }
+}
+
+struct DensLayout {
+  double* rho;
+  double* rinv_s;
+  float* rinv_f;
+  double* stats;
+  double* grho;     // d fields
+  double* hrho;     // 6 fields, slot hidx(i, j)
+  cpx<double>* s0;  // scratch spectral fields (2)
+};
+
+static DensLayout dens_layout(const vd_grid* G, vd_op op, void* base, size_t* bytes) {
+  const GridDesc& g = G->g;
+  Carver c{(char*)base, 0, (size_t)-1};
+  DensLayout L;
+  const size_t nr = (size_t)g.nreal, nc = (size_t)g.ncplx;
+  L.rho = c.take<double>(nr * 8);
+  L.rinv_s = c.take<double>(nr * 8);
+  L.rinv_f = c.take<float>(nr * 4);
+  L.stats = c.take<double>(3 * 1024 * 8);
+  L.grho = L.hrho = nullptr;
+  L.s0 = nullptr;
+  if (op == VD_OP_VELOCITY) {
+    L.grho = c.take<double>(nr * 8 * g.ndim);
+    L.hrho = c.take<double>(nr * 8 * 6);   // indexed by hidx(i, j) in [0, 6)
+    L.s0 = c.take<cpx<double>>(nc * 16 * 2);
+  }
+  *bytes = c.off;
+  return L;
+}
+
+}  // namespace vd
+
+extern "C" {
+
+size_t vd_density_bytes(const vd_grid* G, vd_op op) {
+  if (!G) return 0;
+  size_t b = 0;
+  dens_layout(G, op, nullptr, &b);
+  return b;
+}
+
+vd_status vd_density_set(vd_grid* G, vd_op op, const double* rho, void* ws, size_t ws_bytes, vd_stream stream) {
+  if (!G || !rho || !ws) return fail(VD_ERR_INVALID_ARG, "null argument");
+  if (op != VD_OP_PRESSURE && op != VD_OP_VELOCITY) return fail(VD_ERR_INVALID_ARG, "unknown operator");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t need = 0;
+  DensLayout L = dens_layout(G, op, ws, &need);
+  if (ws_bytes < need) return fail(VD_ERR_OOM, "density workspace too small");
+  const GridDesc& g = G->g;
+  const int blocks = (int)std::min<long long>(1024, (g.nreal + 255) / 256);
+  k_density_prep<<<blocks, 256, 0, st>>>(g.nreal, rho, L.rho, L.rinv_s, L.rinv_f, 1.0 / (double)g.nreal, L.stats);
+  VD_CUDA(cudaGetLastError());
+  std::vector<double> stats(3 * blocks);
+  VD_CUDA(cudaMemcpyAsync(stats.data(), L.stats, stats.size() * 8, cudaMemcpyDeviceToHost, st));
+  VD_CUDA(cudaStreamSynchronize(st));
+  double mn = 1e308, mx = -1e308, bd = 0;
+  for (int b = 0; b < blocks; ++b) {
+    mn = std::min(mn, stats[3 * b]);
+    mx = std::max(mx, stats[3 * b + 1]);
+    bd = std::max(bd, stats[3 * b + 2]);
+  }
+  if (bd != 0.0) {
+    G->has_density = 0;
+    return fail(VD_ERR_INVALID_ARG, "density must be positive and finite");
+  }
+  G->rho = L.rho;
+  G->rinv_s = L.rinv_s;
+  G->rinv_s_f = L.rinv_f;
+  G->rho_min = mn;
+  G->rho_max = mx;
+  G->has_density = 1;
+  G->has_velocity_data = 0;
+  for (int j = 0; j < 3; ++j) G->grho[j] = nullptr;
+  for (int j = 0; j < 6; ++j) G->hrho[j] = nullptr;
+  if (op == VD_OP_VELOCITY) {
+    const int d = g.ndim;
+    const size_t nr = (size_t)g.nreal, nc = (size_t)g.ncplx;
+    cpx<double>* rh = L.s0;
+    cpx<double>* tmp = L.s0 + nc;
+    fwd_transform<double>(G, L.rho, rh, st);
+    for (int j = 0; j < d; ++j) {
+      Mult m;
+      m.deriv[j] = 1;
+      inv_transform<double>(G, rh, m, L.grho + j * nr, tmp, st);
+      G->grho[j] = L.grho + j * nr;
+    }
+    for (int i = 0; i < d; ++i)
+      for (int j = i; j < d; ++j) {
+        Mult m;
+        m.deriv[i] += 1;
+        m.deriv[j] += 1;
+        double* dst = L.hrho + hidx(i, j) * nr;
+        inv_transform<double>(G, rh, m, dst, tmp, st);
+        G->hrho[hidx(i, j)] = dst;
+      }
+    VD_CUDA(cudaGetLastError());
+    G->has_velocity_data = 1;
+  }
+  return VD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// workspace layout of apply / solve
+// ---------------------------------------------------------------------------------------
+
+namespace vd {
+
+struct SolveLayout {
+  KState* ks;
+  double* partials;
+  unsigned* counter;
+  double* hist;
+  double* sym;           // ncplx
+  float* sym_f;          // ncplx (mixed)
+  cpx<double>* bh;       // len
+  cpx<double>* xh;       // len
+  cpx<double>* rh;       // len (true residual / refinement)
+  void* vecs;            // Krylov vectors (double, or float for mixed)
+  cpx<double>* tmp;      // operator temporaries (double)
+  cpx<float>* tmp_f;     // operator temporaries (float, mixed)
+  cpx<float>* bh_f;      // inner rhs (mixed)
+  cpx<float>* xh_f;      // inner solution (mixed)
+};
+
+static int op_ncomp(const vd_grid* G, vd_op op) { return op == VD_OP_VELOCITY ? G->g.ndim : 1; }
+static int op_tmp_fields(const vd_grid* G, vd_op op) {
+  return op == VD_OP_VELOCITY ? velocity_tmp_fields(G->g.ndim) : pressure_tmp_fields(G->g.ndim);
+}
+
+static SolveLayout solve_layout(const vd_grid* G, vd_op op, int solver, int restart, int maxit, int precision,
+                                void* base, size_t* bytes) {
+  const size_t nc = (size_t)G->g.ncplx;
+  const int ncomp = op_ncomp(G, op);
+  const size_t len = nc * ncomp;
+  Carver c{(char*)base, 0, (size_t)-1};
+  SolveLayout L;
+  L.ks = c.take<KState>(sizeof(KState));
+  L.partials = c.take<double>(sizeof(double) * kRedBlocks * 8);
+  L.counter = c.take<unsigned>(sizeof(unsigned) * 4);
+  L.hist = c.take<double>(sizeof(double) * (size_t)(std::max(maxit, 1) + 2));
+  L.sym = c.take<double>(nc * 8);
+  L.sym_f = nullptr;
+  L.bh = c.take<cpx<double>>(len * 16);
+  L.xh = c.take<cpx<double>>(len * 16);
+  L.rh = c.take<cpx<double>>(len * 16);
+  SpecSystem dummy{};
+  dummy.len = (long long)len;
+  const int tf = std::max(op_tmp_fields(G, op), 1);
+  if (precision == VD_PREC_MIXED) {
+    L.sym_f = c.take<float>(nc * 4);
+    L.vecs = c.take<char>(krylov_vec_bytes<float>(dummy, solver, restart));
+    L.bh_f = c.take<cpx<float>>(len * 8);
+    L.xh_f = c.take<cpx<float>>(len * 8);
+    L.tmp_f = c.take<cpx<float>>(nc * 8 * tf);
+    // the double operator (true residual) needs its own temporaries and two vectors
+    L.tmp = c.take<cpx<double>>(nc * 16 * tf);
+  } else {
+    L.vecs = c.take<char>(krylov_vec_bytes<double>(dummy, solver, restart));
+    L.tmp = c.take<cpx<double>>(nc * 16 * tf);
+    L.tmp_f = nullptr;
+    L.bh_f = L.xh_f = nullptr;
+  }
+  *bytes = c.off;
+  return L;
+}
+
+// operator callbacks ---------------------------------------------------------------------
+
+template <typename T>
+static void apply_cb(const SpecSystem& sys, const void* in, void* out, bool with_sym, const int* done,
+                     cudaStream_t st) {
+  const vd_grid* G = sys.G;
+  const T* sym = with_sym ? (const T*)sys.sym : nullptr;
+  if (sys.ncomp == 1 && sys.ctx[1] == nullptr) {
+    apply_pressure_spec<T>(G, (const cpx<T>*)in, (cpx<T>*)out, sym, (const T*)sys.ctx[0], (cpx<T>*)sys.ctx[2], done, st);
+  } else {
+    apply_velocity_spec<T>(G, (const cpx<T>*)in, (cpx<T>*)out, sym, sys.a, sys.inv_sc, (cpx<T>*)sys.ctx[2], done, st);
+  }
+}
+
+template <typename T>
+static SpecSystem make_system(const vd_grid* G, vd_op op, const vd_op_params* p, const void* sym, void* tmp) {
+  SpecSystem s{};
+  s.G = G;
+  s.ncomp = op_ncomp(G, op);
+  s.len = (long long)G->g.ncplx * s.ncomp;
+  s.h0 = G->g.h0;
+  s.sym = sym;
+  s.is_float = sizeof(T) == 4;
+  s.apply = &apply_cb<T>;
+  s.ctx[0] = (sizeof(T) == 8) ? (void*)G->rinv_s : (void*)G->rinv_s_f;
+  s.ctx[1] = (op == VD_OP_VELOCITY) ? (void*)1 : nullptr;
+  s.ctx[2] = tmp;
+  s.a = p ? p->a : 0.0;
+  s.inv_sc = p ? p->inv_sc : 1.0;
+  return s;
+}
+
+static vd_status check_op(const vd_grid* G, vd_op op, const vd_op_params* p) {
+  if (!G) return fail(VD_ERR_INVALID_ARG, "null grid");
+  if (op != VD_OP_PRESSURE && op != VD_OP_VELOCITY) return fail(VD_ERR_INVALID_ARG, "unknown operator");
+  if (!G->has_density) return fail(VD_ERR_NO_DENSITY, "vd_density_set has not been called");
+  if (op == VD_OP_VELOCITY) {
+    if (!p) return fail(VD_ERR_INVALID_ARG, "velocity operator needs vd_op_params");
+    if (!G->has_velocity_data) return fail(VD_ERR_NO_DENSITY, "density was set for the pressure operator only");
+    if (!(p->a >= 0.0) || !std::isfinite(p->a) || !std::isfinite(p->inv_sc))
+      return fail(VD_ERR_INVALID_ARG, "velocity parameters must be finite, a >= 0");
+  }
+  return VD_OK;
+}
+
+// forward transform of every component (physical double -> spectral double)
+static void fwd_all(const vd_grid* G, int ncomp, const double* in, cpx<double>* out, cudaStream_t st) {
+  for (int c = 0; c < ncomp; ++c)
+    fwd_transform<double>(G, in + (size_t)c * G->g.nreal, out + (size_t)c * G->g.ncplx, st);
+}
+static void inv_all(const vd_grid* G, int ncomp, const cpx<double>* in, double* out, cpx<double>* tmp,
+                    cudaStream_t st) {
+  for (int c = 0; c < ncomp; ++c) {
+    Mult m;
+    inv_transform<double>(G, in + (size_t)c * G->g.ncplx, m, out + (size_t)c * G->g.nreal, tmp, st);
+  }
+}
+
+}  // namespace vd
+
+extern "C" {
+
+size_t vd_workspace_bytes(const vd_grid* G, vd_op op, vd_solver solver, const vd_solve_params* p) {
+  if (!G) return 0;
+  const int restart = p ? p->restart : 30;
+  const int maxit = p ? p->max_it : 1000;
+  const int prec = p ? p->precision : VD_PREC_FP64;
+  size_t b = 0;
+  solve_layout(G, op, solver, restart, maxit, prec, nullptr, &b);
+  return b;
+}
+
+vd_status vd_apply_op(const vd_grid* G, vd_op op, const vd_op_params* p, const double* in, double* out, void* ws,
+                      size_t ws_bytes, vd_stream stream) {
+  vd_status e = check_op(G, op, p);
+  if (e != VD_OK) return e;
+  if (!in || !out || !ws) return fail(VD_ERR_INVALID_ARG, "null buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t need = 0;
+  SolveLayout L = solve_layout(G, op, VD_SOLVER_RMR, 1, 1, VD_PREC_FP64, ws, &need);
+  if (ws_bytes < need) return fail(VD_ERR_OOM, "workspace too small");
+  const int ncomp = op_ncomp(G, op);
+  SpecSystem sys = make_system<double>(G, op, p, nullptr, L.tmp);
+  fwd_all(G, ncomp, in, L.bh, st);
+  sys.apply(sys, L.bh, L.xh, false, nullptr, st);
+  inv_all(G, ncomp, L.xh, out, L.tmp, st);
+  VD_CUDA(cudaGetLastError());
+  return VD_OK;
+}
+
+vd_status vd_apply_precond(const vd_grid* G, vd_op op, const vd_op_params* p, const double* in, double* out,
+                           void* ws, size_t ws_bytes, vd_stream stream) {
+  if (!G) return fail(VD_ERR_INVALID_ARG, "null grid");
+  if (op == VD_OP_VELOCITY && !p) return fail(VD_ERR_INVALID_ARG, "velocity preconditioner needs vd_op_params");
+  if (!in || !out || !ws) return fail(VD_ERR_INVALID_ARG, "null buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t need = 0;
+  SolveLayout L = solve_layout(G, op, VD_SOLVER_RMR, 1, 1, VD_PREC_FP64, ws, &need);
+  if (ws_bytes < need) return fail(VD_ERR_OOM, "workspace too small");
+  const int ncomp = op_ncomp(G, op);
+  fill_symbol<double>(G, op == VD_OP_PRESSURE ? SYM_PRESSURE : SYM_VELOCITY, p ? p->a : 0.0, L.sym, st);
+  fwd_all(G, ncomp, in, L.bh, st);
+  for (int c = 0; c < ncomp; ++c) {
+    Mult m;
+    m.sym = 1;
+    m.symarr = L.sym;
+    inv_transform<double>(G, L.bh + (size_t)c * G->g.ncplx, m, out + (size_t)c * G->g.nreal, L.tmp, st);
+  }
+  VD_CUDA(cudaGetLastError());
+  return VD_OK;
+}
+
+vd_status vd_divergence(const vd_grid* G, const double* u, double* out, void* ws, size_t ws_bytes, vd_stream stream) {
+  if (!G || !u || !out || !ws) return fail(VD_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const GridDesc& g = G->g;
+  const size_t need = align256((size_t)g.ncplx * 16 * 3);
+  if (ws_bytes < need) return fail(VD_ERR_OOM, "workspace too small (3 spectral fields)");
+  cpx<double>* a = (cpx<double>*)ws;
+  cpx<double>* acc = a + g.ncplx;
+  cpx<double>* tmp = acc + g.ncplx;
+  // out = sum_j F^-1(i k_j F u_j): accumulate i k_j u^_j in spectral space via derivative transforms
+  VD_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * g.nreal, st));
+  for (int j = 0; j < g.ndim; ++j) {
+    fwd_transform<double>(G, u + (size_t)j * g.nreal, a, st);
+    Mult m;
+    m.deriv[j] = 1;
+    inv_transform<double>(G, a, m, reinterpret_cast<double*>(acc), tmp, st);
+    // out += acc (physical): reuse spectral axpy on reals viewed as complex pairs
+    spec_axpy<double>(g.nreal / 2, 1.0, acc, out, st);
+  }
+  VD_CUDA(cudaGetLastError());
+  return VD_OK;
+}
+
+vd_status vd_gradient(const vd_grid* G, const double* phi, double* out, void* ws, size_t ws_bytes, vd_stream stream) {
+  if (!G || !phi || !out || !ws) return fail(VD_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const GridDesc& g = G->g;
+  const size_t need = align256((size_t)g.ncplx * 16 * 3);
+  if (ws_bytes < need) return fail(VD_ERR_OOM, "workspace too small (3 spectral fields)");
+  cpx<double>* a = (cpx<double>*)ws;
+  cpx<double>* tmp = a + g.ncplx;
+  fwd_transform<double>(G, phi, a, st);
+  for (int j = 0; j < g.ndim; ++j) {
+    Mult m;
+    m.deriv[j] = 1;
+    inv_transform<double>(G, a, m, out + (size_t)j * g.nreal, tmp, st);
+  }
+  VD_CUDA(cudaGetLastError());
+  return VD_OK;
+}
+
+vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_params* opp, const vd_solve_params* prm,
+                   const double* b, double* x, vd_solve_info* info, void* ws, size_t ws_bytes, vd_stream stream) {
+  vd_status e = check_op(G, op, opp);
+  if (e != VD_OK) return e;
+  if (!prm || !b || !x || !ws) return fail(VD_ERR_INVALID_ARG, "null argument");
+  if (solver != VD_SOLVER_CG && solver != VD_SOLVER_GMRES && solver != VD_SOLVER_RMR)
+    return fail(VD_ERR_INVALID_ARG, "unknown solver");
+  if (solver == VD_SOLVER_CG && op == VD_OP_VELOCITY)
+    return fail(VD_ERR_INVALID_ARG, "CG needs a symmetric operator; V_rho is not symmetric");
+  if (!(prm->tol >= 0.0) || prm->max_it < 0) return fail(VD_ERR_INVALID_ARG, "tol must be >= 0 and max_it >= 0");
+  if (prm->precision != VD_PREC_FP64 && prm->precision != VD_PREC_MIXED)
+    return fail(VD_ERR_INVALID_ARG, "unknown precision mode");
+  if (solver == VD_SOLVER_GMRES && prm->restart > kMaxRestart)
+    return fail(VD_ERR_INVALID_ARG, "GMRES restart must be <= 64");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int restart = prm->restart > 0 ? prm->restart : 30;
+  size_t need = 0;
+  SolveLayout L = solve_layout(G, op, solver, restart, prm->max_it, prm->precision, ws, &need);
+  if (ws_bytes < need) return fail(VD_ERR_OOM, "workspace too small");
+  const GridDesc& g = G->g;
+  const int ncomp = op_ncomp(G, op);
+  const long long len = g.ncplx * ncomp;
+  const int symkind = (op == VD_OP_PRESSURE) ? SYM_PRESSURE : SYM_VELOCITY;
+  // the reduction ticket counter must start at zero (the workspace is uninitialised memory)
+  VD_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned), st));
+  fill_symbol<double>(G, symkind, opp ? opp->a : 0.0, L.sym, st);
+  // spectral right-hand side and initial guess
+  fwd_all(G, ncomp, b, L.bh, st);
+  if (op == VD_OP_PRESSURE) spec_project<double>(G, 1, L.bh, st);
+  if (prm->use_x0) {
+    fwd_all(G, ncomp, x, L.xh, st);
+    if (op == VD_OP_PRESSURE) spec_project<double>(G, 1, L.xh, st);
+  } else {
+    VD_CUDA(cudaMemsetAsync(L.xh, 0, sizeof(cpx<double>) * len, st));
+  }
+  KWork kw{L.ks, L.partials, L.counter, L.hist};
+  SolveOpts so;
+  so.solver = solver;
+  so.tol = prm->tol;
+  so.maxit = prm->max_it;
+  so.restart = restart;
+  so.check_every = prm->check_every > 0 ? prm->check_every : 1;
+  SolveOut res{0, VD_ERR_NOT_CONVERGED, 0.0};
+  double* hh = (info && info->hist && info->hist_cap > 0) ? info->hist : nullptr;
+  // the device history buffer holds max_it + 2 entries
+  const int hcap = hh ? std::min(info->hist_cap, prm->max_it + 2) : 0;
+  SpecSystem sys64 = make_system<double>(G, op, opp, L.sym, L.tmp);
+  int outer = 0;
+  double relres_true = 0.0;
+  if (prm->precision == VD_PREC_FP64) {
+    e = krylov_solve<double>(sys64, so, L.bh, L.xh, L.vecs, kw, hh, hcap, &res, st);
+    if (e != VD_OK) return e;
+  } else {
+    // iterative refinement: r = b - A64 x; inner float solve A32 d = r/|r|; x += |r| d
+    fill_symbol<float>(G, symkind, opp ? opp->a : 0.0, L.sym_f, st);
+    SpecSystem sys32 = make_system<float>(G, op, opp, L.sym_f, L.tmp_f);
+    const double bb = spec_norm2_host<double>(sys64, L.bh, kw, st);
+    const double bnorm = std::sqrt(bb);
+    if (prm->use_x0) {
+      sys64.apply(sys64, L.xh, L.rh, false, nullptr, st);
+      spec_sub<double>(len, L.bh, L.rh, L.rh, st);
+    } else {
+      VD_CUDA(cudaMemcpyAsync(L.rh, L.bh, sizeof(cpx<double>) * len, cudaMemcpyDeviceToDevice, st));
+    }
+    double rnorm = std::sqrt(spec_norm2_host<double>(sys64, L.rh, kw, st));
+    int total = 0;
+    int hlen = 0;
+    if (hh && hcap > 0) hh[hlen++] = bnorm > 0 ? rnorm / bnorm : 0.0;
+    res.status = VD_ERR_NOT_CONVERGED;
+    const double itol = prm->inner_tol > 0 ? prm->inner_tol : 1e-5;
+    const int max_outer = 20;
+    for (;;) {
+      const double rel = bnorm > 0 ? rnorm / bnorm : 0.0;
+      res.relres = rel;
+      if (!std::isfinite(rel)) {
+        res.status = VD_ERR_NONFINITE;
+        break;
+      }
+      if (rel <= prm->tol) {
+        res.status = VD_OK;
+        break;
+      }
+      if (total >= prm->max_it || outer >= max_outer) break;
+      spec_copy_scale<double>(len, L.rh, 1.0 / rnorm, L.rh, st);
+      spec_d2f(len, L.rh, L.bh_f, st);
+      VD_CUDA(cudaMemsetAsync(L.xh_f, 0, sizeof(cpx<float>) * len, st));
+      SolveOpts si = so;
+      // ask the inner solve for a little more than needed so that the refined residual lands
+      // below tol when it is the last sweep
+      si.tol = std::max(itol, 0.5 * prm->tol / rel);
+      si.maxit = prm->max_it - total;
+      SolveOut ri{0, 0, 0.0};
+      std::vector<double> ih;
+      const int icap = hh ? std::min(std::max(0, hcap - hlen) + 1, prm->max_it + 2) : 0;
+      if (icap > 0) ih.resize(icap);
+      e = krylov_solve<float>(sys32, si, L.bh_f, L.xh_f, L.vecs, kw, icap > 0 ? ih.data() : nullptr, icap, &ri, st);
+      if (e != VD_OK) return e;
+      // history: inner residuals rescaled to the outer right-hand side
+      for (int i = 1; i <= ri.iters && hlen < hcap && i < (int)ih.size(); ++i) hh[hlen++] = ih[i] * rel;
+      total += ri.iters;
+      ++outer;
+      // x += rnorm * d  (d promoted to double)
+      spec_f2d(len, L.xh_f, L.rh, st);
+      spec_axpy<double>(len, rnorm, L.rh, L.xh, st);
+      // true residual with the double operator
+      sys64.apply(sys64, L.xh, L.rh, false, nullptr, st);
+      spec_sub<double>(len, L.bh, L.rh, L.rh, st);
+      rnorm = std::sqrt(spec_norm2_host<double>(sys64, L.rh, kw, st));
+      if (ri.status == VD_ERR_NONFINITE) {
+        res.status = VD_ERR_NONFINITE;
+        break;
+      }
+      if (ri.iters == 0 && ri.status != VD_OK) break;
+    }
+    res.iters = total;
+    relres_true = bnorm > 0 ? rnorm / bnorm : 0.0;
+    if (info) info->hist_len = hlen;
+  }
+  // back to physical space
+  inv_all(G, ncomp, L.xh, x, L.tmp, st);
+  if (prm->precision == VD_PREC_FP64) {
+    // true residual of the returned iterate
+    const double bb = spec_norm2_host<double>(sys64, L.bh, kw, st);
+    sys64.apply(sys64, L.xh, L.rh, false, nullptr, st);
+    spec_sub<double>(len, L.bh, L.rh, L.rh, st);
+    const double rr = spec_norm2_host<double>(sys64, L.rh, kw, st);
+    relres_true = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+    if (info) info->hist_len = hh ? std::min(hcap, res.iters + 1) : 0;
+  }
+  VD_CUDA(cudaGetLastError());
+  VD_CUDA(cudaStreamSynchronize(st));
+  if (info) {
+    info->iters = res.iters;
+    info->outer_iters = outer;
+    info->status = res.status;
+    info->relres = res.relres;
+    info->relres_true = relres_true;
+  }
+  if (res.status != VD_OK) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "solve ended with status %d after %d iterations (relres %.3e)", res.status,
+                  res.iters, res.relres);
+    g_err = buf;
+  }
+  return (vd_status)res.status;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal host-side structures of the library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "vd.h"
+#include "vd_common.cuh"
+#include "vd_passes.cuh"
+
+struct vd_grid {
+  vd::GridDesc g;
+  double L[3];
+  void* tw_d = nullptr;   // cpx<double> twiddle table (library-owned)
+  void* tw_f = nullptr;   // cpx<float> copy
+  // density data (inside the caller's density workspace; set by vd_density_set)
+  const double* rinv_s = nullptr;    // 1/(N rho), physical
+  const float* rinv_s_f = nullptr;   // same, float
+  const double* grho[3] = {nullptr, nullptr, nullptr};     // D_j rho
+  const double* hrho[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // D_i D_j rho (i<=j)
+  const double* rho = nullptr;       // copy of rho
+  double rho_min = 0, rho_max = 0;
+  int has_density = 0;
+  int has_velocity_data = 0;
+};
+
+namespace vd {
+
+// set the thread-local error message and return the status
+vd_status fail(vd_status st, const std::string& msg);
+vd_status cuda_fail(cudaError_t e, const char* what);
+
+#define VD_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return vd::cuda_fail(e_, #call); \
+  } while (0)
+
+// index of the symmetric second-derivative pair (i <= j) in hrho[]
+inline int hidx(int i, int j) {
+  if (i > j) {
+    int t = i;
+    i = j;
+    j = t;
+  }
+  static const int tab[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+  return tab[i][j];
+}
+
+// ------------------------------------------------------------------------------------
+// generic transforms (vd_ops.cu).  Spectral fields hold g.ncplx elements, physical ones
+// g.nreal.  deriv[j] in {0,1,2}: multiply by (i k~_j)^deriv[j]; sym/negk2 as MulFlags.
+// ------------------------------------------------------------------------------------
+
+struct Mult {
+  int deriv[3] = {0, 0, 0};
+  int sym = 0;          // multiply by symbol array
+  int negk2 = 0;        // multiply by -|k~|^2
+  const void* symarr = nullptr;
+  double scale = 1.0;
+};
+
+// physical (T, nreal) -> spectral (cpx<T>, ncplx).  tmp: one spectral field.
+template <typename T>
+void fwd_transform(const vd_grid* G, const T* in, cpx<T>* out, cudaStream_t st);
+// spectral -> physical with multiplier. tmp: one spectral field (2D/3D); `in` untouched.
+template <typename T>
+void inv_transform(const vd_grid* G, const cpx<T>* in, const Mult& m, T* out, cpx<T>* tmp, cudaStream_t st);
+
+// Pressure operator in spectral space: out = L~ (S in) with S = symarr (if non-null) else 1.
+// tmp: 3 spectral fields (3D), 2 (2D), 0 (1D).  done: optional early-exit flag.
+template <typename T>
+void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, const T* rinv_s,
+                         cpx<T>* tmp, const int* done, cudaStream_t st);
+
+// Velocity operator in spectral space: out_i = (S in)_i - a * F[rho^-1 (Lap u + Sc^-1 (...))]_i with u =
+// F^-1 (S in).  ncomp = ndim components stored back to back.  tmp: see velocity_tmp_fields().
+template <typename T>
+void apply_velocity_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, double a,
+                         double inv_sc, cpx<T>* tmp, const int* done, cudaStream_t st);
+int velocity_tmp_fields(int ndim);   // spectral-field-sized temporaries
+int pressure_tmp_fields(int ndim);
+
+// symbol arrays (real, ncplx): pressure -1/|k~|^2 (0 on corners), velocity 1/(1+a|k~|^2),
+// projection 1 / 0 on corners
+template <typename T>
+void fill_symbol(const vd_grid* G, int kind, double a, T* out, cudaStream_t st);
+
+}  // namespace vd

@@ -1,0 +1,777 @@
+// Krylov solvers: CG, restarted GMRES (CGS2 Arnoldi) and Richardson Minimal Residual.
+//
+// Every reduction is a two-level deterministic sum in double precision: a fixed number of
+// blocks writes per-block partials, and the last block to finish (atomic ticket) adds them
+// in a fixed order and runs the scalar epilogue of the algorithm (step lengths, Givens
+// rotations, convergence tests) in one thread.  The scalars never leave the device; the
+// host only reads the `done` flag every `check_every` iterations.  Kernels of an iteration
+// return at once when the flag is set, so the host may enqueue iterations ahead.
+#include "vd_krylov.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+
+namespace vd {
+
+// ---------------------------------------------------------------------------------------
+// reduction machinery
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ double wgt(long long e, int h0) {
+  const int kx = (int)(e % h0);
+  return (kx == 0 || kx == h0 - 1) ? 1.0 : 2.0;
+}
+
+template <typename T>
+__device__ __forceinline__ cpx<double> ld(const cpx<T>* p, long long e) {
+  const cpx<T> v = p[e];
+  return mk<double>((double)v.x, (double)v.y);
+}
+
+// Block-sum v[0..NV) into per-block partials; the last block gets the totals in thread 0.
+// Returns true (in every thread of the last block) when the caller must run the epilogue.
+template <int NV>
+__device__ bool reduce_last(double (&v)[NV], double* partials, unsigned* counter, double (&tot)[NV]) {
+  __shared__ double sm[NV][kRedThreads / 32];
+  __shared__ int am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = v[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sm[i][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double s = 0.0;
+      for (int w = 0; w < kRedThreads / 32; ++w) s += sm[i][w];
+      partials[blockIdx.x * NV + i] = s;
+    }
+    __threadfence();
+    const unsigned t = atomicAdd(counter, 1u);
+    am_last = (t == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  double a[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) a[i] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) a[i] += __ldcg(partials + b * NV + i);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = a[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sm[i][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double s = 0.0;
+      for (int w = 0; w < kRedThreads / 32; ++w) s += sm[i][w];
+      tot[i] = s;
+    }
+    *counter = 0u;
+  }
+  return true;
+}
+
+static inline int red_blocks(long long len) {
+  return (int)std::max<long long>(1, std::min<long long>(kRedBlocks, (len + kRedThreads - 1) / kRedThreads));
+}
+
+#define GRID_STRIDE(e, len) \
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (len); e += (long long)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ bool bad(double v) { return !isfinite(v); }
+
+__device__ void finish(KState* ks, int status) {
+  ks->status = status;
+  ks->done = 1;
+  ks->cycle_done = 1;
+}
+
+__device__ void record(KState* ks, double* hist, double rel) {
+  if (ks->iters < ks->hist_cap) hist[ks->iters] = rel;
+}
+
+// ---------------------------------------------------------------------------------------
+// epilogues
+// ---------------------------------------------------------------------------------------
+
+enum Epi : int {
+  EPI_INIT_CG = 0,    // tot = [bb, rr, rz]
+  EPI_CG_ALPHA = 1,   // tot = [pq]
+  EPI_CG_UPDATE = 2,  // tot = [rr, rz]
+  EPI_INIT_RMR = 3,   // tot = [bb, rr]
+  EPI_RMR_ALPHA = 4,  // tot = [rw, ww]
+  EPI_RMR_UPDATE = 5, // tot = [rr]
+  EPI_BB = 6,         // tot = [bb]
+  EPI_GM_BETA = 7,    // tot = [rr]
+  EPI_GM_H1 = 8,      // tot[i] -> h1[off + i]
+  EPI_GM_H2 = 9,      // tot[i] -> h2[off + i]
+  EPI_GM_NORM = 10,   // tot = [ww]
+  EPI_NORM = 11,      // tot = [vv] -> ks->rr
+};
+
+template <int NV>
+__device__ void epilogue(int epi, const double (&t)[NV], KState* ks, double* hist, double tol, int off, int j) {
+  switch (epi) {
+    case EPI_INIT_CG:
+    case EPI_INIT_RMR: {
+      ks->bb = t[0];
+      ks->tol2bb = tol * tol * t[0];
+      if (t[0] == 0.0) {
+        ks->relres = 0.0;
+        record(ks, hist, 0.0);
+        finish(ks, 0);
+        return;
+      }
+      const double rel = sqrt(t[1] / t[0]);
+      ks->relres = rel;
+      ks->best = rel;
+      ks->rr = t[1];
+      if (epi == EPI_INIT_CG) ks->rz = t[NV > 2 ? 2 : 0];
+      record(ks, hist, rel);
+      if (bad(rel)) finish(ks, VD_ERR_NONFINITE);
+      else if (rel <= tol) finish(ks, 0);
+      else if (ks->maxit <= 0) finish(ks, VD_ERR_NOT_CONVERGED);
+      return;
+    }
+    case EPI_CG_ALPHA: {
+      const double pq = t[0];
+      ks->pq = pq;
+      if (pq == 0.0 || ks->rz == 0.0) {
+        ks->iters += 1;
+        finish(ks, VD_ERR_BREAKDOWN);
+        return;
+      }
+      ks->alpha = ks->rz / pq;
+      if (bad(ks->alpha)) {
+        ks->iters += 1;
+        finish(ks, VD_ERR_NONFINITE);
+      }
+      return;
+    }
+    case EPI_CG_UPDATE:
+    case EPI_RMR_UPDATE: {
+      ks->iters += 1;
+      const double rr = t[0];
+      const double rel = sqrt(rr / ks->bb);
+      ks->rr = rr;
+      ks->relres = rel;
+      record(ks, hist, rel);
+      if (bad(rel)) {
+        finish(ks, VD_ERR_NONFINITE);
+        return;
+      }
+      if (rr <= ks->tol2bb) {
+        finish(ks, 0);
+        return;
+      }
+      if (rel > 1e3 * ks->best) {
+        finish(ks, VD_ERR_DIVERGED);
+        return;
+      }
+      ks->best = fmin(ks->best, rel);
+      if (epi == EPI_CG_UPDATE) {
+        const double rz = t[NV > 1 ? 1 : 0];
+        ks->beta = rz / ks->rz;
+        ks->rz = rz;
+      }
+      if (ks->iters >= ks->maxit) finish(ks, VD_ERR_NOT_CONVERGED);
+      return;
+    }
+    case EPI_RMR_ALPHA: {
+      const double ww = t[NV > 1 ? 1 : 0];
+      ks->rw = t[0];
+      ks->ww = ww;
+      if (ww == 0.0) {
+        ks->iters += 1;
+        finish(ks, VD_ERR_BREAKDOWN);
+        return;
+      }
+      ks->alpha = t[0] / ww;
+      return;
+    }
+    case EPI_BB: {
+      ks->bb = t[0];
+      ks->tol2bb = tol * tol * t[0];
+      return;
+    }
+    case EPI_GM_BETA: {
+      const double beta = sqrt(t[0]);
+      ks->beta0 = beta;
+      if (ks->bb == 0.0) {
+        ks->relres = 0.0;
+        if (ks->iters == 0) record(ks, hist, 0.0);
+        finish(ks, 0);
+        return;
+      }
+      const double rel = beta / sqrt(ks->bb);
+      if (ks->iters == 0) record(ks, hist, rel);
+      ks->relres = rel;
+      if (bad(rel)) finish(ks, VD_ERR_NONFINITE);
+      else if (rel <= tol) finish(ks, 0);
+      else if (ks->iters >= ks->maxit) finish(ks, VD_ERR_NOT_CONVERGED);
+      else {
+        ks->k = 0;
+        ks->cycle_done = 0;
+        ks->gv[0] = beta;
+      }
+      return;
+    }
+    case EPI_GM_H1:
+    case EPI_GM_H2: {
+      double* h = (epi == EPI_GM_H1) ? ks->h1 : ks->h2;
+      for (int i = 0; i < NV; ++i)
+        if (off + i <= j) h[off + i] = t[i];
+      return;
+    }
+    case EPI_GM_NORM: {
+      const int m = ks->m;
+      const double hn = sqrt(t[0]);
+      double* col = ks->H + (size_t)j * (m + 1);
+      for (int i = 0; i <= j; ++i) col[i] = ks->h1[i] + ks->h2[i];
+      col[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double a = ks->cs[i] * col[i] + ks->sn[i] * col[i + 1];
+        col[i + 1] = -ks->sn[i] * col[i] + ks->cs[i] * col[i + 1];
+        col[i] = a;
+      }
+      double c = 1.0, s = 0.0;
+      if (col[j + 1] != 0.0) {
+        const double h = hypot(col[j], col[j + 1]);
+        c = col[j] / h;
+        s = col[j + 1] / h;
+      }
+      ks->cs[j] = c;
+      ks->sn[j] = s;
+      col[j] = c * col[j] + s * col[j + 1];
+      col[j + 1] = 0.0;
+      ks->gv[j + 1] = -s * ks->gv[j];
+      ks->gv[j] = c * ks->gv[j];
+      ks->iters += 1;
+      ks->k = j + 1;
+      const double est = fabs(ks->gv[j + 1]) / sqrt(ks->bb);
+      ks->relres = est;
+      record(ks, hist, est);
+      ks->ww = hn;
+      if (bad(est)) {
+        ks->status = VD_ERR_NONFINITE;
+        ks->cycle_done = 1;
+      } else if (est <= tol || hn == 0.0) {
+        ks->status = 0;   // converged (or invariant Krylov space): finished after the update
+        ks->cycle_done = 1;
+      } else if (j + 1 >= m || ks->iters >= ks->maxit) {
+        ks->cycle_done = 1;
+      }
+      return;
+    }
+    case EPI_NORM: {
+      ks->rr = t[0];
+      return;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------------------
+
+struct RedArgs {
+  KState* ks;
+  double* partials;
+  unsigned* counter;
+  double* hist;
+  double tol;
+};
+
+// CG start: p = S r, reduce [bb, rr, rz]
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_cg_init(long long len, int h0, long long ncplx,
+                                                         const cpx<T>* __restrict__ b, const cpx<T>* __restrict__ r,
+                                                         cpx<T>* __restrict__ p, const T* __restrict__ sym,
+                                                         RedArgs ra) {
+  double v[3] = {0.0, 0.0, 0.0};
+  GRID_STRIDE(e, len) {
+    const double w = wgt(e, h0);
+    const cpx<double> bv = ld(b, e), rv = ld(r, e);
+    const double s = (double)sym[e % ncplx];
+    p[e] = mk<T>((T)(s * rv.x), (T)(s * rv.y));
+    v[0] += w * (bv.x * bv.x + bv.y * bv.y);
+    const double r2 = rv.x * rv.x + rv.y * rv.y;
+    v[1] += w * r2;
+    v[2] += w * s * r2;
+  }
+  double t[3];
+  if (reduce_last<3>(v, ra.partials, ra.counter, t) && threadIdx.x == 0)
+    epilogue<3>(EPI_INIT_CG, t, ra.ks, ra.hist, ra.tol, 0, 0);
+}
+
+// reduce [(u,v)_w] or [(u,v)_w, (v,v)_w]
+template <typename T, int NV>
+__global__ void __launch_bounds__(kRedThreads) k_dot(long long len, int h0, const cpx<T>* __restrict__ u,
+                                                     const cpx<T>* __restrict__ v, int epi, RedArgs ra,
+                                                     const int* done) {
+  if (*done) return;
+  double a[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) a[i] = 0.0;
+  GRID_STRIDE(e, len) {
+    const double w = wgt(e, h0);
+    const cpx<double> uu = ld(u, e), vv = ld(v, e);
+    a[0] += w * (uu.x * vv.x + uu.y * vv.y);
+    if (NV > 1) a[NV - 1] += w * (vv.x * vv.x + vv.y * vv.y);
+  }
+  double t[NV];
+  if (reduce_last<NV>(a, ra.partials, ra.counter, t) && threadIdx.x == 0)
+    epilogue<NV>(epi, t, ra.ks, ra.hist, ra.tol, 0, 0);
+}
+
+// CG: x += alpha p, r -= alpha q; reduce [rr, (r, S r)]
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_cg_update(long long len, int h0, long long ncplx,
+                                                           cpx<T>* __restrict__ x, const cpx<T>* __restrict__ p,
+                                                           cpx<T>* __restrict__ r, const cpx<T>* __restrict__ q,
+                                                           const T* __restrict__ sym, RedArgs ra) {
+  if (ra.ks->done) return;
+  const double al = ra.ks->alpha;
+  double v[2] = {0.0, 0.0};
+  GRID_STRIDE(e, len) {
+    const double w = wgt(e, h0);
+    const cpx<double> pv = ld(p, e), qv = ld(q, e);
+    cpx<double> xv = ld(x, e), rv = ld(r, e);
+    xv = mk<double>(fma(al, pv.x, xv.x), fma(al, pv.y, xv.y));
+    rv = mk<double>(fma(-al, qv.x, rv.x), fma(-al, qv.y, rv.y));
+    x[e] = mk<T>((T)xv.x, (T)xv.y);
+    const cpx<T> rt = mk<T>((T)rv.x, (T)rv.y);
+    r[e] = rt;
+    const double r2 = (double)rt.x * rt.x + (double)rt.y * rt.y;
+    v[0] += w * r2;
+    v[1] += w * (double)sym[e % ncplx] * r2;
+  }
+  double t[2];
+  if (reduce_last<2>(v, ra.partials, ra.counter, t) && threadIdx.x == 0)
+    epilogue<2>(EPI_CG_UPDATE, t, ra.ks, ra.hist, ra.tol, 0, 0);
+}
+
+// CG: p = S r + beta p
+template <typename T>
+__global__ void k_cg_p(long long len, long long ncplx, cpx<T>* __restrict__ p, const cpx<T>* __restrict__ r,
+                       const T* __restrict__ sym, const KState* ks) {
+  if (ks->done) return;
+  const double be = ks->beta;
+  GRID_STRIDE(e, len) {
+    const double s = (double)sym[e % ncplx];
+    const cpx<double> rv = ld(r, e), pv = ld(p, e);
+    p[e] = mk<T>((T)fma(be, pv.x, s * rv.x), (T)fma(be, pv.y, s * rv.y));
+  }
+}
+
+// RMR / GMRES start: reduce [bb, rr] or [rr]
+template <typename T, int NV>
+__global__ void __launch_bounds__(kRedThreads) k_norms(long long len, int h0, const cpx<T>* __restrict__ b,
+                                                       const cpx<T>* __restrict__ r, int epi, RedArgs ra,
+                                                       const int* done) {
+  if (done && *done) return;
+  double v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.0;
+  GRID_STRIDE(e, len) {
+    const double w = wgt(e, h0);
+    const cpx<double> rv = ld(r, e);
+    if (NV == 2) {
+      const cpx<double> bv = ld(b, e);
+      v[0] += w * (bv.x * bv.x + bv.y * bv.y);
+    }
+    v[NV - 1] += w * (rv.x * rv.x + rv.y * rv.y);
+  }
+  double t[NV];
+  if (reduce_last<NV>(v, ra.partials, ra.counter, t) && threadIdx.x == 0)
+    epilogue<NV>(epi, t, ra.ks, ra.hist, ra.tol, 0, 0);
+}
+
+// RMR: x += alpha S r, r -= alpha w; reduce [rr]
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_rmr_update(long long len, int h0, long long ncplx,
+                                                            cpx<T>* __restrict__ x, cpx<T>* __restrict__ r,
+                                                            const cpx<T>* __restrict__ wv, const T* __restrict__ sym,
+                                                            RedArgs ra) {
+  if (ra.ks->done) return;
+  const double al = ra.ks->alpha;
+  double v[1] = {0.0};
+  GRID_STRIDE(e, len) {
+    const double w = wgt(e, h0);
+    const double s = (double)sym[e % ncplx];
+    const cpx<double> wq = ld(wv, e);
+    cpx<double> xv = ld(x, e), rv = ld(r, e);
+    xv = mk<double>(fma(al * s, rv.x, xv.x), fma(al * s, rv.y, xv.y));
+    rv = mk<double>(fma(-al, wq.x, rv.x), fma(-al, wq.y, rv.y));
+    x[e] = mk<T>((T)xv.x, (T)xv.y);
+    const cpx<T> rt = mk<T>((T)rv.x, (T)rv.y);
+    r[e] = rt;
+    v[0] += w * ((double)rt.x * rt.x + (double)rt.y * rt.y);
+  }
+  double t[1];
+  if (reduce_last<1>(v, ra.partials, ra.counter, t) && threadIdx.x == 0)
+    epilogue<1>(EPI_RMR_UPDATE, t, ra.ks, ra.hist, ra.tol, 0, 0);
+}
+
+// GMRES: dst = src / beta0 (first basis vector) or src / H[j+1,j] (next)
+template <typename T>
+__global__ void k_gm_scale(long long len, cpx<T>* __restrict__ dst, const cpx<T>* __restrict__ src, const KState* ks,
+                           int first) {
+  if (ks->cycle_done) return;
+  const double s = 1.0 / (first ? ks->beta0 : ks->ww);
+  GRID_STRIDE(e, len) {
+    const cpx<double> v = ld(src, e);
+    dst[e] = mk<T>((T)(v.x * s), (T)(v.y * s));
+  }
+}
+
+// GMRES: h[off + i] = (w, V_{off+i})_w for i < nv (<= 8)
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_gm_mdot(long long len, int h0, const cpx<T>* __restrict__ w,
+                                                         const cpx<T>* __restrict__ V, int off, int nv, int epi, int j,
+                                                         RedArgs ra) {
+  if (ra.ks->cycle_done) return;
+  double a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = 0.0;
+  GRID_STRIDE(e, len) {
+    const double wt = wgt(e, h0);
+    const cpx<double> wv = ld(w, e);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (i < nv) {
+        const cpx<double> vv = ld(V + (size_t)(off + i) * len, e);
+        a[i] += wt * (wv.x * vv.x + wv.y * vv.y);
+      }
+    }
+  }
+  double t[8];
+  if (reduce_last<8>(a, ra.partials, ra.counter, t) && threadIdx.x == 0)
+    epilogue<8>(epi, t, ra.ks, ra.hist, ra.tol, off, j);
+}
+
+// GMRES: w -= sum_{i<=j} h_i V_i (h = h1 or h2); with_norm: reduce [(w,w)] -> EPI_GM_NORM
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_gm_maxpy(long long len, int h0, cpx<T>* __restrict__ w,
+                                                          const cpx<T>* __restrict__ V, int j, int which, int with_norm,
+                                                          RedArgs ra) {
+  if (ra.ks->cycle_done) return;
+  const double* h = which ? ra.ks->h2 : ra.ks->h1;
+  double v[1] = {0.0};
+  GRID_STRIDE(e, len) {
+    cpx<double> wv = ld(w, e);
+    for (int i = 0; i <= j; ++i) {
+      const double c = h[i];
+      const cpx<double> vv = ld(V + (size_t)i * len, e);
+      wv = mk<double>(fma(-c, vv.x, wv.x), fma(-c, vv.y, wv.y));
+    }
+    const cpx<T> wt = mk<T>((T)wv.x, (T)wv.y);
+    w[e] = wt;
+    v[0] += wgt(e, h0) * ((double)wt.x * wt.x + (double)wt.y * wt.y);
+  }
+  if (!with_norm) return;
+  double t[1];
+  if (reduce_last<1>(v, ra.partials, ra.counter, t) && threadIdx.x == 0)
+    epilogue<1>(EPI_GM_NORM, t, ra.ks, ra.hist, ra.tol, 0, j);
+}
+
+// GMRES: back substitution H(0:k,0:k) y = g (one thread)
+__global__ void k_gm_solve(KState* ks) {
+  if (ks->done || threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = ks->k, m = ks->m;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = ks->gv[i];
+    for (int l = i + 1; l < k; ++l) s -= ks->H[i + (size_t)l * (m + 1)] * ks->y[l];
+    ks->y[i] = s / ks->H[i + (size_t)i * (m + 1)];
+  }
+}
+
+// GMRES: x += S sum_{i<k} y_i V_i
+template <typename T>
+__global__ void k_gm_update(long long len, long long ncplx, cpx<T>* __restrict__ x, const cpx<T>* __restrict__ V,
+                            const T* __restrict__ sym, const KState* ks) {
+  if (ks->done) return;
+  const int k = ks->k;
+  GRID_STRIDE(e, len) {
+    double ax = 0.0, ay = 0.0;
+    for (int i = 0; i < k; ++i) {
+      const cpx<double> vv = ld(V + (size_t)i * len, e);
+      ax = fma(ks->y[i], vv.x, ax);
+      ay = fma(ks->y[i], vv.y, ay);
+    }
+    const double s = (double)sym[e % ncplx];
+    const cpx<double> xv = ld(x, e);
+    x[e] = mk<T>((T)fma(s, ax, xv.x), (T)fma(s, ay, xv.y));
+  }
+}
+
+// GMRES end of cycle: converged inside the cycle -> finished
+__global__ void k_gm_close(KState* ks) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || ks->done) return;
+  if (ks->status == 0 || ks->status == VD_ERR_NONFINITE) ks->done = 1;
+}
+
+// ---------------------------------------------------------------------------------------
+// small vector helpers
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_copy_scale(long long len, const cpx<T>* __restrict__ x, double s, cpx<T>* __restrict__ y) {
+  GRID_STRIDE(e, len) {
+    const cpx<double> v = ld(x, e);
+    y[e] = mk<T>((T)(v.x * s), (T)(v.y * s));
+  }
+}
+template <typename T>
+__global__ void k_axpy(long long len, double a, const cpx<T>* __restrict__ x, cpx<T>* __restrict__ y) {
+  GRID_STRIDE(e, len) {
+    const cpx<double> v = ld(x, e), w = ld(y, e);
+    y[e] = mk<T>((T)fma(a, v.x, w.x), (T)fma(a, v.y, w.y));
+  }
+}
+template <typename T>
+__global__ void k_sub(long long len, const cpx<T>* __restrict__ b, const cpx<T>* __restrict__ q,
+                      cpx<T>* __restrict__ r, const int* done) {
+  if (done && *done) return;
+  GRID_STRIDE(e, len) { r[e] = b[e] - q[e]; }
+}
+__global__ void k_d2f(long long len, const cpx<double>* __restrict__ in, cpx<float>* __restrict__ out) {
+  GRID_STRIDE(e, len) { out[e] = mk<float>((float)in[e].x, (float)in[e].y); }
+}
+__global__ void k_f2d(long long len, const cpx<float>* __restrict__ in, cpx<double>* __restrict__ out) {
+  GRID_STRIDE(e, len) { out[e] = mk<double>((double)in[e].x, (double)in[e].y); }
+}
+template <typename T>
+__global__ void k_project(GridDesc g, int ncomp, cpx<T>* v) {
+  const int t = threadIdx.x;   // one thread per corner mode and component
+  const int d = g.ndim;
+  const int ncorner = 1 << d;
+  if (t >= ncorner * ncomp) return;
+  const int c = t / ncorner, m = t % ncorner;
+  const int kx = (m & 1) ? g.n0 / 2 : 0;
+  const int ky = (d >= 2 && (m & 2)) ? g.n1 / 2 : 0;
+  const int kz = (d >= 3 && (m & 4)) ? g.n2 / 2 : 0;
+  const long long e = ((long long)kz * g.n1 + ky) * g.h0 + kx;
+  v[(long long)c * g.ncplx + e] = mk<T>(T(0), T(0));
+}
+
+static inline int ew_blocks(long long len) {
+  return (int)std::max<long long>(1, std::min<long long>((len + 255) / 256, 8 * 1024));
+}
+
+template <typename T>
+void spec_copy_scale(long long len, const void* x, double s, void* y, cudaStream_t st) {
+  k_copy_scale<T><<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<T>*)x, s, (cpx<T>*)y);
+}
+template <typename T>
+void spec_axpy(long long len, double a, const void* x, void* y, cudaStream_t st) {
+  k_axpy<T><<<ew_blocks(len), 256, 0, st>>>(len, a, (const cpx<T>*)x, (cpx<T>*)y);
+}
+template <typename T>
+void spec_sub(long long len, const void* b, const void* q, void* r, cudaStream_t st) {
+  k_sub<T><<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<T>*)b, (const cpx<T>*)q, (cpx<T>*)r, nullptr);
+}
+void spec_d2f(long long len, const void* in, void* out, cudaStream_t st) {
+  k_d2f<<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<double>*)in, (cpx<float>*)out);
+}
+void spec_f2d(long long len, const void* in, void* out, cudaStream_t st) {
+  k_f2d<<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<float>*)in, (cpx<double>*)out);
+}
+template <typename T>
+void spec_project(const vd_grid* G, int ncomp, void* v, cudaStream_t st) {
+  k_project<T><<<1, 32, 0, st>>>(G->g, ncomp, (cpx<T>*)v);
+}
+
+template <typename T>
+double spec_norm2_host(const SpecSystem& sys, const void* v, const KWork& kw, cudaStream_t st) {
+  RedArgs ra{kw.ks, kw.partials, kw.counter, kw.hist, 0.0};
+  k_norms<T, 1><<<red_blocks(sys.len), kRedThreads, 0, st>>>(sys.len, sys.h0, nullptr, (const cpx<T>*)v, EPI_NORM, ra,
+                                                            nullptr);
+  double rr = 0.0;
+  cudaMemcpyAsync(&rr, &kw.ks->rr, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  return rr;
+}
+
+// ---------------------------------------------------------------------------------------
+// host drivers
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+size_t krylov_vec_bytes(const SpecSystem& sys, int solver, int restart) {
+  const size_t v = sizeof(cpx<T>) * (size_t)sys.len;
+  if (solver == VD_SOLVER_CG) return 3 * v;
+  if (solver == VD_SOLVER_RMR) return 2 * v;
+  const int m = restart > 0 ? restart : 30;
+  return (size_t)(m + 2) * v;
+}
+
+struct KHead {   // host mirror of the first fields of KState
+  double bb, tol2bb, rr, rz, pq, alpha, beta, rw, ww, best, relres;
+  int iters, maxit, status, done, hist_cap, m, k, cycle_done, pad;
+};
+static_assert(offsetof(KState, bb) == 0, "layout");
+
+static vd_status read_head(const KWork& kw, KHead* h, cudaStream_t st) {
+  VD_CUDA(cudaMemcpyAsync(h, kw.ks, sizeof(KHead), cudaMemcpyDeviceToHost, st));
+  VD_CUDA(cudaStreamSynchronize(st));
+  return VD_OK;
+}
+
+template <typename T>
+vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b, void* x, void* vecs,
+                       const KWork& kw, double* host_hist, int host_hist_cap, SolveOut* out, cudaStream_t st) {
+  const long long len = sys.len;
+  const long long nc = sys.G->g.ncplx;
+  const int h0 = sys.h0;
+  const T* sym = (const T*)sys.sym;
+  const int rb = red_blocks(len);
+  const int eb = ew_blocks(len);
+  RedArgs ra{kw.ks, kw.partials, kw.counter, kw.hist, o.tol};
+  int* done = &kw.ks->done;
+  int* cdone = &kw.ks->cycle_done;
+  const int m = std::min(std::max(o.restart > 0 ? o.restart : 30, 1), kMaxRestart);
+  const int check = std::max(1, o.check_every);
+
+  // reset the scalar state
+  KHead h0s;
+  std::memset(&h0s, 0, sizeof(h0s));
+  h0s.maxit = o.maxit;
+  h0s.status = KS_RUNNING;
+  h0s.hist_cap = host_hist_cap > 0 ? std::min(host_hist_cap, 1 << 20) : 0;
+  h0s.m = m;
+  VD_CUDA(cudaMemcpyAsync(kw.ks, &h0s, sizeof(KHead), cudaMemcpyHostToDevice, st));
+  VD_CUDA(cudaMemsetAsync(kw.counter, 0, sizeof(unsigned), st));
+
+  cpx<T>* X = (cpx<T>*)x;
+  const cpx<T>* B = (const cpx<T>*)b;
+  cpx<T>* vb = (cpx<T>*)vecs;
+  KHead hd;
+
+  if (o.solver == VD_SOLVER_CG) {
+    cpx<T>* r = vb;
+    cpx<T>* p = vb + len;
+    cpx<T>* q = vb + 2 * len;
+    sys.apply(sys, X, q, false, nullptr, st);
+    k_sub<T><<<eb, 256, 0, st>>>(len, B, q, r, nullptr);
+    k_cg_init<T><<<rb, kRedThreads, 0, st>>>(len, h0, nc, B, r, p, sym, ra);
+    int it = 0;
+    for (;;) {
+      for (int c = 0; c < check && it < o.maxit; ++c, ++it) {
+        sys.apply(sys, p, q, false, done, st);
+        k_dot<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, p, q, EPI_CG_ALPHA, ra, done);
+        k_cg_update<T><<<rb, kRedThreads, 0, st>>>(len, h0, nc, X, p, r, q, sym, ra);
+        k_cg_p<T><<<eb, 256, 0, st>>>(len, nc, p, r, sym, kw.ks);
+      }
+      vd_status e = read_head(kw, &hd, st);
+      if (e != VD_OK) return e;
+      if (hd.done || it >= o.maxit) break;
+    }
+  } else if (o.solver == VD_SOLVER_RMR) {
+    cpx<T>* r = vb;
+    cpx<T>* w = vb + len;
+    sys.apply(sys, X, w, false, nullptr, st);
+    k_sub<T><<<eb, 256, 0, st>>>(len, B, w, r, nullptr);
+    k_norms<T, 2><<<rb, kRedThreads, 0, st>>>(len, h0, B, r, EPI_INIT_RMR, ra, nullptr);
+    int it = 0;
+    for (;;) {
+      for (int c = 0; c < check && it < o.maxit; ++c, ++it) {
+        sys.apply(sys, r, w, true, done, st);
+        k_dot<T, 2><<<rb, kRedThreads, 0, st>>>(len, h0, r, w, EPI_RMR_ALPHA, ra, done);
+        k_rmr_update<T><<<rb, kRedThreads, 0, st>>>(len, h0, nc, X, r, w, sym, ra);
+      }
+      vd_status e = read_head(kw, &hd, st);
+      if (e != VD_OK) return e;
+      if (hd.done || it >= o.maxit) break;
+    }
+  } else {
+    cpx<T>* V = vb;
+    cpx<T>* w = vb + (size_t)(m + 1) * len;
+    k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, nullptr, B, EPI_BB, ra, nullptr);
+    for (int cycle = 0;; ++cycle) {
+      // r = b - A x into V_0 (unnormalised), then V_0 /= beta
+      sys.apply(sys, X, w, false, done, st);
+      k_sub<T><<<eb, 256, 0, st>>>(len, B, w, V, done);
+      k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, nullptr, V, EPI_GM_BETA, ra, done);
+      k_gm_scale<T><<<eb, 256, 0, st>>>(len, V, V, kw.ks, 1);
+      for (int j = 0; j < m; ++j) {
+        cpx<T>* Vj = V + (size_t)j * len;
+        sys.apply(sys, Vj, w, true, cdone, st);
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int off = 0; off <= j; off += 8) {
+            const int nv = std::min(8, j + 1 - off);
+            k_gm_mdot<T><<<rb, kRedThreads, 0, st>>>(len, h0, w, V, off, nv, pass ? EPI_GM_H2 : EPI_GM_H1, j, ra);
+          }
+          k_gm_maxpy<T><<<rb, kRedThreads, 0, st>>>(len, h0, w, V, j, pass, pass, ra);
+        }
+        k_gm_scale<T><<<eb, 256, 0, st>>>(len, V + (size_t)(j + 1) * len, w, kw.ks, 0);
+        if ((j + 1) % check == 0 || j + 1 == m) {
+          vd_status e = read_head(kw, &hd, st);
+          if (e != VD_OK) return e;
+          if (hd.cycle_done || hd.done) break;
+        }
+      }
+      k_gm_solve<<<1, 1, 0, st>>>(kw.ks);
+      k_gm_update<T><<<eb, 256, 0, st>>>(len, nc, X, V, sym, kw.ks);
+      k_gm_close<<<1, 1, 0, st>>>(kw.ks);
+      vd_status e = read_head(kw, &hd, st);
+      if (e != VD_OK) return e;
+      if (hd.done) break;
+      if (hd.iters >= o.maxit) {
+        // one more loop head forms the true residual and sets the final status
+        sys.apply(sys, X, w, false, done, st);
+        k_sub<T><<<eb, 256, 0, st>>>(len, B, w, V, done);
+        k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, nullptr, V, EPI_GM_BETA, ra, done);
+        e = read_head(kw, &hd, st);
+        if (e != VD_OK) return e;
+        break;
+      }
+    }
+  }
+  VD_CUDA(cudaGetLastError());
+  vd_status e = read_head(kw, &hd, st);
+  if (e != VD_OK) return e;
+  if (!hd.done) hd.status = VD_ERR_NOT_CONVERGED;
+  out->iters = hd.iters;
+  out->status = hd.status < 0 ? VD_ERR_NOT_CONVERGED : hd.status;
+  out->relres = hd.relres;
+  if (host_hist && h0s.hist_cap > 0) {
+    const int nh = std::min(h0s.hist_cap, hd.iters + 1);
+    VD_CUDA(cudaMemcpyAsync(host_hist, kw.hist, sizeof(double) * nh, cudaMemcpyDeviceToHost, st));
+    VD_CUDA(cudaStreamSynchronize(st));
+  }
+  return VD_OK;
+}
+
+template vd_status krylov_solve<double>(const SpecSystem&, const SolveOpts&, const void*, void*, void*, const KWork&,
+                                        double*, int, SolveOut*, cudaStream_t);
+template vd_status krylov_solve<float>(const SpecSystem&, const SolveOpts&, const void*, void*, void*, const KWork&,
+                                       double*, int, SolveOut*, cudaStream_t);
+template size_t krylov_vec_bytes<double>(const SpecSystem&, int, int);
+template size_t krylov_vec_bytes<float>(const SpecSystem&, int, int);
+template void spec_copy_scale<double>(long long, const void*, double, void*, cudaStream_t);
+template void spec_copy_scale<float>(long long, const void*, double, void*, cudaStream_t);
+template void spec_axpy<double>(long long, double, const void*, void*, cudaStream_t);
+template void spec_axpy<float>(long long, double, const void*, void*, cudaStream_t);
+template void spec_sub<double>(long long, const void*, const void*, void*, cudaStream_t);
+template void spec_sub<float>(long long, const void*, const void*, void*, cudaStream_t);
+template void spec_project<double>(const vd_grid*, int, void*, cudaStream_t);
+template void spec_project<float>(const vd_grid*, int, void*, cudaStream_t);
+template double spec_norm2_host<double>(const SpecSystem&, const void*, const KWork&, cudaStream_t);
+template double spec_norm2_host<float>(const SpecSystem&, const void*, const KWork&, cudaStream_t);
+
+}  // namespace vd

@@ -1,0 +1,105 @@
+// Krylov solvers in spectral space (device scalar state, host-driven iteration loop).
+//
+// The unknowns live in the half-spectrum representation: a real field is stored as its
+// coefficients cpx[n2][n1][n0/2+1] (times ncomp components).  By Parseval the Euclidean
+// inner product of two real fields is proportional to sum_k w(kx) Re(u_k conj(v_k)) with
+// w = 1 on the kx = 0 and kx = n0/2 planes and w = 2 elsewhere, so CG, GMRES and RMR run on
+// the spectral coefficients with that weighted inner product and produce the same iterates
+// as on the physical grid.  The preconditioners are diagonal there (a symbol array).
+#pragma once
+
+#include "vd_internal.h"
+
+namespace vd {
+
+constexpr int kMaxRestart = 64;
+constexpr int kRedBlocks = 512;   // fixed block count of every reduction (deterministic)
+constexpr int kRedThreads = 256;
+
+// device-resident scalar state of one solve
+struct KState {
+  double bb;       // ||b||^2
+  double tol2bb;   // tol^2 ||b||^2
+  double rr, rz, pq, alpha, beta, rw, ww;
+  double best;     // best monitored relres so far
+  double relres;
+  int iters, maxit, status, done;
+  int hist_cap;
+  // GMRES
+  int m, k, cycle_done, pad;
+  double beta0;
+  double H[(kMaxRestart + 1) * kMaxRestart];   // column-major: H[i + j*(m+1)]
+  double cs[kMaxRestart], sn[kMaxRestart], gv[kMaxRestart + 1], y[kMaxRestart];
+  double h1[kMaxRestart + 1], h2[kMaxRestart + 1];
+};
+
+struct KWork {
+  KState* ks;
+  double* partials;     // kRedBlocks * 8
+  unsigned* counter;
+  double* hist;         // hist_cap entries
+};
+
+// status codes stored in KState::status (mirror vd_status)
+enum KStatus { KS_RUNNING = -1 };
+
+struct Vec {
+  void* p;        // cpx<T>*
+  long long len;  // complex elements (ncomp * ncplx)
+};
+
+// Solve in spectral space.  Operator callbacks apply A (optionally right-preconditioned:
+// with_sym = true means A S) on the stream.
+struct SpecSystem {
+  const vd_grid* G;
+  int ncomp;
+  long long len;            // ncomp * ncplx
+  int h0;
+  const void* sym;          // symbol array of the preconditioner (ncplx, type T)
+  int is_float;             // vectors and transforms in float
+  void (*apply)(const SpecSystem& sys, const void* in, void* out, bool with_sym, const int* done, cudaStream_t st);
+  void* ctx[4];             // opaque per-operator data (rinv, tmp, params)
+  double a, inv_sc;
+};
+
+struct SolveOpts {
+  int solver;  // vd_solver
+  double tol;
+  int maxit;
+  int restart;
+  int check_every;
+};
+
+struct SolveOut {
+  int iters;
+  int status;
+  double relres;
+};
+
+// x (in/out), b: spectral vectors of sys.len complex elements of type T.
+// Workspace vectors: CG needs r,p,q (3 len); RMR r,w (2 len); GMRES V ((m+1) len) + w.
+template <typename T>
+vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b, void* x, void* vecs,
+                       const KWork& kw, double* host_hist, int host_hist_cap, SolveOut* out, cudaStream_t st);
+
+template <typename T>
+size_t krylov_vec_bytes(const SpecSystem& sys, int solver, int restart);
+
+// helpers shared with the API layer
+template <typename T>
+void spec_copy_scale(long long len, const void* x, double s, void* y, cudaStream_t st);   // y = s x
+template <typename T>
+void spec_axpy(long long len, double a, const void* x, void* y, cudaStream_t st);         // y += a x
+template <typename T>
+void spec_sub(long long len, const void* b, const void* q, void* r, cudaStream_t st);     // r = b - q
+// weighted norm^2 of a spectral vector -> host (synchronises)
+template <typename T>
+double spec_norm2_host(const SpecSystem& sys, const void* v, const KWork& kw, cudaStream_t st);
+// zero the 2^d null-space coefficients of each component
+template <typename T>
+void spec_project(const vd_grid* G, int ncomp, void* v, cudaStream_t st);
+// precision conversions of spectral vectors
+void spec_d2f(long long len, const void* in, void* out, cudaStream_t st);
+void spec_f2d(long long len, const void* in, void* out, cudaStream_t st);
+
+}  // namespace vd

@@ -1,0 +1,429 @@
+// Operator pipelines built from the transform passes.
+//
+// Pressure operator (Eq. VDINSE.Lrho.num), spectral in -> spectral out:
+//   L~ psi = sum_j i k~_j F[ rho^-1 F^-1( i k~_j psi ) ]
+// Velocity operator (Eq. VDINSE.zeta with the Crank--Nicolson factor a = dt/(2 Re)):
+//   V~ u = u - a F[ rho^-1 ( Lap u + Sc^-1 ( (u.grad) grad rho + (grad rho.grad) u ) ) ]
+#include "vd_internal.h"
+#include "vd_fft.cuh"
+
+#include <algorithm>
+
+namespace vd {
+
+static inline Xf mkxf(int src, int dst, int pre, int post, bool first, bool last, double scale = 1.0,
+                      bool nofft = false) {
+  Xf x;
+  x.src = (int8_t)src;
+  x.dst = (int8_t)dst;
+  x.pre = (int8_t)pre;
+  x.post = (int8_t)post;
+  x.first = first ? 1 : 0;
+  x.last = last ? 1 : 0;
+  x.nofft = nofft ? 1 : 0;
+  x.pad = 0;
+  x.scale = scale;
+  return x;
+}
+
+template <typename T>
+static const void* twtab(const vd_grid* G) {
+  return (sizeof(T) == 8) ? G->tw_d : G->tw_f;
+}
+
+int pressure_tmp_fields(int ndim) { return ndim == 3 ? 3 : (ndim == 2 ? 2 : 0); }
+int velocity_tmp_fields(int ndim) { return 1 + ndim * ndim + 2 * ndim; }
+
+// ---------------------------------------------------------------------------------------
+// plain transforms
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+void fwd_transform(const vd_grid* G, const T* in, cpx<T>* out, cudaStream_t st) {
+  const GridDesc& g = G->g;
+  XProg X{};
+  X.ncomp = 1;
+  X.mode = 1;
+  X.in[0] = in;
+  X.out[0] = out;
+  X.scale = 0.5;
+  launch_xpass<T>(X, g, twtab<T>(G), st);
+  if (g.ndim >= 2) {
+    AxisProg P{};
+    P.nxf = 1;
+    P.xf[0] = mkxf(0, 0, 0, 0, true, true);
+    P.in[0] = out;
+    P.out[0] = out;
+    P.axis = 1;
+    launch_axis<T>(P, -1, g, twtab<T>(G), st);
+    if (g.ndim == 3) {
+      P.axis = 2;
+      launch_axis<T>(P, -1, g, twtab<T>(G), st);
+    }
+  }
+}
+
+template <typename T>
+void inv_transform(const vd_grid* G, const cpx<T>* in, const Mult& mu, T* out, cpx<T>* tmp, cudaStream_t st) {
+  const GridDesc& g = G->g;
+  auto dflag = [](int d) { return d == 1 ? MUL_IK : (d == 2 ? MUL_IK2 : 0); };
+  const int allk = (mu.sym ? MUL_SYM : 0) | (mu.negk2 ? MUL_NEGK2 : 0);
+  const cpx<T>* cur = in;
+  int pending = allk;   // multipliers that need every axis spectral: applied in the first pass
+  double scale = mu.scale;
+  if (g.ndim == 3) {
+    AxisProg P{};
+    P.nxf = 1;
+    P.xf[0] = mkxf(0, 0, dflag(mu.deriv[2]) | pending, 0, true, true, scale);
+    P.in[0] = cur;
+    P.out[0] = tmp;
+    P.symarr = mu.symarr;
+    P.axis = 2;
+    launch_axis<T>(P, +1, g, twtab<T>(G), st);
+    cur = tmp;
+    pending = 0;
+    scale = 1.0;
+  }
+  if (g.ndim >= 2) {
+    AxisProg P{};
+    P.nxf = 1;
+    P.xf[0] = mkxf(0, 0, dflag(mu.deriv[1]) | pending, 0, true, true, scale);
+    P.in[0] = cur;
+    P.out[0] = tmp;
+    P.symarr = mu.symarr;
+    P.axis = 1;
+    launch_axis<T>(P, +1, g, twtab<T>(G), st);
+    cur = tmp;
+    pending = 0;
+    scale = 1.0;
+  }
+  XProg X{};
+  X.ncomp = 1;
+  X.mode = 2;
+  X.in[0] = cur;
+  X.out[0] = out;
+  X.pre[0] = dflag(mu.deriv[0]) | pending;
+  X.symarr = mu.symarr;
+  X.scale = scale / (double)g.nreal;
+  launch_xpass<T>(X, g, twtab<T>(G), st);
+}
+
+// ---------------------------------------------------------------------------------------
+// pressure operator
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, const T* rinv_s,
+                         cpx<T>* tmp, const int* done, cudaStream_t st) {
+  const GridDesc& g = G->g;
+  const int S = symarr ? MUL_SYM : 0;
+  const size_t nc = (size_t)g.ncplx;
+  const void* tw = twtab<T>(G);
+  if (g.ndim == 1) {
+    XProg X{};
+    X.ncomp = 1;
+    X.mode = 0;
+    X.in[0] = in;
+    X.out[0] = out;
+    X.pre[0] = S | MUL_IK;
+    X.post[0] = MUL_IK;
+    X.wfield = rinv_s;
+    X.scale = 0.5;
+    X.symarr = symarr;
+    X.done = done;
+    launch_xpass<T>(X, g, tw, st);
+    return;
+  }
+  cpx<T>* T0 = tmp;
+  cpx<T>* T1 = tmp + nc;
+  if (g.ndim == 2) {
+    // y inverse: T1 = F_y^-1(i ky S v), T0 = F_y^-1(S v)
+    AxisProg P{};
+    P.nxf = 2;
+    P.xf[0] = mkxf(0, 1, S | MUL_IK, 0, true, true);
+    P.xf[1] = mkxf(0, 0, S, 0, true, true);
+    P.in[0] = in;
+    P.out[0] = T0;
+    P.out[1] = T1;
+    P.symarr = symarr;
+    P.done = done;
+    P.axis = 1;
+    launch_axis<T>(P, +1, g, tw, st);
+    // x fused: T0 <- i kx R2C(w C2R(i kx T0)), T1 <- R2C(w C2R(T1))
+    XProg X{};
+    X.ncomp = 2;
+    X.mode = 0;
+    X.in[0] = T0;
+    X.out[0] = T0;
+    X.pre[0] = MUL_IK;
+    X.post[0] = MUL_IK;
+    X.in[1] = T1;
+    X.out[1] = T1;
+    X.wfield = rinv_s;
+    X.scale = 0.5;
+    X.done = done;
+    launch_xpass<T>(X, g, tw, st);
+    // y forward + divergence: out = F_y(T0) + i ky F_y(T1)
+    AxisProg Q{};
+    Q.nxf = 2;
+    Q.xf[0] = mkxf(0, 0, 0, 0, true, false);
+    Q.xf[1] = mkxf(1, 0, 0, MUL_IK, false, true);
+    Q.in[0] = T0;
+    Q.in[1] = T1;
+    Q.out[0] = out;
+    Q.done = done;
+    Q.axis = 1;
+    launch_axis<T>(Q, -1, g, tw, st);
+    return;
+  }
+  cpx<T>* T2 = tmp + 2 * nc;
+  // P1, z inverse: T0 = F_z^-1(S v), T1 = F_z^-1(i kz S v)
+  {
+    AxisProg P{};
+    P.nxf = 2;
+    P.xf[0] = mkxf(0, 1, S | MUL_IK, 0, true, true);
+    P.xf[1] = mkxf(0, 0, S, 0, true, true);
+    P.in[0] = in;
+    P.out[0] = T0;
+    P.out[1] = T1;
+    P.symarr = symarr;
+    P.done = done;
+    P.axis = 2;
+    launch_axis<T>(P, +1, g, tw, st);
+  }
+  // P2, y inverse: T2 = F_y^-1(i ky T0), T0 <- F_y^-1(T0), T1 <- F_y^-1(T1)
+  {
+    AxisProg P{};
+    P.nxf = 3;
+    P.xf[0] = mkxf(0, 2, MUL_IK, 0, true, true);
+    P.xf[1] = mkxf(0, 0, 0, 0, true, true);
+    P.xf[2] = mkxf(1, 1, 0, 0, true, true);
+    P.in[0] = T0;
+    P.in[1] = T1;
+    P.out[0] = T0;
+    P.out[1] = T1;
+    P.out[2] = T2;
+    P.done = done;
+    P.axis = 1;
+    launch_axis<T>(P, +1, g, tw, st);
+  }
+  // P3, x fused (in place): T0 <- i kx R2C(w C2R(i kx T0)), T2 <- R2C(w C2R(T2)), T1 likewise
+  {
+    XProg X{};
+    X.ncomp = 3;
+    X.mode = 0;
+    X.in[0] = T0;
+    X.out[0] = T0;
+    X.pre[0] = MUL_IK;
+    X.post[0] = MUL_IK;
+    X.in[1] = T2;
+    X.out[1] = T2;
+    X.in[2] = T1;
+    X.out[2] = T1;
+    X.wfield = rinv_s;
+    X.scale = 0.5;
+    X.done = done;
+    launch_xpass<T>(X, g, tw, st);
+  }
+  // P4, y forward: T0 <- F_y(T0) + i ky F_y(T2), T1 <- F_y(T1)
+  {
+    AxisProg P{};
+    P.nxf = 3;
+    P.xf[0] = mkxf(0, 0, 0, 0, true, false);
+    P.xf[1] = mkxf(1, 0, 0, MUL_IK, false, true);
+    P.xf[2] = mkxf(2, 1, 0, 0, true, true);
+    P.in[0] = T0;
+    P.in[1] = T2;
+    P.in[2] = T1;
+    P.out[0] = T0;
+    P.out[1] = T1;
+    P.done = done;
+    P.axis = 1;
+    launch_axis<T>(P, -1, g, tw, st);
+  }
+  // P5, z forward + divergence: out = F_z(T0) + i kz F_z(T1)
+  {
+    AxisProg P{};
+    P.nxf = 2;
+    P.xf[0] = mkxf(0, 0, 0, 0, true, false);
+    P.xf[1] = mkxf(1, 0, 0, MUL_IK, false, true);
+    P.in[0] = T0;
+    P.in[1] = T1;
+    P.out[0] = out;
+    P.done = done;
+    P.axis = 2;
+    launch_axis<T>(P, -1, g, tw, st);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// velocity operator
+// ---------------------------------------------------------------------------------------
+
+void spec_axpby_sym_launch(const vd_grid* G, int sz, const void* x, const void* symarr, double alpha, const void* y,
+                           double beta, void* out, const int* done, cudaStream_t st);
+void velocity_combine_launch(const vd_grid* G, int sz, const void* u, const void* du, void* lap, double inv_sc,
+                             const int* done, cudaStream_t st);
+
+template <typename T>
+void apply_velocity_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, double a,
+                         double inv_sc, cpx<T>* tmp, const int* done, cudaStream_t st) {
+  const GridDesc& g = G->g;
+  const int d = g.ndim;
+  const size_t nc = (size_t)g.ncplx;
+  const size_t nr = (size_t)g.nreal;
+  // physical scratch carved from spectral-sized temporaries (a spectral field holds >= nreal reals)
+  cpx<T>* ttmp = tmp;                                      // 1 field: transform scratch
+  T* u = reinterpret_cast<T*>(tmp + nc);                   // d fields
+  T* du = reinterpret_cast<T*>(tmp + nc * (1 + d));        // d*d fields
+  T* lap = reinterpret_cast<T*>(tmp + nc * (1 + d + d * d));  // d fields
+  static_assert(sizeof(cpx<T>) == 2 * sizeof(T), "layout");
+  // u = F^-1(S in_i), du_ij = F^-1(i k_j S in_i), lap_i = F^-1(-|k|^2 S in_i)
+  for (int i = 0; i < d; ++i) {
+    const cpx<T>* vi = in + i * nc;
+    Mult m;
+    m.sym = symarr ? 1 : 0;
+    m.symarr = symarr;
+    inv_transform<T>(G, vi, m, u + i * nr, ttmp, st);
+    for (int j = 0; j < d; ++j) {
+      Mult mj = m;
+      mj.deriv[j] = 1;
+      inv_transform<T>(G, vi, mj, du + (i * d + j) * nr, ttmp, st);
+    }
+    Mult ml = m;
+    ml.negk2 = 1;
+    inv_transform<T>(G, vi, ml, lap + i * nr, ttmp, st);
+  }
+  // pointwise bracket g_i = rho^-1 (lap_i + Sc^-1 sum_j (u_j D_j D_i rho + D_j rho D_j u_i)),
+  // written over lap_i
+  velocity_combine_launch(G, (int)sizeof(T), u, du, lap, inv_sc, done, st);
+  // out_i = S in_i - a F(g_i)
+  for (int i = 0; i < d; ++i) {
+    fwd_transform<T>(G, lap + i * nr, ttmp, st);
+    // out_i = S in_i - a ttmp  (diagonal combine in spectral space)
+    spec_axpby_sym_launch(G, (int)sizeof(T), in + i * nc, symarr, 1.0, ttmp, -a, out + i * nc, done, st);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// small pointwise kernels used above
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_spec_axpby_sym(long long n, const cpx<T>* __restrict__ x, const T* __restrict__ sym, T alpha,
+                                 const cpx<T>* __restrict__ y, T beta, cpx<T>* __restrict__ out, const int* done) {
+  if (done && *done) return;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const T s = sym ? sym[e] * alpha : alpha;
+    out[e] = scal(x[e], s) + scal(y[e], beta);
+  }
+}
+
+void spec_axpby_sym_launch(const vd_grid* G, int sz, const void* x, const void* symarr, double alpha, const void* y,
+                           double beta, void* out, const int* done, cudaStream_t st) {
+  const long long n = G->g.ncplx;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+  if (sz == 8)
+    k_spec_axpby_sym<double><<<blocks, 256, 0, st>>>(n, (const cpx<double>*)x, (const double*)symarr, alpha,
+                                                     (const cpx<double>*)y, beta, (cpx<double>*)out, done);
+  else
+    k_spec_axpby_sym<float><<<blocks, 256, 0, st>>>(n, (const cpx<float>*)x, (const float*)symarr, (float)alpha,
+                                                    (const cpx<float>*)y, (float)beta, (cpx<float>*)out, done);
+}
+
+struct DensPtrs {
+  const double* g[3];
+  const double* h[6];
+};
+
+template <typename T>
+__global__ void k_vel_combine(int d, long long nreal, const T* __restrict__ u, const T* __restrict__ du,
+                              T* __restrict__ lap, const double* __restrict__ rho, DensPtrs dp, double inv_sc,
+                              const int* done) {
+  if (done && *done) return;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nreal;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double rinv = 1.0 / rho[e];
+    T out[3];
+    for (int i = 0; i < d; ++i) {
+      double t = 0.0;
+      for (int j = 0; j < d; ++j) {
+        const int a = i < j ? i : j, b = i < j ? j : i;
+        const int hi = (a == 0) ? b : (a == 1 ? 2 + b : 5);
+        t += (double)u[j * nreal + e] * dp.h[hi][e] + dp.g[j][e] * (double)du[(i * d + j) * nreal + e];
+      }
+      out[i] = (T)(rinv * ((double)lap[i * nreal + e] + inv_sc * t));
+    }
+    for (int i = 0; i < d; ++i) lap[i * nreal + e] = out[i];
+  }
+}
+
+void velocity_combine_launch(const vd_grid* G, int sz, const void* u, const void* du, void* lap, double inv_sc,
+                             const int* done, cudaStream_t st) {
+  const long long n = G->g.nreal;
+  DensPtrs dp;
+  for (int j = 0; j < 3; ++j) dp.g[j] = G->grho[j];
+  for (int j = 0; j < 6; ++j) dp.h[j] = G->hrho[j];
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+  if (sz == 8)
+    k_vel_combine<double><<<blocks, 256, 0, st>>>(G->g.ndim, n, (const double*)u, (const double*)du, (double*)lap,
+                                                  G->rho, dp, inv_sc, done);
+  else
+    k_vel_combine<float><<<blocks, 256, 0, st>>>(G->g.ndim, n, (const float*)u, (const float*)du, (float*)lap,
+                                                 G->rho, dp, inv_sc, done);
+}
+
+// ---------------------------------------------------------------------------------------
+// symbol arrays
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_fill_symbol(GridDesc g, int kind, double a, T* __restrict__ out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < g.ncplx;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long line = e / g.h0;
+    const int kxi = (int)(e - line * g.h0);
+    const int kyi = (int)(line % g.n1);
+    const int kzi = (int)(line / g.n1);
+    const double kx = g.kfac[0] * freq_tilde(kxi, g.n0);
+    double k2 = kx * kx;
+    if (g.ndim >= 2) {
+      const double ky = g.kfac[1] * freq_tilde(kyi, g.n1);
+      k2 += ky * ky;
+    }
+    if (g.ndim == 3) {
+      const double kz = g.kfac[2] * freq_tilde(kzi, g.n2);
+      k2 += kz * kz;
+    }
+    double v = 1.0;
+    if (kind == SYM_PRESSURE) v = (k2 == 0.0) ? 0.0 : -1.0 / k2;
+    else if (kind == SYM_VELOCITY) v = 1.0 / (1.0 + a * k2);
+    else if (kind == SYM_PROJECT) v = (k2 == 0.0) ? 0.0 : 1.0;
+    out[e] = (T)v;
+  }
+}
+
+template <typename T>
+void fill_symbol(const vd_grid* G, int kind, double a, T* out, cudaStream_t st) {
+  const long long n = G->g.ncplx;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+  k_fill_symbol<T><<<blocks, 256, 0, st>>>(G->g, kind, a, out);
+}
+
+template void fwd_transform<double>(const vd_grid*, const double*, cpx<double>*, cudaStream_t);
+template void fwd_transform<float>(const vd_grid*, const float*, cpx<float>*, cudaStream_t);
+template void inv_transform<double>(const vd_grid*, const cpx<double>*, const Mult&, double*, cpx<double>*,
+                                    cudaStream_t);
+template void inv_transform<float>(const vd_grid*, const cpx<float>*, const Mult&, float*, cpx<float>*, cudaStream_t);
+template void apply_pressure_spec<double>(const vd_grid*, const cpx<double>*, cpx<double>*, const double*,
+                                          const double*, cpx<double>*, const int*, cudaStream_t);
+template void apply_pressure_spec<float>(const vd_grid*, const cpx<float>*, cpx<float>*, const float*, const float*,
+                                         cpx<float>*, const int*, cudaStream_t);
+template void apply_velocity_spec<double>(const vd_grid*, const cpx<double>*, cpx<double>*, const double*, double,
+                                          double, cpx<double>*, const int*, cudaStream_t);
+template void apply_velocity_spec<float>(const vd_grid*, const cpx<float>*, cpx<float>*, const float*, double,
+                                         double, cpx<float>*, const int*, cudaStream_t);
+template void fill_symbol<double>(const vd_grid*, int, double, double*, cudaStream_t);
+template void fill_symbol<float>(const vd_grid*, int, double, float*, cudaStream_t);
+
+}  // namespace vd

@@ -1,0 +1,78 @@
+// Transform passes of the spectral operators (host-side declarations).
+//
+// A 3D operator apply in spectral space is a chain of passes, each reading and writing
+// half-spectrum fields in HBM once:
+//   z pass (lines along z) -> y pass (lines along y) -> fused x pass (inverse real
+//   transform, pointwise physical-space work, forward real transform) -> y pass -> z pass.
+// 2D chains drop the z passes and 1D chains are a single fused x pass.  Multipliers that
+// are diagonal in Fourier space (derivatives i k~_j, -|k~|^2, preconditioner symbols)
+// are applied while a pass loads or stores, so they cost no extra memory traffic.
+#pragma once
+
+#include "vd_common.cuh"
+
+namespace vd {
+
+// pre/post multiplier flags (combinable)
+enum MulFlags : int {
+  MUL_IK = 1,      // i k~ of the pass axis
+  MUL_SYM = 2,     // the program's diagonal symbol (needs every axis in spectral space)
+  MUL_NEGK2 = 4,   // -|k~|^2 (needs every axis in spectral space)
+  MUL_IK2 = 8,     // (i k~)^2 = -k~^2 of the pass axis
+};
+
+constexpr int kMaxXf = 16;
+constexpr int kMaxIO = 16;
+
+// One transform of an axis pass: out[dst] (=|+=) scale * post( FFT( pre( in[src] ) ) ).
+// MUL_SYM reads the program's symbol array at the element's spectral index, so it is only
+// meaningful where every axis is in spectral space (first inverse / last forward pass).
+struct Xf {
+  int8_t src, dst, pre, post;
+  int8_t first;   // start a new accumulation for dst
+  int8_t last;    // write dst after this transform
+  int8_t nofft;   // skip the transform (pure diagonal multiply)
+  int8_t pad;
+  double scale;
+};
+
+struct AxisProg {
+  int nxf;
+  Xf xf[kMaxXf];
+  const void* in[kMaxIO];
+  void* out[kMaxIO];
+  const void* symarr;   // real symbol array (ncplx, same layout as the spectral fields)
+  const int* done;      // if non-null and *done != 0 the kernel returns at once
+  int axis;   // 1 = y, 2 = z
+};
+
+// Fused x pass: for every component c, in[c] (half spectrum) -> pre -> inverse real FFT ->
+// multiply by wfield (real, n0 per line; nullptr = 1) -> forward real FFT -> post -> out[c].
+// mode 0: fused as described; mode 1: real in (in[c] is T*), forward only; mode 2: inverse
+// only, real out (out[c] is T*).  scale multiplies the result.
+struct XProg {
+  int ncomp;
+  int mode;
+  const void* in[4];
+  void* out[4];
+  int pre[4];
+  int post[4];
+  const void* wfield;
+  double scale;
+  const void* symarr;
+  const int* done;
+};
+
+template <typename T>
+void launch_axis(const AxisProg& P, int dir, const GridDesc& g, const void* tw, cudaStream_t st);
+
+template <typename T>
+void launch_xpass(const XProg& P, const GridDesc& g, const void* tw, cudaStream_t st);
+
+// shared memory footprint (bytes) of the pass kernels, for the attribute setup
+template <typename T>
+size_t axis_smem_bytes(const GridDesc& g, int axis);
+template <typename T>
+size_t xpass_smem_bytes(const GridDesc& g);
+
+}  // namespace vd

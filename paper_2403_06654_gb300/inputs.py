@@ -76,6 +76,7 @@ def rt_2d(nx=512, nz=1024, Lx=1.0, Lz=2.0, s=3.0, delta=0.02, eta_amp=0.05,
     x, z = coords((nx, nz), (Lx, Lz))
     eta = eta_amp * np.cos(2 * math.pi * x / Lx)
     rho = 1.0 + (s - 1.0) / 2.0 * (np.tanh((z - 0.5) / delta + eta) - np.tanh((z - 1.5) / delta))
+    rho = np.array(np.broadcast_to(rho, (nz, nx)), copy=True)
     rng = np.random.default_rng(seed)
     u = noise * rng.standard_normal((2, nz, nx))
     return RTCase(n=(nx, nz), L=(Lx, Lz), rho=rho, u=u, Re=Re, Sc=Sc, Fr=Fr, dt=dt, gravity_axis=1)
@@ -98,12 +99,12 @@ def jet_3d(n=256, s=0.5, R=0.5, d=0.05, q=1.0, noise=1e-3, seed=3, L=2 * math.pi
     x, y, z = coords((n, n, n), (L, L, L))
     yc, zc = y - L / 2, z - L / 2
     r = np.sqrt(yc ** 2 + zc ** 2)
-    prof = 0.5 * (1.0 - np.tanh((r - R) / d))
-    rho = 1.0 + (s - 1.0) * prof
+    prof = np.broadcast_to(0.5 * (1.0 - np.tanh((r - R) / d)), (n, n, n))
+    rho = np.ascontiguousarray(1.0 + (s - 1.0) * prof)
     rng = np.random.default_rng(seed)
     u = np.empty((3, n, n, n))
     # V_theta e_theta = q r V_x (-sin t, cos t) in the (y, z) plane
-    u[0] = prof + 0 * x
+    u[0] = prof
     u[1] = -q * prof * zc
     u[2] = q * prof * yc
     u += noise * rng.standard_normal(u.shape)
@@ -140,7 +141,8 @@ def slab_density(n, L, s, axis, centre, width, thick):
     xa = X[axis]
     La = L[axis]
     dist = (xa - centre + La / 2) % La - La / 2
-    return 1.0 + (s - 1.0) / 2.0 * (np.tanh((dist + width / 2) / thick) - np.tanh((dist - width / 2) / thick))
+    rho = 1.0 + (s - 1.0) / 2.0 * (np.tanh((dist + width / 2) / thick) - np.tanh((dist - width / 2) / thick))
+    return np.array(np.broadcast_to(rho, tuple(reversed(n))), copy=True)
 
 
 # ---------------------------------------------------------------------------------------
