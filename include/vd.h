@@ -168,6 +168,20 @@ vd_status vd_divergence(const vd_grid* grid, const double* u, double* out, void*
 vd_status vd_gradient(const vd_grid* grid, const double* phi, double* out, void* ws, size_t ws_bytes,
                       vd_stream stream);
 
+/*
+ * Instrumentation (not part of the method; used by the benchmark to report achieved
+ * bandwidth).  vd_launch_count: kernels launched by this library since it was loaded.
+ * vd_profile_enable(1): bracket every transform-pass launch with CUDA events on its stream
+ * and accumulate, per class, launches, elapsed ms, algorithmic bytes (every input and
+ * output field once) and flops (5 n log2 n per complex line transform).  Classes:
+ * 0 strided pass double, 1 strided pass float, 2 x pass double, 3 x pass float.
+ * vd_profile_read synchronises on the recorded events; vd_profile_reset clears the totals.
+ */
+long long vd_launch_count(void);
+vd_status vd_profile_enable(int on);
+vd_status vd_profile_reset(void);
+vd_status vd_profile_read(int cls, long long* launches, double* ms, double* alg_bytes, double* alg_flops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,11 @@ _SIGS = {
                       ctypes.POINTER(vd_solve_info), _P, _SZ, _P]),
     "vd_divergence": (_I, [_P, _P, _P, _P, _SZ, _P]),
     "vd_gradient": (_I, [_P, _P, _P, _P, _SZ, _P]),
+    "vd_launch_count": (ctypes.c_longlong, []),
+    "vd_profile_enable": (_I, [_I]),
+    "vd_profile_reset": (_I, []),
+    "vd_profile_read": (_I, [_I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -171,6 +176,28 @@ def vd_divergence(h, u, out, ws, stream=None):
 
 def vd_gradient(h, phi, out, ws, stream=None):
     _check(lib().vd_gradient(h, _ptr(phi), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def vd_launch_count():
+    return int(lib().vd_launch_count())
+
+
+def vd_profile_enable(on):
+    _check(lib().vd_profile_enable(int(bool(on))))
+
+
+def vd_profile_reset():
+    _check(lib().vd_profile_reset())
+
+
+PROFILE_CLASSES = {0: "axis_f64", 1: "axis_f32", 2: "xpass_f64", 3: "xpass_f32"}
+
+
+def vd_profile_read(cls):
+    n = ctypes.c_longlong()
+    ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().vd_profile_read(cls, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), ctypes.byref(fl)))
+    return {"launches": n.value, "ms": ms.value, "alg_bytes": by.value, "alg_flops": fl.value}
 
 
 # ------------------------------------------------------------------------------------------

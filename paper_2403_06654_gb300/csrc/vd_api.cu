@@ -2,6 +2,7 @@
 // the preconditioned solves (double and mixed precision).
 #include "vd_krylov.cuh"
 #include "vd_internal.h"
+#include "vd_prof.h"
 
 #include <algorithm>
 #include <cmath>
@@ -251,7 +252,7 @@ vd_status vd_density_set(vd_grid* G, vd_op op, const double* rho, void* ws, size
   if (ws_bytes < need) return fail(VD_ERR_OOM, "density workspace too small");
   const GridDesc& g = G->g;
   const int blocks = (int)std::min<long long>(1024, (g.nreal + 255) / 256);
-  k_density_prep<<<blocks, 256, 0, st>>>(g.nreal, rho, L.rho, L.rinv_s, L.rinv_f, 1.0 / (double)g.nreal, L.stats);
+  { k_density_prep<<<blocks, 256, 0, st>>>(g.nreal, rho, L.rho, L.rinv_s, L.rinv_f, 1.0 / (double)g.nreal, L.stats); count_launch(); }
   VD_CUDA(cudaGetLastError());
   std::vector<double> stats(3 * blocks);
   VD_CUDA(cudaMemcpyAsync(stats.data(), L.stats, stats.size() * 8, cudaMemcpyDeviceToHost, st));
@@ -564,6 +565,7 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
   so.maxit = prm->max_it;
   so.restart = restart;
   so.check_every = prm->check_every > 0 ? prm->check_every : 1;
+  so.x_zero = prm->use_x0 ? 0 : 1;
   SolveOut res{0, VD_ERR_NOT_CONVERGED, 0.0};
   double* hh = (info && info->hist && info->hist_cap > 0) ? info->hist : nullptr;
   // the device history buffer holds max_it + 2 entries
@@ -613,6 +615,7 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
       // below tol when it is the last sweep
       si.tol = std::max(itol, 0.5 * prm->tol / rel);
       si.maxit = prm->max_it - total;
+      si.x_zero = 1;
       SolveOut ri{0, 0, 0.0};
       std::vector<double> ih;
       const int icap = hh ? std::min(std::max(0, hcap - hlen) + 1, prm->max_it + 2) : 0;

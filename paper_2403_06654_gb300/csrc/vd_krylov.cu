@@ -7,6 +7,7 @@
 // host only reads the `done` flag every `check_every` iterations.  Kernels of an iteration
 // return at once when the flag is set, so the host may enqueue iterations ahead.
 #include "vd_krylov.cuh"
+#include "vd_prof.h"
 
 #include <algorithm>
 #include <cmath>
@@ -575,32 +576,32 @@ static inline int ew_blocks(long long len) {
 
 template <typename T>
 void spec_copy_scale(long long len, const void* x, double s, void* y, cudaStream_t st) {
-  k_copy_scale<T><<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<T>*)x, s, (cpx<T>*)y);
+  { k_copy_scale<T><<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<T>*)x, s, (cpx<T>*)y); count_launch(); }
 }
 template <typename T>
 void spec_axpy(long long len, double a, const void* x, void* y, cudaStream_t st) {
-  k_axpy<T><<<ew_blocks(len), 256, 0, st>>>(len, a, (const cpx<T>*)x, (cpx<T>*)y);
+  { k_axpy<T><<<ew_blocks(len), 256, 0, st>>>(len, a, (const cpx<T>*)x, (cpx<T>*)y); count_launch(); }
 }
 template <typename T>
 void spec_sub(long long len, const void* b, const void* q, void* r, cudaStream_t st) {
-  k_sub<T><<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<T>*)b, (const cpx<T>*)q, (cpx<T>*)r, nullptr);
+  { k_sub<T><<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<T>*)b, (const cpx<T>*)q, (cpx<T>*)r, nullptr); count_launch(); }
 }
 void spec_d2f(long long len, const void* in, void* out, cudaStream_t st) {
-  k_d2f<<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<double>*)in, (cpx<float>*)out);
+  { k_d2f<<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<double>*)in, (cpx<float>*)out); count_launch(); }
 }
 void spec_f2d(long long len, const void* in, void* out, cudaStream_t st) {
-  k_f2d<<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<float>*)in, (cpx<double>*)out);
+  { k_f2d<<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<float>*)in, (cpx<double>*)out); count_launch(); }
 }
 template <typename T>
 void spec_project(const vd_grid* G, int ncomp, void* v, cudaStream_t st) {
-  k_project<T><<<1, 32, 0, st>>>(G->g, ncomp, (cpx<T>*)v);
+  { k_project<T><<<1, 32, 0, st>>>(G->g, ncomp, (cpx<T>*)v); count_launch(); }
 }
 
 template <typename T>
 double spec_norm2_host(const SpecSystem& sys, const void* v, const KWork& kw, cudaStream_t st) {
   RedArgs ra{kw.ks, kw.partials, kw.counter, kw.hist, 0.0};
-  k_norms<T, 1><<<red_blocks(sys.len), kRedThreads, 0, st>>>(sys.len, sys.h0, nullptr, (const cpx<T>*)v, EPI_NORM, ra,
-                                                            nullptr);
+  { k_norms<T, 1><<<red_blocks(sys.len), kRedThreads, 0, st>>>(sys.len, sys.h0, nullptr, (const cpx<T>*)v, EPI_NORM, ra,
+                                                            nullptr); count_launch(); }
   double rr = 0.0;
   cudaMemcpyAsync(&rr, &kw.ks->rr, sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
@@ -666,16 +667,20 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
     cpx<T>* r = vb;
     cpx<T>* p = vb + len;
     cpx<T>* q = vb + 2 * len;
-    sys.apply(sys, X, q, false, nullptr, st);
-    k_sub<T><<<eb, 256, 0, st>>>(len, B, q, r, nullptr);
-    k_cg_init<T><<<rb, kRedThreads, 0, st>>>(len, h0, nc, B, r, p, sym, ra);
+    if (o.x_zero) {
+      VD_CUDA(cudaMemcpyAsync(r, B, sizeof(cpx<T>) * len, cudaMemcpyDeviceToDevice, st));
+    } else {
+      sys.apply(sys, X, q, false, nullptr, st);
+      { k_sub<T><<<eb, 256, 0, st>>>(len, B, q, r, nullptr); count_launch(); }
+    }
+    { k_cg_init<T><<<rb, kRedThreads, 0, st>>>(len, h0, nc, B, r, p, sym, ra); count_launch(); }
     int it = 0;
     for (;;) {
       for (int c = 0; c < check && it < o.maxit; ++c, ++it) {
         sys.apply(sys, p, q, false, done, st);
-        k_dot<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, p, q, EPI_CG_ALPHA, ra, done);
-        k_cg_update<T><<<rb, kRedThreads, 0, st>>>(len, h0, nc, X, p, r, q, sym, ra);
-        k_cg_p<T><<<eb, 256, 0, st>>>(len, nc, p, r, sym, kw.ks);
+        { k_dot<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, p, q, EPI_CG_ALPHA, ra, done); count_launch(); }
+        { k_cg_update<T><<<rb, kRedThreads, 0, st>>>(len, h0, nc, X, p, r, q, sym, ra); count_launch(); }
+        { k_cg_p<T><<<eb, 256, 0, st>>>(len, nc, p, r, sym, kw.ks); count_launch(); }
       }
       vd_status e = read_head(kw, &hd, st);
       if (e != VD_OK) return e;
@@ -684,15 +689,19 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
   } else if (o.solver == VD_SOLVER_RMR) {
     cpx<T>* r = vb;
     cpx<T>* w = vb + len;
-    sys.apply(sys, X, w, false, nullptr, st);
-    k_sub<T><<<eb, 256, 0, st>>>(len, B, w, r, nullptr);
-    k_norms<T, 2><<<rb, kRedThreads, 0, st>>>(len, h0, B, r, EPI_INIT_RMR, ra, nullptr);
+    if (o.x_zero) {
+      VD_CUDA(cudaMemcpyAsync(r, B, sizeof(cpx<T>) * len, cudaMemcpyDeviceToDevice, st));
+    } else {
+      sys.apply(sys, X, w, false, nullptr, st);
+      { k_sub<T><<<eb, 256, 0, st>>>(len, B, w, r, nullptr); count_launch(); }
+    }
+    { k_norms<T, 2><<<rb, kRedThreads, 0, st>>>(len, h0, B, r, EPI_INIT_RMR, ra, nullptr); count_launch(); }
     int it = 0;
     for (;;) {
       for (int c = 0; c < check && it < o.maxit; ++c, ++it) {
         sys.apply(sys, r, w, true, done, st);
-        k_dot<T, 2><<<rb, kRedThreads, 0, st>>>(len, h0, r, w, EPI_RMR_ALPHA, ra, done);
-        k_rmr_update<T><<<rb, kRedThreads, 0, st>>>(len, h0, nc, X, r, w, sym, ra);
+        { k_dot<T, 2><<<rb, kRedThreads, 0, st>>>(len, h0, r, w, EPI_RMR_ALPHA, ra, done); count_launch(); }
+        { k_rmr_update<T><<<rb, kRedThreads, 0, st>>>(len, h0, nc, X, r, w, sym, ra); count_launch(); }
       }
       vd_status e = read_head(kw, &hd, st);
       if (e != VD_OK) return e;
@@ -701,41 +710,45 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
   } else {
     cpx<T>* V = vb;
     cpx<T>* w = vb + (size_t)(m + 1) * len;
-    k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, nullptr, B, EPI_BB, ra, nullptr);
+    { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, nullptr, B, EPI_BB, ra, nullptr); count_launch(); }
     for (int cycle = 0;; ++cycle) {
       // r = b - A x into V_0 (unnormalised), then V_0 /= beta
-      sys.apply(sys, X, w, false, done, st);
-      k_sub<T><<<eb, 256, 0, st>>>(len, B, w, V, done);
-      k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, nullptr, V, EPI_GM_BETA, ra, done);
-      k_gm_scale<T><<<eb, 256, 0, st>>>(len, V, V, kw.ks, 1);
+      if (cycle == 0 && o.x_zero) {
+        VD_CUDA(cudaMemcpyAsync(V, B, sizeof(cpx<T>) * len, cudaMemcpyDeviceToDevice, st));
+      } else {
+        sys.apply(sys, X, w, false, done, st);
+        { k_sub<T><<<eb, 256, 0, st>>>(len, B, w, V, done); count_launch(); }
+      }
+      { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, nullptr, V, EPI_GM_BETA, ra, done); count_launch(); }
+      { k_gm_scale<T><<<eb, 256, 0, st>>>(len, V, V, kw.ks, 1); count_launch(); }
       for (int j = 0; j < m; ++j) {
         cpx<T>* Vj = V + (size_t)j * len;
         sys.apply(sys, Vj, w, true, cdone, st);
         for (int pass = 0; pass < 2; ++pass) {
           for (int off = 0; off <= j; off += 8) {
             const int nv = std::min(8, j + 1 - off);
-            k_gm_mdot<T><<<rb, kRedThreads, 0, st>>>(len, h0, w, V, off, nv, pass ? EPI_GM_H2 : EPI_GM_H1, j, ra);
+            { k_gm_mdot<T><<<rb, kRedThreads, 0, st>>>(len, h0, w, V, off, nv, pass ? EPI_GM_H2 : EPI_GM_H1, j, ra); count_launch(); }
           }
-          k_gm_maxpy<T><<<rb, kRedThreads, 0, st>>>(len, h0, w, V, j, pass, pass, ra);
+          { k_gm_maxpy<T><<<rb, kRedThreads, 0, st>>>(len, h0, w, V, j, pass, pass, ra); count_launch(); }
         }
-        k_gm_scale<T><<<eb, 256, 0, st>>>(len, V + (size_t)(j + 1) * len, w, kw.ks, 0);
+        { k_gm_scale<T><<<eb, 256, 0, st>>>(len, V + (size_t)(j + 1) * len, w, kw.ks, 0); count_launch(); }
         if ((j + 1) % check == 0 || j + 1 == m) {
           vd_status e = read_head(kw, &hd, st);
           if (e != VD_OK) return e;
           if (hd.cycle_done || hd.done) break;
         }
       }
-      k_gm_solve<<<1, 1, 0, st>>>(kw.ks);
-      k_gm_update<T><<<eb, 256, 0, st>>>(len, nc, X, V, sym, kw.ks);
-      k_gm_close<<<1, 1, 0, st>>>(kw.ks);
+      { k_gm_solve<<<1, 1, 0, st>>>(kw.ks); count_launch(); }
+      { k_gm_update<T><<<eb, 256, 0, st>>>(len, nc, X, V, sym, kw.ks); count_launch(); }
+      { k_gm_close<<<1, 1, 0, st>>>(kw.ks); count_launch(); }
       vd_status e = read_head(kw, &hd, st);
       if (e != VD_OK) return e;
       if (hd.done) break;
       if (hd.iters >= o.maxit) {
         // one more loop head forms the true residual and sets the final status
         sys.apply(sys, X, w, false, done, st);
-        k_sub<T><<<eb, 256, 0, st>>>(len, B, w, V, done);
-        k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, nullptr, V, EPI_GM_BETA, ra, done);
+        { k_sub<T><<<eb, 256, 0, st>>>(len, B, w, V, done); count_launch(); }
+        { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, nullptr, V, EPI_GM_BETA, ra, done); count_launch(); }
         e = read_head(kw, &hd, st);
         if (e != VD_OK) return e;
         break;

@@ -68,6 +68,7 @@ struct SolveOpts {
   int maxit;
   int restart;
   int check_every;
+  int x_zero;   // x is known to be zero on entry: the first residual is b (no operator apply)
 };
 
 struct SolveOut {

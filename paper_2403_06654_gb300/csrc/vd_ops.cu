@@ -5,6 +5,7 @@
 // Velocity operator (Eq. VDINSE.zeta with the Crank--Nicolson factor a = dt/(2 Re)):
 //   V~ u = u - a F[ rho^-1 ( Lap u + Sc^-1 ( (u.grad) grad rho + (grad rho.grad) u ) ) ]
 #include "vd_internal.h"
+#include "vd_prof.h"
 #include "vd_fft.cuh"
 
 #include <algorithm>
@@ -324,11 +325,11 @@ void spec_axpby_sym_launch(const vd_grid* G, int sz, const void* x, const void* 
   const long long n = G->g.ncplx;
   const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
   if (sz == 8)
-    k_spec_axpby_sym<double><<<blocks, 256, 0, st>>>(n, (const cpx<double>*)x, (const double*)symarr, alpha,
-                                                     (const cpx<double>*)y, beta, (cpx<double>*)out, done);
+    { k_spec_axpby_sym<double><<<blocks, 256, 0, st>>>(n, (const cpx<double>*)x, (const double*)symarr, alpha,
+                                                     (const cpx<double>*)y, beta, (cpx<double>*)out, done); count_launch(); }
   else
-    k_spec_axpby_sym<float><<<blocks, 256, 0, st>>>(n, (const cpx<float>*)x, (const float*)symarr, (float)alpha,
-                                                    (const cpx<float>*)y, (float)beta, (cpx<float>*)out, done);
+    { k_spec_axpby_sym<float><<<blocks, 256, 0, st>>>(n, (const cpx<float>*)x, (const float*)symarr, (float)alpha,
+                                                    (const cpx<float>*)y, (float)beta, (cpx<float>*)out, done); count_launch(); }
 }
 
 struct DensPtrs {
@@ -366,11 +367,11 @@ void velocity_combine_launch(const vd_grid* G, int sz, const void* u, const void
   for (int j = 0; j < 6; ++j) dp.h[j] = G->hrho[j];
   const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
   if (sz == 8)
-    k_vel_combine<double><<<blocks, 256, 0, st>>>(G->g.ndim, n, (const double*)u, (const double*)du, (double*)lap,
-                                                  G->rho, dp, inv_sc, done);
+    { k_vel_combine<double><<<blocks, 256, 0, st>>>(G->g.ndim, n, (const double*)u, (const double*)du, (double*)lap,
+                                                  G->rho, dp, inv_sc, done); count_launch(); }
   else
-    k_vel_combine<float><<<blocks, 256, 0, st>>>(G->g.ndim, n, (const float*)u, (const float*)du, (float*)lap,
-                                                 G->rho, dp, inv_sc, done);
+    { k_vel_combine<float><<<blocks, 256, 0, st>>>(G->g.ndim, n, (const float*)u, (const float*)du, (float*)lap,
+                                                 G->rho, dp, inv_sc, done); count_launch(); }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -407,7 +408,7 @@ template <typename T>
 void fill_symbol(const vd_grid* G, int kind, double a, T* out, cudaStream_t st) {
   const long long n = G->g.ncplx;
   const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
-  k_fill_symbol<T><<<blocks, 256, 0, st>>>(G->g, kind, a, out);
+  { k_fill_symbol<T><<<blocks, 256, 0, st>>>(G->g, kind, a, out); count_launch(); }
 }
 
 template void fwd_transform<double>(const vd_grid*, const double*, cpx<double>*, cudaStream_t);

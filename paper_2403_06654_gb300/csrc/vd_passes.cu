@@ -1,6 +1,9 @@
 // Transform pass kernels: strided-axis passes (y, z) and the fused contiguous x pass.
 #include "vd_passes.cuh"
 #include "vd_fft.cuh"
+#include "vd_prof.h"
+
+#include <cmath>
 
 #include <algorithm>
 
@@ -304,6 +307,20 @@ void launch_axis(const AxisProg& P, int dir, const GridDesc& g, const void* tw, 
   const long long blocks = outer_n * ((inner_n + W - 1) / W);
   const size_t smem = axis_smem_bytes<T>(g, P.axis);
   const cpx<T>* twp = reinterpret_cast<const cpx<T>*>(tw);
+  // algorithmic traffic: every distinct input and output field once, the symbol array once
+  unsigned inmask = 0, outmask = 0;
+  int nfft = 0;
+  bool sym = false;
+  for (int t = 0; t < P.nxf; ++t) {
+    inmask |= 1u << P.xf[t].src;
+    outmask |= 1u << P.xf[t].dst;
+    nfft += P.xf[t].nofft ? 0 : 1;
+    sym = sym || ((P.xf[t].pre | P.xf[t].post) & MUL_SYM);
+  }
+  const double fb = (double)g.ncplx * sizeof(cpx<T>);
+  const double bytes = (__builtin_popcount(inmask) + __builtin_popcount(outmask)) * fb + (sym ? g.ncplx * sizeof(T) : 0);
+  const double flops = (double)nfft * (double)g.ncplx * 5.0 * std::log2((double)n);
+  ProfScope ps(sizeof(T) == 8 ? PC_AXIS64 : PC_AXIS32, st, bytes, flops);
   if (dir < 0) {
     set_axis_attr<T, -1>(smem);
     k_axis<T, -1><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, W);
@@ -325,6 +342,20 @@ void launch_xpass(const XProg& P, const GridDesc& g, const void* tw, cudaStream_
     cudaFuncSetAttribute(k_xpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     done = smem;
   }
+  const double fc = (double)g.ncplx * sizeof(cpx<T>), fr = (double)g.nreal * sizeof(T);
+  double bytes = 0, flops = 0;
+  const double real_fft = (double)g.nreal * 2.5 * std::log2((double)g.n0);   // one real transform of every line
+  if (P.mode == 0) {
+    bytes = P.ncomp * 2.0 * fc + (P.wfield ? fr : 0.0);
+    flops = P.ncomp * 2.0 * real_fft;
+  } else {
+    bytes = P.ncomp * (fc + fr);
+    flops = P.ncomp * real_fft;
+  }
+  bool sym = false;
+  for (int c = 0; c < P.ncomp; ++c) sym = sym || ((P.pre[c] | P.post[c]) & MUL_SYM);
+  if (sym) bytes += (double)g.ncplx * sizeof(T);
+  ProfScope ps(sizeof(T) == 8 ? PC_XPASS64 : PC_XPASS32, st, bytes, flops);
   k_xpass<T><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, reinterpret_cast<const cpx<T>*>(tw), L);
 }
 

@@ -1,0 +1,113 @@
+// Launch counter and per-class event timing of the transform passes.
+#include "vd_prof.h"
+#include "vd_internal.h"
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+namespace vd {
+
+static std::atomic<long long> g_launches{0};
+static std::atomic<int> g_prof_on{0};
+
+struct Pending {
+  int cls;
+  cudaEvent_t a, b;
+  double bytes, flops;
+};
+struct ClassTotals {
+  long long launches = 0;
+  double ms = 0.0, bytes = 0.0, flops = 0.0;
+};
+
+static std::mutex g_mu;
+static std::vector<Pending> g_pending;
+static std::vector<cudaEvent_t> g_free;
+static ClassTotals g_tot[PC_N];
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static cudaEvent_t get_event() {
+  if (!g_free.empty()) {
+    cudaEvent_t e = g_free.back();
+    g_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+ProfScope::ProfScope(int c, cudaStream_t s, double by, double fl) : cls(c), st(s), bytes(by), flops(fl), slot(-1) {
+  count_launch();
+  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Pending p;
+  p.cls = c;
+  p.a = get_event();
+  p.b = get_event();
+  p.bytes = by;
+  p.flops = fl;
+  cudaEventRecord(p.a, s);
+  g_pending.push_back(p);
+  slot = (int)g_pending.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaEventRecord(g_pending[slot].b, st);
+}
+
+static void collect_locked() {
+  for (auto& p : g_pending) {
+    cudaEventSynchronize(p.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    ClassTotals& t = g_tot[p.cls];
+    t.launches += 1;
+    t.ms += ms;
+    t.bytes += p.bytes;
+    t.flops += p.flops;
+    g_free.push_back(p.a);
+    g_free.push_back(p.b);
+  }
+  g_pending.clear();
+}
+
+}  // namespace vd
+
+using namespace vd;
+
+extern "C" {
+
+long long vd_launch_count(void) { return g_launches.load(); }
+
+vd_status vd_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!on) collect_locked();
+  g_prof_on.store(on ? 1 : 0);
+  return VD_OK;
+}
+
+vd_status vd_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  collect_locked();
+  for (auto& t : g_tot) t = ClassTotals();
+  return VD_OK;
+}
+
+vd_status vd_profile_read(int cls, long long* launches, double* ms, double* alg_bytes, double* alg_flops) {
+  if (cls < 0 || cls >= PC_N) return fail(VD_ERR_INVALID_ARG, "unknown profile class");
+  std::lock_guard<std::mutex> lk(g_mu);
+  collect_locked();
+  const ClassTotals& t = g_tot[cls];
+  if (launches) *launches = t.launches;
+  if (ms) *ms = t.ms;
+  if (alg_bytes) *alg_bytes = t.bytes;
+  if (alg_flops) *alg_flops = t.flops;
+  return VD_OK;
+}
+
+}  // extern "C"

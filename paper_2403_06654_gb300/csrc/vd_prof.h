@@ -1,0 +1,34 @@
+// Launch counting and optional per-kernel-class event timing.
+//
+// Every kernel launch of the library increments a process-wide counter.  When profiling is
+// enabled, the transform-pass launches are bracketed by CUDA events recorded on the launching
+// stream, and the algorithmic bytes (each input/output field once) and flops (5 n log2 n per
+// complex line transform of length n) of the launch are accumulated per class.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace vd {
+
+enum ProfClass : int {
+  PC_AXIS64 = 0,   // strided y/z pass, double
+  PC_AXIS32 = 1,   // strided y/z pass, float
+  PC_XPASS64 = 2,  // contiguous x pass, double
+  PC_XPASS32 = 3,  // contiguous x pass, float
+  PC_OTHER = 4,    // reductions, vector updates, pointwise kernels
+  PC_N = 5
+};
+
+void count_launch();
+
+// RAII bracket of one launch; records events only when profiling is on
+struct ProfScope {
+  ProfScope(int cls, cudaStream_t st, double bytes, double flops);
+  ~ProfScope();
+  int cls;
+  cudaStream_t st;
+  double bytes, flops;
+  int slot;
+};
+
+}  // namespace vd
