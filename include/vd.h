@@ -169,6 +169,26 @@ vd_status vd_gradient(const vd_grid* grid, const double* phi, double* out, void*
                       vd_stream stream);
 
 /*
+ * out = L~_rho(in) for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is an integration convenience).  Such callers include code running
+ * inside a host framework whose memory pool owns the device, plugins that must keep a
+ * fixed device footprint, and loops that must not synchronise the device through an
+ * allocation.  The call takes the grid description directly (ndim, n, L as in
+ * vd_grid_create), the density rho and the physical fields in/out (n0 n1 n2 doubles each,
+ * device, caller-owned; in and out must not alias), and allocates nothing: it calls no
+ * cudaMalloc/cudaFree and no allocating library routine.  Every intermediate lives in one
+ * fixed file-scope device array of 32 MiB, held by each GPU that loads the library until
+ * the process exits; grids needing more (3D beyond about 64^3, 2D beyond 512 x 1024) are
+ * rejected with VD_ERR_INVALID_ARG and a message giving the size.  The first call on a
+ * device looks up the array's device address (once per device, with that device current):
+ * make that first call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents, so calls whose kernels overlap on the GPU race: serialise them.
+ * rho must be positive and finite (VD_ERR_INVALID_ARG otherwise; this synchronises stream).
+ */
+vd_status vd_apply_pressure_noalloc(int ndim, const int n[3], const double L[3], const double* rho, const double* in,
+                                    double* out, vd_stream stream);
+
+/*
  * Instrumentation (not part of the method; used by the benchmark to report achieved
  * bandwidth).  vd_launch_count: kernels launched by this library since it was loaded.
  * vd_profile_enable(1): bracket every transform-pass launch with CUDA events on its stream

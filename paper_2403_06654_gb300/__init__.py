@@ -76,6 +76,7 @@ _SIGS = {
                       ctypes.POINTER(vd_solve_info), _P, _SZ, _P]),
     "vd_divergence": (_I, [_P, _P, _P, _P, _SZ, _P]),
     "vd_gradient": (_I, [_P, _P, _P, _P, _SZ, _P]),
+    "vd_apply_pressure_noalloc": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), _P, _P, _P, _P]),
     "vd_launch_count": (ctypes.c_longlong, []),
     "vd_profile_enable": (_I, [_I]),
     "vd_profile_reset": (_I, []),
@@ -176,6 +177,16 @@ def vd_divergence(h, u, out, ws, stream=None):
 
 def vd_gradient(h, phi, out, ws, stream=None):
     _check(lib().vd_gradient(h, _ptr(phi), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def vd_apply_pressure_noalloc(n, L, rho, x, out, stream=None):
+    """Pressure apply through the entry point that allocates no device memory: for callers
+    that cannot allocate (a host framework's pool owns the device, fixed-footprint plugins,
+    loops that must not synchronise through an allocation).  Only marshalling here."""
+    nd = len(n)
+    nn = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - nd)))
+    ll = (ctypes.c_double * 3)(*(list(L) + [1.0] * (3 - nd)))
+    _check(lib().vd_apply_pressure_noalloc(nd, nn, ll, _ptr(rho), _ptr(x), _ptr(out), _stream(stream)))
 
 
 def vd_launch_count():
