@@ -59,9 +59,14 @@ typedef enum { VD_OP_PRESSURE = 0, VD_OP_VELOCITY = 1 } vd_op;
 typedef enum { VD_SOLVER_CG = 0, VD_SOLVER_GMRES = 1, VD_SOLVER_RMR = 2 } vd_solver;
 typedef enum {
   VD_PREC_FP64 = 0,  /* every transform, product and reduction in IEEE double */
-  VD_PREC_MIXED = 1  /* inner Krylov solve with float transforms and preconditioner, double
+  VD_PREC_MIXED = 1, /* inner Krylov solve with float transforms and preconditioner, double
                         dot products, inside a double iterative-refinement loop whose true
                         residual uses the double operator (spec precision form) */
+  VD_PREC_MIXED_DD = 2 /* as VD_PREC_MIXED, but the refinement residual b - A x of the pressure
+                        operator is formed with float-pair transforms (two floats per value,
+                        ~2^-48 relative rounding, on the FP32 pipes; storage stays double).
+                        On GB300 double arithmetic runs at 1/69 of the float rate, which makes
+                        this much faster; the velocity operator keeps the double residual. */
 } vd_precision;
 
 /* Parameters of the velocity operator: a = dt/(2 Re) (Eq. VDINSE.Vrho), inv_sc = 1/Sc. */
@@ -194,7 +199,8 @@ vd_status vd_apply_pressure_noalloc(int ndim, const int n[3], const double L[3],
  * vd_profile_enable(1): bracket every transform-pass launch with CUDA events on its stream
  * and accumulate, per class, launches, elapsed ms, algorithmic bytes (every input and
  * output field once) and flops (5 n log2 n per complex line transform).  Classes:
- * 0 strided pass double, 1 strided pass float, 2 x pass double, 3 x pass float.
+ * 0 strided pass double, 1 strided pass float, 2 x pass double, 3 x pass float,
+ * 5 strided pass float-pair, 6 x pass float-pair (4: unused).
  * vd_profile_read synchronises on the recorded events; vd_profile_reset clears the totals.
  */
 long long vd_launch_count(void);

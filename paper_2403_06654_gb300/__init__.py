@@ -27,10 +27,10 @@ STATUS_NAMES = {0: "converged", 1: "invalid_arg", 2: "oom", 3: "cuda", 4: "max_i
                 6: "diverged", 7: "nonfinite", 8: "no_density"}
 VD_OP_PRESSURE, VD_OP_VELOCITY = 0, 1
 VD_SOLVER_CG, VD_SOLVER_GMRES, VD_SOLVER_RMR = 0, 1, 2
-VD_PREC_FP64, VD_PREC_MIXED = 0, 1
+VD_PREC_FP64, VD_PREC_MIXED, VD_PREC_MIXED_DD = 0, 1, 2
 OPS = {"pressure": VD_OP_PRESSURE, "velocity": VD_OP_VELOCITY}
 SOLVERS = {"cg": VD_SOLVER_CG, "gmres": VD_SOLVER_GMRES, "rmr": VD_SOLVER_RMR}
-PRECISIONS = {"fp64": VD_PREC_FP64, "mixed": VD_PREC_MIXED}
+PRECISIONS = {"fp64": VD_PREC_FP64, "mixed": VD_PREC_MIXED, "mixed_dd": VD_PREC_MIXED_DD}
 
 
 class VDError(RuntimeError):
@@ -201,7 +201,7 @@ def vd_profile_reset():
     _check(lib().vd_profile_reset())
 
 
-PROFILE_CLASSES = {0: "axis_f64", 1: "axis_f32", 2: "xpass_f64", 3: "xpass_f32"}
+PROFILE_CLASSES = {0: "axis_f64", 1: "axis_f32", 2: "xpass_f64", 3: "xpass_f32", 5: "axis_dd", 6: "xpass_dd"}
 
 
 def vd_profile_read(cls):

@@ -1,6 +1,7 @@
 // C ABI of the library: grids, density data, operator/preconditioner application and
 // the preconditioned solves (double and mixed precision).
 #include "vd_krylov.cuh"
+#include "vd_dd.cuh"
 #include "vd_internal.h"
 #include "vd_prof.h"
 
@@ -45,12 +46,23 @@ static bool make_plan(int n, FftPlan* p) {
   return p->nst <= kMaxStages;
 }
 
-// exp(-2 pi i j / n) evaluated in extended precision, rounded once to double
-static void twiddle(long long j, long long n, double* re, double* im) {
+// exp(-2 pi i j / n) evaluated in extended precision
+static void twiddle_ld(long long j, long long n, long double* re, long double* im) {
   j %= n;
   const long double th = 2.0L * 3.14159265358979323846264338327950288L * (long double)j / (long double)n;
-  *re = (double)cosl(th);
-  *im = (double)(-sinl(th));
+  *re = cosl(th);
+  *im = -sinl(th);
+}
+static void twiddle(long long j, long long n, double* re, double* im) {
+  long double r, i;
+  twiddle_ld(j, n, &r, &i);
+  *re = (double)r;
+  *im = (double)i;
+}
+// float-pair split of an extended-precision value
+static void split_ld(long double v, float* hi, float* lo) {
+  *hi = (float)v;
+  *lo = (float)(v - (long double)*hi);
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -97,9 +109,15 @@ vd_status vd_grid_create(int ndim, const int n[3], const double L[3], vd_grid** 
   g.h0 = nn[0] / 2 + 1;
   g.nreal = (long long)nn[0] * nn[1] * nn[2];
   g.ncplx = (long long)g.h0 * nn[1] * nn[2];
+  if (g.ncplx * 3 >= (1ll << 31)) {
+    delete G;
+    return fail(VD_ERR_INVALID_ARG, "grid too large: field offsets must fit in 32 bits");
+  }
   for (int j = 0; j < 3; ++j) {
     G->L[j] = (j < ndim) ? L[j] : 1.0;
     g.kfac[j] = 2.0 * 3.14159265358979323846 / G->L[j];
+    const long double kl = 2.0L * 3.14159265358979323846264338327950288L / (long double)G->L[j];
+    split_ld(kl, &g.kfac_dd[j][0], &g.kfac_dd[j][1]);
   }
   bool ok = make_plan(nn[0] / 2, &g.px);
   if (ndim >= 2) ok = ok && make_plan(nn[1], &g.py);
@@ -135,13 +153,32 @@ vd_status vd_grid_create(int ndim, const int n[3], const double L[3], vd_grid** 
   }
   std::vector<float> twf(tw.size());
   for (size_t i = 0; i < tw.size(); ++i) twf[i] = (float)tw[i];
+  // float-pair table, split from the extended-precision values (same index layout)
+  std::vector<float> twdd(2 * tw.size());
+  {
+    auto put = [&](size_t at, int j, int len) {
+      long double re, im;
+      twiddle_ld(j, len, &re, &im);
+      split_ld(re, &twdd[4 * at + 0], &twdd[4 * at + 1]);
+      split_ld(im, &twdd[4 * at + 2], &twdd[4 * at + 3]);
+    };
+    for (int j = 0; j < g.px.n; ++j) put(g.px.tw_off + j, j, g.px.n);
+    if (ndim >= 2)
+      for (int j = 0; j < g.py.n; ++j) put(g.py.tw_off + j, j, g.py.n);
+    if (ndim == 3)
+      for (int j = 0; j < g.pz.n; ++j) put(g.pz.tw_off + j, j, g.pz.n);
+    for (int k = 0; k <= nn[0] / 2; ++k) put(g.pk_off + k, k, nn[0]);
+  }
   cudaError_t e = cudaMalloc(&G->tw_d, tw.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&G->tw_f, twf.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&G->tw_dd, twdd.size() * sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpy(G->tw_d, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(G->tw_f, twf.data(), twf.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(G->tw_dd, twdd.data(), twdd.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     if (G->tw_d) cudaFree(G->tw_d);
     if (G->tw_f) cudaFree(G->tw_f);
+    if (G->tw_dd) cudaFree(G->tw_dd);
     delete G;
     return cuda_fail(e, "vd_grid_create");
   }
@@ -153,6 +190,7 @@ vd_status vd_grid_destroy(vd_grid* G) {
   if (!G) return VD_OK;
   if (G->tw_d) cudaFree(G->tw_d);
   if (G->tw_f) cudaFree(G->tw_f);
+  if (G->tw_dd) cudaFree(G->tw_dd);
   delete G;
   return VD_OK;
 }
@@ -169,7 +207,8 @@ size_t vd_grid_modes(const vd_grid* G) { return G ? (size_t)G->g.ncplx : 0; }
 namespace vd {
 
 __global__ void k_density_prep(long long n, const double* __restrict__ rho, double* __restrict__ rcopy,
-                               double* __restrict__ rinv_s, float* __restrict__ rinv_f, double invN,
+                               double* __restrict__ rinv_s, float* __restrict__ rinv_f, dd* __restrict__ rinv_dd,
+                               double invN,
                                double* __restrict__ stats /* [min, max, bad] via block partials */) {
   __shared__ double smin[256], smax[256], sbad[256];
   double mn = 1e308, mx = -1e308, bd = 0.0;
@@ -179,6 +218,7 @@ __global__ void k_density_prep(long long n, const double* __restrict__ rho, doub
     const double ri = invN / r;
     rinv_s[e] = ri;
     rinv_f[e] = (float)ri;
+    rinv_dd[e] = dd_from_double(ri);
     if (!(r > 0.0) || !isfinite(r)) bd = 1.0;
     mn = fmin(mn, r);
     mx = fmax(mx, r);
@@ -206,6 +246,7 @@ struct DensLayout {
   double* rho;
   double* rinv_s;
   float* rinv_f;
+  dd* rinv_dd;
   double* stats;
   double* grho;     // d fields
   double* hrho;     // 6 fields, slot hidx(i, j)
@@ -220,6 +261,7 @@ static DensLayout dens_layout(const vd_grid* G, vd_op op, void* base, size_t* by
   L.rho = c.take<double>(nr * 8);
   L.rinv_s = c.take<double>(nr * 8);
   L.rinv_f = c.take<float>(nr * 4);
+  L.rinv_dd = c.take<dd>(nr * sizeof(dd));
   L.stats = c.take<double>(3 * 1024 * 8);
   L.grho = L.hrho = nullptr;
   L.s0 = nullptr;
@@ -252,7 +294,8 @@ vd_status vd_density_set(vd_grid* G, vd_op op, const double* rho, void* ws, size
   if (ws_bytes < need) return fail(VD_ERR_OOM, "density workspace too small");
   const GridDesc& g = G->g;
   const int blocks = (int)std::min<long long>(1024, (g.nreal + 255) / 256);
-  { k_density_prep<<<blocks, 256, 0, st>>>(g.nreal, rho, L.rho, L.rinv_s, L.rinv_f, 1.0 / (double)g.nreal, L.stats); count_launch(); }
+  { k_density_prep<<<blocks, 256, 0, st>>>(g.nreal, rho, L.rho, L.rinv_s, L.rinv_f, L.rinv_dd, 1.0 / (double)g.nreal,
+                                        L.stats); count_launch(); }
   VD_CUDA(cudaGetLastError());
   std::vector<double> stats(3 * blocks);
   VD_CUDA(cudaMemcpyAsync(stats.data(), L.stats, stats.size() * 8, cudaMemcpyDeviceToHost, st));
@@ -270,6 +313,7 @@ vd_status vd_density_set(vd_grid* G, vd_op op, const double* rho, void* ws, size
   G->rho = L.rho;
   G->rinv_s = L.rinv_s;
   G->rinv_s_f = L.rinv_f;
+  G->rinv_s_dd = L.rinv_dd;
   G->rho_min = mn;
   G->rho_max = mx;
   G->has_density = 1;
@@ -352,7 +396,7 @@ static SolveLayout solve_layout(const vd_grid* G, vd_op op, int solver, int rest
   SpecSystem dummy{};
   dummy.len = (long long)len;
   const int tf = std::max(op_tmp_fields(G, op), 1);
-  if (precision == VD_PREC_MIXED) {
+  if (precision == VD_PREC_MIXED || precision == VD_PREC_MIXED_DD) {
     L.sym_f = c.take<float>(nc * 4);
     L.vecs = c.take<char>(krylov_vec_bytes<float>(dummy, solver, restart));
     L.bh_f = c.take<cpx<float>>(len * 8);
@@ -533,7 +577,7 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
   if (solver == VD_SOLVER_CG && op == VD_OP_VELOCITY)
     return fail(VD_ERR_INVALID_ARG, "CG needs a symmetric operator; V_rho is not symmetric");
   if (!(prm->tol >= 0.0) || prm->max_it < 0) return fail(VD_ERR_INVALID_ARG, "tol must be >= 0 and max_it >= 0");
-  if (prm->precision != VD_PREC_FP64 && prm->precision != VD_PREC_MIXED)
+  if (prm->precision != VD_PREC_FP64 && prm->precision != VD_PREC_MIXED && prm->precision != VD_PREC_MIXED_DD)
     return fail(VD_ERR_INVALID_ARG, "unknown precision mode");
   if (solver == VD_SOLVER_GMRES && prm->restart > kMaxRestart)
     return fail(VD_ERR_INVALID_ARG, "GMRES restart must be <= 64");
@@ -580,10 +624,16 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
     // iterative refinement: r = b - A64 x; inner float solve A32 d = r/|r|; x += |r| d
     fill_symbol<float>(G, symkind, opp ? opp->a : 0.0, L.sym_f, st);
     SpecSystem sys32 = make_system<float>(G, op, opp, L.sym_f, L.tmp_f);
+    // residual operator of the refinement: double, or float-pair transforms (pressure)
+    const bool use_dd = prm->precision == VD_PREC_MIXED_DD && op == VD_OP_PRESSURE;
+    auto resid_apply = [&](const cpx<double>* xin, cpx<double>* yout) {
+      if (use_dd) apply_pressure_spec_dd(G, xin, yout, L.tmp, nullptr, st);
+      else sys64.apply(sys64, xin, yout, false, nullptr, st);
+    };
     const double bb = spec_norm2_host<double>(sys64, L.bh, kw, st);
     const double bnorm = std::sqrt(bb);
     if (prm->use_x0) {
-      sys64.apply(sys64, L.xh, L.rh, false, nullptr, st);
+      resid_apply(L.xh, L.rh);
       spec_sub<double>(len, L.bh, L.rh, L.rh, st);
     } else {
       VD_CUDA(cudaMemcpyAsync(L.rh, L.bh, sizeof(cpx<double>) * len, cudaMemcpyDeviceToDevice, st));
@@ -629,8 +679,8 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
       // x += rnorm * d  (d promoted to double)
       spec_f2d(len, L.xh_f, L.rh, st);
       spec_axpy<double>(len, rnorm, L.rh, L.xh, st);
-      // true residual with the double operator
-      sys64.apply(sys64, L.xh, L.rh, false, nullptr, st);
+      // true residual (double operator, or float-pair transforms in VD_PREC_MIXED_DD)
+      resid_apply(L.xh, L.rh);
       spec_sub<double>(len, L.bh, L.rh, L.rh, st);
       rnorm = std::sqrt(spec_norm2_host<double>(sys64, L.rh, kw, st));
       if (ri.status == VD_ERR_NONFINITE) {

@@ -10,9 +10,9 @@
 // W = exp(-2 pi i/.), inverse ones its conjugate; neither is normalised.
 //
 // Many independent lines are transformed together: element idx of line l lives at
-// buf[l * ls + idx * es].  Strided-axis tiles use (es, ls) = (W, 1), contiguous x lines use
-// (1, n + pad); LINE_FAST selects the thread mapping that keeps shared-memory accesses of a
-// warp on consecutive addresses for each layout.
+// buf[l * ls + idx * es].  Strided-axis tiles use (es, ls) = (W, 1) (W lines side by side),
+// contiguous x lines use (1, n + 1).  Each thread keeps one line for the whole transform, so
+// the index arithmetic needs no division by run-time widths.
 #pragma once
 
 #include "vd_common.cuh"
@@ -100,6 +100,43 @@ __device__ __forceinline__ void dft8(cpx<T>* u) {
   u[7] = e[3] - o[3];
 }
 
+// 16-point DFT as 4 x 4 (n = 4a + b, k = c + 4d) with the internal twiddles W16^{bc}
+template <typename T, int S>
+__device__ __forceinline__ cpx<T> w16(cpx<T> v, int m) {
+  // v * exp(S 2 pi i m / 16), m in {0, 1, 2, 3, 4, 6, 9}
+  const T c1 = T(0.92387953251128675612818318939679);   // cos(pi/8)
+  const T s1 = T(0.38268343236508977172845998403040);   // sin(pi/8)
+  const T r2 = T(0.70710678118654752440084436210485);   // 1/sqrt(2)
+  switch (m) {
+    case 0: return v;
+    case 1: return cmul(v, mk<T>(c1, T(S) * s1));
+    case 2: return scal(v + mul_si<T, S>(v), r2);
+    case 3: return cmul(v, mk<T>(s1, T(S) * c1));
+    case 4: return mul_si<T, S>(v);
+    case 6: return scal(mul_si<T, S>(v) - v, r2);
+    default: return cmul(v, mk<T>(-c1, T(-S) * s1));   // m = 9: cos(9pi/8), S sin(9pi/8)
+  }
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void dft16(cpx<T>* u) {
+  cpx<T> v[4][4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    cpx<T> t[4] = {u[b], u[4 + b], u[8 + b], u[12 + b]};
+    dft4<T, S>(t);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[b][c] = w16<T, S>(t[c], b * c);
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    cpx<T> t[4] = {v[0][c], v[1][c], v[2][c], v[3][c]};
+    dft4<T, S>(t);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) u[c + 4 * d] = t[d];
+  }
+}
+
 template <typename T, int S, int R>
 __device__ __forceinline__ void dftR(cpx<T>* u) {
   if constexpr (R == 2) {
@@ -110,30 +147,27 @@ __device__ __forceinline__ void dftR(cpx<T>* u) {
     dft4<T, S>(u);
   } else if constexpr (R == 5) {
     dft5<T, S>(u);
+  } else if constexpr (R == 16) {
+    dft16<T, S>(u);
   } else {
     dft8<T, S>(u);
   }
 }
 
-// one Stockham stage over nlines lines
-template <typename T, int S, int R, bool LINE_FAST>
-__device__ __forceinline__ void stockham_stage(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
-                                               int es, int ls, int nlines, int n, int p,
-                                               const cpx<T>* __restrict__ tw, int tid, int nthr) {
+// One Stockham stage.  Every thread owns one line (element idx of it at
+// buf[lofs + idx * es]) and the butterflies i0, i0 + istep, ... of that line.  k = i mod p
+// uses a mask when p is a power of two (pmask >= 0), an integer division otherwise.
+template <typename T, int S, int R>
+__device__ __forceinline__ void stockham_stage(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst, int es,
+                                               int lofs, int i0, int istep, int n, int p,
+                                               const cpx<T>* __restrict__ tw) {
   const int nb = n / R;
-  const int total = nb * nlines;
   const int tws = n / (p * R);
-  for (int q = tid; q < total; q += nthr) {
-    int line, i;
-    if (LINE_FAST) {
-      line = q % nlines;
-      i = q / nlines;
-    } else {
-      i = q % nb;
-      line = q / nb;
-    }
-    const int k = i % p;
-    const cpx<T>* s = src + line * ls;
+  const int pmask = ((p & (p - 1)) == 0) ? p - 1 : -1;
+#pragma unroll 1
+  for (int i = i0; i < nb; i += istep) {
+    const int k = (pmask >= 0) ? (i & pmask) : (i % p);
+    const cpx<T>* s = src + lofs;
     cpx<T> u[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) u[r] = s[(i + r * nb) * es];
@@ -145,17 +179,17 @@ __device__ __forceinline__ void stockham_stage(const cpx<T>* __restrict__ src, c
       }
     }
     dftR<T, S, R>(u);
-    cpx<T>* d = dst + line * ls + ((i - k) * R + k) * es;
+    cpx<T>* d = dst + lofs + ((i - k) * R + k) * es;
 #pragma unroll
     for (int r = 0; r < R; ++r) d[r * p * es] = u[r];
   }
 }
 
-// Full transform; input in a.  Returns the buffer holding the result.
-// Must be called by all threads of the block; syncs before every stage and at the end.
-template <typename T, int S, bool LINE_FAST>
-__device__ cpx<T>* fft_pingpong(cpx<T>* a, cpx<T>* b, int es, int ls, int nlines, const FftPlan& pl,
-                                const cpx<T>* tw, int tid, int nthr) {
+// Full transform of every line of the block; input in a.  Returns the buffer holding the
+// result.  Must be called by all threads of the block (syncs before every stage and at the end).
+template <typename T, int S>
+__device__ cpx<T>* fft_lines(cpx<T>* a, cpx<T>* b, int es, int lofs, int i0, int istep, const FftPlan& pl,
+                             const cpx<T>* tw) {
   cpx<T>* src = a;
   cpx<T>* dst = b;
   int p = 1;
@@ -163,11 +197,11 @@ __device__ cpx<T>* fft_pingpong(cpx<T>* a, cpx<T>* b, int es, int ls, int nlines
     const int R = pl.rad[s];
     __syncthreads();
     switch (R) {
-      case 2: stockham_stage<T, S, 2, LINE_FAST>(src, dst, es, ls, nlines, pl.n, p, tw, tid, nthr); break;
-      case 3: stockham_stage<T, S, 3, LINE_FAST>(src, dst, es, ls, nlines, pl.n, p, tw, tid, nthr); break;
-      case 4: stockham_stage<T, S, 4, LINE_FAST>(src, dst, es, ls, nlines, pl.n, p, tw, tid, nthr); break;
-      case 5: stockham_stage<T, S, 5, LINE_FAST>(src, dst, es, ls, nlines, pl.n, p, tw, tid, nthr); break;
-      default: stockham_stage<T, S, 8, LINE_FAST>(src, dst, es, ls, nlines, pl.n, p, tw, tid, nthr); break;
+      case 2: stockham_stage<T, S, 2>(src, dst, es, lofs, i0, istep, pl.n, p, tw); break;
+      case 3: stockham_stage<T, S, 3>(src, dst, es, lofs, i0, istep, pl.n, p, tw); break;
+      case 4: stockham_stage<T, S, 4>(src, dst, es, lofs, i0, istep, pl.n, p, tw); break;
+      case 5: stockham_stage<T, S, 5>(src, dst, es, lofs, i0, istep, pl.n, p, tw); break;
+      default: stockham_stage<T, S, 8>(src, dst, es, lofs, i0, istep, pl.n, p, tw); break;
     }
     p *= R;
     cpx<T>* t = src;

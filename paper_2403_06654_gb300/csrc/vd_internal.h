@@ -15,9 +15,11 @@ struct vd_grid {
   double L[3];
   void* tw_d = nullptr;   // cpx<double> twiddle table (library-owned)
   void* tw_f = nullptr;   // cpx<float> copy
+  void* tw_dd = nullptr;  // cpx<dd> copy (float-pair split of the extended-precision values)
   // density data (inside the caller's density workspace; set by vd_density_set)
   const double* rinv_s = nullptr;    // 1/(N rho), physical
   const float* rinv_s_f = nullptr;   // same, float
+  const void* rinv_s_dd = nullptr;   // same, float-pair (dd per point)
   const double* grho[3] = {nullptr, nullptr, nullptr};     // D_j rho
   const double* hrho[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // D_i D_j rho (i<=j)
   const double* rho = nullptr;       // copy of rho
@@ -74,6 +76,11 @@ void inv_transform(const vd_grid* G, const cpx<T>* in, const Mult& m, T* out, cp
 template <typename T>
 void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, const T* rinv_s,
                          cpx<T>* tmp, const int* done, cudaStream_t st);
+
+// Pressure operator with float-pair transforms: double spectral fields in and out (no
+// preconditioner), float-pair intermediates in tmp (3 spectral fields of 16 bytes per element).
+void apply_pressure_spec_dd(const vd_grid* G, const cpx<double>* in, cpx<double>* out, void* tmp, const int* done,
+                            cudaStream_t st);
 
 // Velocity operator in spectral space: out_i = (S in)_i - a * F[rho^-1 (Lap u + Sc^-1 (...))]_i with u =
 // F^-1 (S in).  ncomp = ndim components stored back to back.  tmp: see velocity_tmp_fields().

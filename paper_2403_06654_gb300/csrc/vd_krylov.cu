@@ -297,23 +297,59 @@ struct RedArgs {
   double tol;
 };
 
+// Grid-stride iteration over a spectral vector that tracks, without any division inside
+// the loop, kx = e mod h0 (Parseval weight) and the symbol index e mod ncplx.
+struct Ix {
+  int len, h0, nc;   // vector length (complex elements), x half-spectrum length, field size
+  int sh, sn;        // grid stride mod h0, grid stride mod nc
+};
+
+#define IX_LOOP(ix)                                                                          \
+  const int ix_s_ = gridDim.x * blockDim.x;                                                 \
+  int e = blockIdx.x * blockDim.x + threadIdx.x;                                            \
+  int kx = e % (ix).h0, si = e % (ix).nc;                                                   \
+  for (; e < (ix).len; e += ix_s_, kx += (ix).sh, kx -= (kx >= (ix).h0) ? (ix).h0 : 0,      \
+                       si += (ix).sn, si -= (si >= (ix).nc) ? (ix).nc : 0)
+
+template <typename T>
+__device__ __forceinline__ T pweight(int kx, int h0) {
+  return (kx == 0 || kx == h0 - 1) ? T(1) : T(2);
+}
+
+// Double-precision accumulator fed by short sub-sums in the vector precision (four terms)
+template <typename T>
+struct Acc {
+  double a = 0.0;
+  T s = T(0);
+  int c = 0;
+  __device__ __forceinline__ void add(T v) {
+    s += v;
+    if (++c == 4) {
+      a += (double)s;
+      s = T(0);
+      c = 0;
+    }
+  }
+  __device__ __forceinline__ double total() const { return a + (double)s; }
+};
+
 // CG start: p = S r, reduce [bb, rr, rz]
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_cg_init(long long len, int h0, long long ncplx,
-                                                         const cpx<T>* __restrict__ b, const cpx<T>* __restrict__ r,
-                                                         cpx<T>* __restrict__ p, const T* __restrict__ sym,
-                                                         RedArgs ra) {
-  double v[3] = {0.0, 0.0, 0.0};
-  GRID_STRIDE(e, len) {
-    const double w = wgt(e, h0);
-    const cpx<double> bv = ld(b, e), rv = ld(r, e);
-    const double s = (double)sym[e % ncplx];
-    p[e] = mk<T>((T)(s * rv.x), (T)(s * rv.y));
-    v[0] += w * (bv.x * bv.x + bv.y * bv.y);
-    const double r2 = rv.x * rv.x + rv.y * rv.y;
-    v[1] += w * r2;
-    v[2] += w * s * r2;
+__global__ void __launch_bounds__(kRedThreads) k_cg_init(Ix ix, const cpx<T>* __restrict__ b,
+                                                         const cpx<T>* __restrict__ r, cpx<T>* __restrict__ p,
+                                                         const T* __restrict__ sym, RedArgs ra) {
+  Acc<T> a0, a1, a2;
+  IX_LOOP(ix) {
+    const T w = pweight<T>(kx, ix.h0);
+    const cpx<T> bv = b[e], rv = r[e];
+    const T sv = sym[si];
+    p[e] = scal(rv, sv);
+    const T r2 = rv.x * rv.x + rv.y * rv.y;
+    a0.add(w * (bv.x * bv.x + bv.y * bv.y));
+    a1.add(w * r2);
+    a2.add(w * sv * r2);
   }
+  double v[3] = {a0.total(), a1.total(), a2.total()};
   double t[3];
   if (reduce_last<3>(v, ra.partials, ra.counter, t) && threadIdx.x == 0)
     epilogue<3>(EPI_INIT_CG, t, ra.ks, ra.hist, ra.tol, 0, 0);
@@ -321,19 +357,20 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_init(long long len, int h0, 
 
 // reduce [(u,v)_w] or [(u,v)_w, (v,v)_w]
 template <typename T, int NV>
-__global__ void __launch_bounds__(kRedThreads) k_dot(long long len, int h0, const cpx<T>* __restrict__ u,
+__global__ void __launch_bounds__(kRedThreads) k_dot(Ix ix, const cpx<T>* __restrict__ u,
                                                      const cpx<T>* __restrict__ v, int epi, RedArgs ra,
                                                      const int* done) {
   if (*done) return;
-  double a[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) a[i] = 0.0;
-  GRID_STRIDE(e, len) {
-    const double w = wgt(e, h0);
-    const cpx<double> uu = ld(u, e), vv = ld(v, e);
-    a[0] += w * (uu.x * vv.x + uu.y * vv.y);
-    if (NV > 1) a[NV - 1] += w * (vv.x * vv.x + vv.y * vv.y);
+  Acc<T> a0, a1;
+  IX_LOOP(ix) {
+    const T w = pweight<T>(kx, ix.h0);
+    const cpx<T> uu = u[e], vv = v[e];
+    a0.add(w * (uu.x * vv.x + uu.y * vv.y));
+    if (NV > 1) a1.add(w * (vv.x * vv.x + vv.y * vv.y));
   }
+  double a[NV];
+  a[0] = a0.total();
+  if (NV > 1) a[NV - 1] = a1.total();
   double t[NV];
   if (reduce_last<NV>(a, ra.partials, ra.counter, t) && threadIdx.x == 0)
     epilogue<NV>(epi, t, ra.ks, ra.hist, ra.tol, 0, 0);
@@ -341,26 +378,26 @@ __global__ void __launch_bounds__(kRedThreads) k_dot(long long len, int h0, cons
 
 // CG: x += alpha p, r -= alpha q; reduce [rr, (r, S r)]
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_cg_update(long long len, int h0, long long ncplx,
-                                                           cpx<T>* __restrict__ x, const cpx<T>* __restrict__ p,
-                                                           cpx<T>* __restrict__ r, const cpx<T>* __restrict__ q,
-                                                           const T* __restrict__ sym, RedArgs ra) {
+__global__ void __launch_bounds__(kRedThreads) k_cg_update(Ix ix, cpx<T>* __restrict__ x,
+                                                           const cpx<T>* __restrict__ p, cpx<T>* __restrict__ r,
+                                                           const cpx<T>* __restrict__ q, const T* __restrict__ sym,
+                                                           RedArgs ra) {
   if (ra.ks->done) return;
-  const double al = ra.ks->alpha;
-  double v[2] = {0.0, 0.0};
-  GRID_STRIDE(e, len) {
-    const double w = wgt(e, h0);
-    const cpx<double> pv = ld(p, e), qv = ld(q, e);
-    cpx<double> xv = ld(x, e), rv = ld(r, e);
-    xv = mk<double>(fma(al, pv.x, xv.x), fma(al, pv.y, xv.y));
-    rv = mk<double>(fma(-al, qv.x, rv.x), fma(-al, qv.y, rv.y));
-    x[e] = mk<T>((T)xv.x, (T)xv.y);
-    const cpx<T> rt = mk<T>((T)rv.x, (T)rv.y);
-    r[e] = rt;
-    const double r2 = (double)rt.x * rt.x + (double)rt.y * rt.y;
-    v[0] += w * r2;
-    v[1] += w * (double)sym[e % ncplx] * r2;
+  const T al = (T)ra.ks->alpha;
+  Acc<T> a0, a1;
+  IX_LOOP(ix) {
+    const T w = pweight<T>(kx, ix.h0);
+    const cpx<T> pv = p[e], qv = q[e];
+    cpx<T> xv = x[e], rv = r[e];
+    xv = mk<T>(fma(al, pv.x, xv.x), fma(al, pv.y, xv.y));
+    rv = mk<T>(fma(-al, qv.x, rv.x), fma(-al, qv.y, rv.y));
+    x[e] = xv;
+    r[e] = rv;
+    const T r2 = rv.x * rv.x + rv.y * rv.y;
+    a0.add(w * r2);
+    a1.add(w * sym[si] * r2);
   }
+  double v[2] = {a0.total(), a1.total()};
   double t[2];
   if (reduce_last<2>(v, ra.partials, ra.counter, t) && threadIdx.x == 0)
     epilogue<2>(EPI_CG_UPDATE, t, ra.ks, ra.hist, ra.tol, 0, 0);
@@ -368,35 +405,36 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(long long len, int h0
 
 // CG: p = S r + beta p
 template <typename T>
-__global__ void k_cg_p(long long len, long long ncplx, cpx<T>* __restrict__ p, const cpx<T>* __restrict__ r,
-                       const T* __restrict__ sym, const KState* ks) {
+__global__ void k_cg_p(Ix ix, cpx<T>* __restrict__ p, const cpx<T>* __restrict__ r, const T* __restrict__ sym,
+                       const KState* ks) {
   if (ks->done) return;
-  const double be = ks->beta;
-  GRID_STRIDE(e, len) {
-    const double s = (double)sym[e % ncplx];
-    const cpx<double> rv = ld(r, e), pv = ld(p, e);
-    p[e] = mk<T>((T)fma(be, pv.x, s * rv.x), (T)fma(be, pv.y, s * rv.y));
+  const T be = (T)ks->beta;
+  IX_LOOP(ix) {
+    const T sv = sym[si];
+    const cpx<T> rv = r[e], pv = p[e];
+    p[e] = mk<T>(fma(be, pv.x, sv * rv.x), fma(be, pv.y, sv * rv.y));
   }
 }
 
 // RMR / GMRES start: reduce [bb, rr] or [rr]
 template <typename T, int NV>
-__global__ void __launch_bounds__(kRedThreads) k_norms(long long len, int h0, const cpx<T>* __restrict__ b,
+__global__ void __launch_bounds__(kRedThreads) k_norms(Ix ix, const cpx<T>* __restrict__ b,
                                                        const cpx<T>* __restrict__ r, int epi, RedArgs ra,
                                                        const int* done) {
   if (done && *done) return;
-  double v[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) v[i] = 0.0;
-  GRID_STRIDE(e, len) {
-    const double w = wgt(e, h0);
-    const cpx<double> rv = ld(r, e);
+  Acc<T> a0, a1;
+  IX_LOOP(ix) {
+    const T w = pweight<T>(kx, ix.h0);
+    const cpx<T> rv = r[e];
     if (NV == 2) {
-      const cpx<double> bv = ld(b, e);
-      v[0] += w * (bv.x * bv.x + bv.y * bv.y);
+      const cpx<T> bv = b[e];
+      a0.add(w * (bv.x * bv.x + bv.y * bv.y));
     }
-    v[NV - 1] += w * (rv.x * rv.x + rv.y * rv.y);
+    a1.add(w * (rv.x * rv.x + rv.y * rv.y));
   }
+  double v[NV];
+  if (NV == 2) v[0] = a0.total();
+  v[NV - 1] = a1.total();
   double t[NV];
   if (reduce_last<NV>(v, ra.partials, ra.counter, t) && threadIdx.x == 0)
     epilogue<NV>(epi, t, ra.ks, ra.hist, ra.tol, 0, 0);
@@ -404,25 +442,24 @@ __global__ void __launch_bounds__(kRedThreads) k_norms(long long len, int h0, co
 
 // RMR: x += alpha S r, r -= alpha w; reduce [rr]
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_rmr_update(long long len, int h0, long long ncplx,
-                                                            cpx<T>* __restrict__ x, cpx<T>* __restrict__ r,
+__global__ void __launch_bounds__(kRedThreads) k_rmr_update(Ix ix, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r,
                                                             const cpx<T>* __restrict__ wv, const T* __restrict__ sym,
                                                             RedArgs ra) {
   if (ra.ks->done) return;
-  const double al = ra.ks->alpha;
-  double v[1] = {0.0};
-  GRID_STRIDE(e, len) {
-    const double w = wgt(e, h0);
-    const double s = (double)sym[e % ncplx];
-    const cpx<double> wq = ld(wv, e);
-    cpx<double> xv = ld(x, e), rv = ld(r, e);
-    xv = mk<double>(fma(al * s, rv.x, xv.x), fma(al * s, rv.y, xv.y));
-    rv = mk<double>(fma(-al, wq.x, rv.x), fma(-al, wq.y, rv.y));
-    x[e] = mk<T>((T)xv.x, (T)xv.y);
-    const cpx<T> rt = mk<T>((T)rv.x, (T)rv.y);
-    r[e] = rt;
-    v[0] += w * ((double)rt.x * rt.x + (double)rt.y * rt.y);
+  const T al = (T)ra.ks->alpha;
+  Acc<T> a0;
+  IX_LOOP(ix) {
+    const T w = pweight<T>(kx, ix.h0);
+    const T as = al * sym[si];
+    const cpx<T> wq = wv[e];
+    cpx<T> xv = x[e], rv = r[e];
+    xv = mk<T>(fma(as, rv.x, xv.x), fma(as, rv.y, xv.y));
+    rv = mk<T>(fma(-al, wq.x, rv.x), fma(-al, wq.y, rv.y));
+    x[e] = xv;
+    r[e] = rv;
+    a0.add(w * (rv.x * rv.x + rv.y * rv.y));
   }
+  double v[1] = {a0.total()};
   double t[1];
   if (reduce_last<1>(v, ra.partials, ra.counter, t) && threadIdx.x == 0)
     epilogue<1>(EPI_RMR_UPDATE, t, ra.ks, ra.hist, ra.tol, 0, 0);
@@ -430,61 +467,63 @@ __global__ void __launch_bounds__(kRedThreads) k_rmr_update(long long len, int h
 
 // GMRES: dst = src / beta0 (first basis vector) or src / H[j+1,j] (next)
 template <typename T>
-__global__ void k_gm_scale(long long len, cpx<T>* __restrict__ dst, const cpx<T>* __restrict__ src, const KState* ks,
+__global__ void k_gm_scale(Ix ix, cpx<T>* __restrict__ dst, const cpx<T>* __restrict__ src, const KState* ks,
                            int first) {
   if (ks->cycle_done) return;
-  const double s = 1.0 / (first ? ks->beta0 : ks->ww);
-  GRID_STRIDE(e, len) {
-    const cpx<double> v = ld(src, e);
-    dst[e] = mk<T>((T)(v.x * s), (T)(v.y * s));
-  }
+  const T s = (T)(1.0 / (first ? ks->beta0 : ks->ww));
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ix.len; e += gridDim.x * blockDim.x)
+    dst[e] = scal(src[e], s);
 }
 
 // GMRES: h[off + i] = (w, V_{off+i})_w for i < nv (<= 8)
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_gm_mdot(long long len, int h0, const cpx<T>* __restrict__ w,
+__global__ void __launch_bounds__(kRedThreads) k_gm_mdot(Ix ix, const cpx<T>* __restrict__ w,
                                                          const cpx<T>* __restrict__ V, int off, int nv, int epi, int j,
                                                          RedArgs ra) {
   if (ra.ks->cycle_done) return;
-  double a[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) a[i] = 0.0;
-  GRID_STRIDE(e, len) {
-    const double wt = wgt(e, h0);
-    const cpx<double> wv = ld(w, e);
+  Acc<T> a[8];
+  IX_LOOP(ix) {
+    const T wt = pweight<T>(kx, ix.h0);
+    const cpx<T> wv = w[e];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       if (i < nv) {
-        const cpx<double> vv = ld(V + (size_t)(off + i) * len, e);
-        a[i] += wt * (wv.x * vv.x + wv.y * vv.y);
+        const cpx<T> vv = V[(size_t)(off + i) * ix.len + e];
+        a[i].add(wt * (wv.x * vv.x + wv.y * vv.y));
       }
     }
   }
+  double v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = a[i].total();
   double t[8];
-  if (reduce_last<8>(a, ra.partials, ra.counter, t) && threadIdx.x == 0)
+  if (reduce_last<8>(v, ra.partials, ra.counter, t) && threadIdx.x == 0)
     epilogue<8>(epi, t, ra.ks, ra.hist, ra.tol, off, j);
 }
 
 // GMRES: w -= sum_{i<=j} h_i V_i (h = h1 or h2); with_norm: reduce [(w,w)] -> EPI_GM_NORM
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_gm_maxpy(long long len, int h0, cpx<T>* __restrict__ w,
+__global__ void __launch_bounds__(kRedThreads) k_gm_maxpy(Ix ix, cpx<T>* __restrict__ w,
                                                           const cpx<T>* __restrict__ V, int j, int which, int with_norm,
                                                           RedArgs ra) {
   if (ra.ks->cycle_done) return;
+  __shared__ T hs[kMaxRestart + 1];
   const double* h = which ? ra.ks->h2 : ra.ks->h1;
-  double v[1] = {0.0};
-  GRID_STRIDE(e, len) {
-    cpx<double> wv = ld(w, e);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) hs[i] = (T)h[i];
+  __syncthreads();
+  Acc<T> a0;
+  IX_LOOP(ix) {
+    cpx<T> wv = w[e];
     for (int i = 0; i <= j; ++i) {
-      const double c = h[i];
-      const cpx<double> vv = ld(V + (size_t)i * len, e);
-      wv = mk<double>(fma(-c, vv.x, wv.x), fma(-c, vv.y, wv.y));
+      const T c = hs[i];
+      const cpx<T> vv = V[(size_t)i * ix.len + e];
+      wv = mk<T>(fma(-c, vv.x, wv.x), fma(-c, vv.y, wv.y));
     }
-    const cpx<T> wt = mk<T>((T)wv.x, (T)wv.y);
-    w[e] = wt;
-    v[0] += wgt(e, h0) * ((double)wt.x * wt.x + (double)wt.y * wt.y);
+    w[e] = wv;
+    a0.add(pweight<T>(kx, ix.h0) * (wv.x * wv.x + wv.y * wv.y));
   }
   if (!with_norm) return;
+  double v[1] = {a0.total()};
   double t[1];
   if (reduce_last<1>(v, ra.partials, ra.counter, t) && threadIdx.x == 0)
     epilogue<1>(EPI_GM_NORM, t, ra.ks, ra.hist, ra.tol, 0, j);
@@ -503,20 +542,23 @@ __global__ void k_gm_solve(KState* ks) {
 
 // GMRES: x += S sum_{i<k} y_i V_i
 template <typename T>
-__global__ void k_gm_update(long long len, long long ncplx, cpx<T>* __restrict__ x, const cpx<T>* __restrict__ V,
-                            const T* __restrict__ sym, const KState* ks) {
+__global__ void k_gm_update(Ix ix, cpx<T>* __restrict__ x, const cpx<T>* __restrict__ V, const T* __restrict__ sym,
+                            const KState* ks) {
   if (ks->done) return;
+  __shared__ T ys[kMaxRestart];
   const int k = ks->k;
-  GRID_STRIDE(e, len) {
-    double ax = 0.0, ay = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = (T)ks->y[i];
+  __syncthreads();
+  IX_LOOP(ix) {
+    T ax = T(0), ay = T(0);
     for (int i = 0; i < k; ++i) {
-      const cpx<double> vv = ld(V + (size_t)i * len, e);
-      ax = fma(ks->y[i], vv.x, ax);
-      ay = fma(ks->y[i], vv.y, ay);
+      const cpx<T> vv = V[(size_t)i * ix.len + e];
+      ax = fma(ys[i], vv.x, ax);
+      ay = fma(ys[i], vv.y, ay);
     }
-    const double s = (double)sym[e % ncplx];
-    const cpx<double> xv = ld(x, e);
-    x[e] = mk<T>((T)fma(s, ax, xv.x), (T)fma(s, ay, xv.y));
+    const T sv = sym[si];
+    const cpx<T> xv = x[e];
+    x[e] = mk<T>(fma(sv, ax, xv.x), fma(sv, ay, xv.y));
   }
 }
 
@@ -570,6 +612,17 @@ __global__ void k_project(GridDesc g, int ncomp, cpx<T>* v) {
   v[(long long)c * g.ncplx + e] = mk<T>(T(0), T(0));
 }
 
+static inline Ix mkix(long long len, int h0, long long nc, int blocks, int threads) {
+  const long long S = (long long)blocks * threads;
+  Ix ix;
+  ix.len = (int)len;
+  ix.h0 = h0;
+  ix.nc = (int)nc;
+  ix.sh = (int)(S % h0);
+  ix.sn = (int)(S % nc);
+  return ix;
+}
+
 static inline int ew_blocks(long long len) {
   return (int)std::max<long long>(1, std::min<long long>((len + 255) / 256, 8 * 1024));
 }
@@ -600,8 +653,9 @@ void spec_project(const vd_grid* G, int ncomp, void* v, cudaStream_t st) {
 template <typename T>
 double spec_norm2_host(const SpecSystem& sys, const void* v, const KWork& kw, cudaStream_t st) {
   RedArgs ra{kw.ks, kw.partials, kw.counter, kw.hist, 0.0};
-  { k_norms<T, 1><<<red_blocks(sys.len), kRedThreads, 0, st>>>(sys.len, sys.h0, nullptr, (const cpx<T>*)v, EPI_NORM, ra,
-                                                            nullptr); count_launch(); }
+  const int rb = red_blocks(sys.len);
+  const Ix ix = mkix(sys.len, sys.h0, sys.G->g.ncplx, rb, kRedThreads);
+  { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ix, nullptr, (const cpx<T>*)v, EPI_NORM, ra, nullptr); count_launch(); }
   double rr = 0.0;
   cudaMemcpyAsync(&rr, &kw.ks->rr, sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
@@ -642,6 +696,8 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
   const T* sym = (const T*)sys.sym;
   const int rb = red_blocks(len);
   const int eb = ew_blocks(len);
+  const Ix ixr = mkix(len, h0, nc, rb, kRedThreads);
+  const Ix ixe = mkix(len, h0, nc, eb, 256);
   RedArgs ra{kw.ks, kw.partials, kw.counter, kw.hist, o.tol};
   int* done = &kw.ks->done;
   int* cdone = &kw.ks->cycle_done;
@@ -673,14 +729,14 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
       sys.apply(sys, X, q, false, nullptr, st);
       { k_sub<T><<<eb, 256, 0, st>>>(len, B, q, r, nullptr); count_launch(); }
     }
-    { k_cg_init<T><<<rb, kRedThreads, 0, st>>>(len, h0, nc, B, r, p, sym, ra); count_launch(); }
+    { k_cg_init<T><<<rb, kRedThreads, 0, st>>>(ixr, B, r, p, sym, ra); count_launch(); }
     int it = 0;
     for (;;) {
       for (int c = 0; c < check && it < o.maxit; ++c, ++it) {
         sys.apply(sys, p, q, false, done, st);
-        { k_dot<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, p, q, EPI_CG_ALPHA, ra, done); count_launch(); }
-        { k_cg_update<T><<<rb, kRedThreads, 0, st>>>(len, h0, nc, X, p, r, q, sym, ra); count_launch(); }
-        { k_cg_p<T><<<eb, 256, 0, st>>>(len, nc, p, r, sym, kw.ks); count_launch(); }
+        { k_dot<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, p, q, EPI_CG_ALPHA, ra, done); count_launch(); }
+        { k_cg_update<T><<<rb, kRedThreads, 0, st>>>(ixr, X, p, r, q, sym, ra); count_launch(); }
+        { k_cg_p<T><<<eb, 256, 0, st>>>(ixe, p, r, sym, kw.ks); count_launch(); }
       }
       vd_status e = read_head(kw, &hd, st);
       if (e != VD_OK) return e;
@@ -695,13 +751,13 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
       sys.apply(sys, X, w, false, nullptr, st);
       { k_sub<T><<<eb, 256, 0, st>>>(len, B, w, r, nullptr); count_launch(); }
     }
-    { k_norms<T, 2><<<rb, kRedThreads, 0, st>>>(len, h0, B, r, EPI_INIT_RMR, ra, nullptr); count_launch(); }
+    { k_norms<T, 2><<<rb, kRedThreads, 0, st>>>(ixr, B, r, EPI_INIT_RMR, ra, nullptr); count_launch(); }
     int it = 0;
     for (;;) {
       for (int c = 0; c < check && it < o.maxit; ++c, ++it) {
         sys.apply(sys, r, w, true, done, st);
-        { k_dot<T, 2><<<rb, kRedThreads, 0, st>>>(len, h0, r, w, EPI_RMR_ALPHA, ra, done); count_launch(); }
-        { k_rmr_update<T><<<rb, kRedThreads, 0, st>>>(len, h0, nc, X, r, w, sym, ra); count_launch(); }
+        { k_dot<T, 2><<<rb, kRedThreads, 0, st>>>(ixr, r, w, EPI_RMR_ALPHA, ra, done); count_launch(); }
+        { k_rmr_update<T><<<rb, kRedThreads, 0, st>>>(ixr, X, r, w, sym, ra); count_launch(); }
       }
       vd_status e = read_head(kw, &hd, st);
       if (e != VD_OK) return e;
@@ -710,7 +766,7 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
   } else {
     cpx<T>* V = vb;
     cpx<T>* w = vb + (size_t)(m + 1) * len;
-    { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, nullptr, B, EPI_BB, ra, nullptr); count_launch(); }
+    { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, nullptr, B, EPI_BB, ra, nullptr); count_launch(); }
     for (int cycle = 0;; ++cycle) {
       // r = b - A x into V_0 (unnormalised), then V_0 /= beta
       if (cycle == 0 && o.x_zero) {
@@ -719,19 +775,19 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
         sys.apply(sys, X, w, false, done, st);
         { k_sub<T><<<eb, 256, 0, st>>>(len, B, w, V, done); count_launch(); }
       }
-      { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, nullptr, V, EPI_GM_BETA, ra, done); count_launch(); }
-      { k_gm_scale<T><<<eb, 256, 0, st>>>(len, V, V, kw.ks, 1); count_launch(); }
+      { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, nullptr, V, EPI_GM_BETA, ra, done); count_launch(); }
+      { k_gm_scale<T><<<eb, 256, 0, st>>>(ixe, V, V, kw.ks, 1); count_launch(); }
       for (int j = 0; j < m; ++j) {
         cpx<T>* Vj = V + (size_t)j * len;
         sys.apply(sys, Vj, w, true, cdone, st);
         for (int pass = 0; pass < 2; ++pass) {
           for (int off = 0; off <= j; off += 8) {
             const int nv = std::min(8, j + 1 - off);
-            { k_gm_mdot<T><<<rb, kRedThreads, 0, st>>>(len, h0, w, V, off, nv, pass ? EPI_GM_H2 : EPI_GM_H1, j, ra); count_launch(); }
+            { k_gm_mdot<T><<<rb, kRedThreads, 0, st>>>(ixr, w, V, off, nv, pass ? EPI_GM_H2 : EPI_GM_H1, j, ra); count_launch(); }
           }
-          { k_gm_maxpy<T><<<rb, kRedThreads, 0, st>>>(len, h0, w, V, j, pass, pass, ra); count_launch(); }
+          { k_gm_maxpy<T><<<rb, kRedThreads, 0, st>>>(ixr, w, V, j, pass, pass, ra); count_launch(); }
         }
-        { k_gm_scale<T><<<eb, 256, 0, st>>>(len, V + (size_t)(j + 1) * len, w, kw.ks, 0); count_launch(); }
+        { k_gm_scale<T><<<eb, 256, 0, st>>>(ixe, V + (size_t)(j + 1) * len, w, kw.ks, 0); count_launch(); }
         if ((j + 1) % check == 0 || j + 1 == m) {
           vd_status e = read_head(kw, &hd, st);
           if (e != VD_OK) return e;
@@ -739,7 +795,7 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
         }
       }
       { k_gm_solve<<<1, 1, 0, st>>>(kw.ks); count_launch(); }
-      { k_gm_update<T><<<eb, 256, 0, st>>>(len, nc, X, V, sym, kw.ks); count_launch(); }
+      { k_gm_update<T><<<eb, 256, 0, st>>>(ixe, X, V, sym, kw.ks); count_launch(); }
       { k_gm_close<<<1, 1, 0, st>>>(kw.ks); count_launch(); }
       vd_status e = read_head(kw, &hd, st);
       if (e != VD_OK) return e;
@@ -748,7 +804,7 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
         // one more loop head forms the true residual and sets the final status
         sys.apply(sys, X, w, false, done, st);
         { k_sub<T><<<eb, 256, 0, st>>>(len, B, w, V, done); count_launch(); }
-        { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(len, h0, nullptr, V, EPI_GM_BETA, ra, done); count_launch(); }
+        { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, nullptr, V, EPI_GM_BETA, ra, done); count_launch(); }
         e = read_head(kw, &hd, st);
         if (e != VD_OK) return e;
         break;

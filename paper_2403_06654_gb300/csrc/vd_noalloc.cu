@@ -128,6 +128,8 @@ extern "C" vd_status vd_apply_pressure_noalloc(int ndim, const int n[3], const d
   for (int j = 0; j < 3; ++j) {
     G.L[j] = (j < ndim) ? L[j] : 1.0;
     g.kfac[j] = 2.0 * 3.14159265358979323846 / G.L[j];
+    g.kfac_dd[j][0] = (float)g.kfac[j];
+    g.kfac_dd[j][1] = (float)(g.kfac[j] - (double)g.kfac_dd[j][0]);
   }
   bool ok = na_plan(nn[0] / 2, &g.px);
   int off = 0;

@@ -7,8 +7,10 @@
 #include "vd_internal.h"
 #include "vd_prof.h"
 #include "vd_fft.cuh"
+#include "vd_dd.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace vd {
 
@@ -29,6 +31,7 @@ static inline Xf mkxf(int src, int dst, int pre, int post, bool first, bool last
 
 template <typename T>
 static const void* twtab(const vd_grid* G) {
+  if (std::is_same<T, dd>::value) return G->tw_dd;
   return (sizeof(T) == 8) ? G->tw_d : G->tw_f;
 }
 
@@ -113,9 +116,10 @@ void inv_transform(const vd_grid* G, const cpx<T>* in, const Mult& mu, T* out, c
 // pressure operator
 // ---------------------------------------------------------------------------------------
 
+// conv: the float-pair instantiation reads `in` and writes `out` as double fields
 template <typename T>
-void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, const T* rinv_s,
-                         cpx<T>* tmp, const int* done, cudaStream_t st) {
+static void pressure_impl(const vd_grid* G, const void* in, void* out, const T* symarr, const void* rinv_s,
+                          cpx<T>* tmp, const int* done, cudaStream_t st, int conv) {
   const GridDesc& g = G->g;
   const int S = symarr ? MUL_SYM : 0;
   const size_t nc = (size_t)g.ncplx;
@@ -132,6 +136,8 @@ void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const 
     X.scale = 0.5;
     X.symarr = symarr;
     X.done = done;
+    X.conv_in = conv;
+    X.conv_out = conv;
     launch_xpass<T>(X, g, tw, st);
     return;
   }
@@ -149,6 +155,7 @@ void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const 
     P.symarr = symarr;
     P.done = done;
     P.axis = 1;
+    P.conv_in = conv;
     launch_axis<T>(P, +1, g, tw, st);
     // x fused: T0 <- i kx R2C(w C2R(i kx T0)), T1 <- R2C(w C2R(T1))
     XProg X{};
@@ -174,6 +181,7 @@ void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const 
     Q.out[0] = out;
     Q.done = done;
     Q.axis = 1;
+    Q.conv_out = conv;
     launch_axis<T>(Q, -1, g, tw, st);
     return;
   }
@@ -190,6 +198,7 @@ void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const 
     P.symarr = symarr;
     P.done = done;
     P.axis = 2;
+    P.conv_in = conv;
     launch_axis<T>(P, +1, g, tw, st);
   }
   // P2, y inverse: T2 = F_y^-1(i ky T0), T0 <- F_y^-1(T0), T1 <- F_y^-1(T1)
@@ -253,8 +262,20 @@ void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const 
     P.out[0] = out;
     P.done = done;
     P.axis = 2;
+    P.conv_out = conv;
     launch_axis<T>(P, -1, g, tw, st);
   }
+}
+
+template <typename T>
+void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, const T* rinv_s,
+                         cpx<T>* tmp, const int* done, cudaStream_t st) {
+  pressure_impl<T>(G, in, out, symarr, rinv_s, tmp, done, st, 0);
+}
+
+void apply_pressure_spec_dd(const vd_grid* G, const cpx<double>* in, cpx<double>* out, void* tmp, const int* done,
+                            cudaStream_t st) {
+  pressure_impl<dd>(G, in, out, nullptr, G->rinv_s_dd, reinterpret_cast<cpx<dd>*>(tmp), done, st, 1);
 }
 
 // ---------------------------------------------------------------------------------------

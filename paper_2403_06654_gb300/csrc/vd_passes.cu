@@ -1,22 +1,67 @@
 // Transform pass kernels: strided-axis passes (y, z) and the fused contiguous x pass.
 #include "vd_passes.cuh"
 #include "vd_fft.cuh"
+#include "vd_dd.cuh"
 #include "vd_prof.h"
 
 #include <cmath>
+#include <type_traits>
 
 #include <algorithm>
 
 namespace vd {
 
+// Element load / store of a pass.  The float-pair instantiation (T = dd) may read its input
+// from, and write its output to, double fields (the Krylov vectors), converting on the fly.
+template <typename T>
+__device__ __forceinline__ cpx<T> ld_el(const void* p, int conv, int go) {
+  if constexpr (std::is_same<T, dd>::value) {
+    if (conv) {
+      const cpx<double> v = reinterpret_cast<const cpx<double>*>(p)[go];
+      return mk<T>(dd_from_double(v.x), dd_from_double(v.y));
+    }
+  }
+  return reinterpret_cast<const cpx<T>*>(p)[go];
+}
+template <typename T>
+__device__ __forceinline__ void st_el(void* p, int conv, int go, cpx<T> v, bool first) {
+  if constexpr (std::is_same<T, dd>::value) {
+    if (conv) {
+      cpx<double>* q = reinterpret_cast<cpx<double>*>(p) + go;
+      const cpx<double> d = mk<double>(dd_to_double(v.x), dd_to_double(v.y));
+      *q = first ? d : (*q + d);
+      return;
+    }
+  }
+  cpx<T>* q = reinterpret_cast<cpx<T>*>(p) + go;
+  *q = first ? v : (*q + v);
+}
+
+// kfac[axis] and a scale factor in the arithmetic type (float-pair values come pre-split)
+template <typename T>
+__device__ __forceinline__ T kfac_t(const GridDesc& g, int a) {
+  if constexpr (std::is_same<T, dd>::value) return dd(g.kfac_dd[a][0], g.kfac_dd[a][1]);
+  else return (T)g.kfac[a];
+}
+template <typename T>
+__device__ __forceinline__ T scale_t(double s, float hi, float lo) {
+  if constexpr (std::is_same<T, dd>::value) return dd(hi, lo);
+  else return (T)s;
+}
+
 constexpr int kThreads = 256;
 template <typename T>
-constexpr int kEPT = (sizeof(T) == 8) ? 8 : 16;   // tile elements per thread
+constexpr int kEPT = (sizeof(T) == 4) ? 16 : 8;   // tile elements per thread (float: 16; double, dd: 8)
 
 static inline int tile_width(int n, int ept) {
   int w = 1;
   while (w < 64 && (2 * w) * n <= ept * kThreads) w *= 2;
   return w;
+}
+static inline int ilog2(int v) {
+  int l = 0;
+  while ((1 << (l + 1)) <= v) ++l;
+  return l;
 }
 static inline int lines_per_cta(int m, int ept) {
   int l = 1;
@@ -29,134 +74,261 @@ static inline int lines_per_cta(int m, int ept) {
 // ---------------------------------------------------------------------------------------
 
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_axis(const AxisProg P, const GridDesc g,
-                                                   const cpx<T>* __restrict__ twg, int W) {
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 ? 2 : 3)) k_axis(const AxisProg P, const GridDesc g,
+                                                   const cpx<T>* __restrict__ twg, int lw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int EPT = kEPT<T>;
+  if (P.done && *P.done) return;
   const int axis = P.axis;
   const FftPlan& pl = (axis == 2) ? g.pz : g.py;
   const int n = pl.n;
+  const int W = 1 << lw;
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* A = tw + n;
   cpx<T>* B = A + W * n;
   const int tid = threadIdx.x;
   for (int j = tid; j < n; j += kThreads) tw[j] = twg[pl.tw_off + j];
 
-  long long line_stride, inner_n, outer_stride;
+  // field offsets fit in 32 bits (ncplx < 2^31 is checked when the grid is created)
+  int line_stride, inner_n, outer_stride;
   if (axis == 2) {
-    line_stride = (long long)g.n1 * g.h0;
+    line_stride = g.n1 * g.h0;
     inner_n = line_stride;
     outer_stride = 0;
   } else {
     line_stride = g.h0;
     inner_n = g.h0;
-    outer_stride = (long long)g.n1 * g.h0;
+    outer_stride = g.n1 * g.h0;
   }
-  const long long tiles = (inner_n + W - 1) / W;
-  const long long o = blockIdx.x / tiles;
-  const long long col0 = (blockIdx.x % tiles) * W;
-  const int tile_elems = W * n;
+  const int tiles = (inner_n + W - 1) >> lw;
+  const int o = blockIdx.x / tiles;
+  const int col0 = (blockIdx.x - o * tiles) << lw;
+  // this thread's line (column) and its first element / butterfly
+  const int w = tid & (W - 1);
+  const int ib = tid >> lw;
+  const int istep = kThreads >> lw;
+  const int col = col0 + w;
+  const bool colok = col < inner_n;
+  const int g0 = o * outer_stride + col + ib * line_stride;   // offset of element ib
+  const int gstep = istep * line_stride;                      // offset step between the thread's elements
   const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr);
-  if (P.done && *P.done) return;
-
-  // global offset of tile element e (or -1 outside the field)
-  auto gofs = [&](int e) -> long long {
-    const int i = e / W;
-    const long long col = col0 + (e - i * W);
-    return (e < tile_elems && col < inner_n) ? (o * outer_stride + i * line_stride + col) : -1;
-  };
-  // real factor of a multiplier at tile element e (global offset go >= 0)
-  auto mult = [&](int flags, int e, long long go, T base) -> T {
-    const int i = e / W;
-    const long long col = col0 + (e - i * W);
-    const T ka = (T)g.kfac[axis] * (T)freq_tilde(i, n);
+  // |k~|^2 of the axes other than the pass axis (constant for the line)
+  T kperp2;
+  if (axis == 2) {
+    const int kyi = col / g.h0;
+    const int kxi = col - kyi * g.h0;
+    const T kx = kfac_t<T>(g, 0) * (T)freq_tilde(kxi, g.n0);
+    const T ky = kfac_t<T>(g, 1) * (T)freq_tilde(kyi, g.n1);
+    kperp2 = kx * kx + ky * ky;
+  } else {
+    const T kx = kfac_t<T>(g, 0) * (T)freq_tilde(col, g.n0);
+    kperp2 = kx * kx;
+    if (g.ndim == 3) {
+      const T kz = kfac_t<T>(g, 2) * (T)freq_tilde(o, g.n2);
+      kperp2 += kz * kz;
+    }
+  }
+  const T kfa = kfac_t<T>(g, axis);
+  // real factor of a multiplier at line element i (global offset go)
+  auto mult = [&](int flags, int i, int go, T base) -> T {
+    const T ka = kfa * (T)freq_tilde(i, n);
     T c = base;
     if (flags & MUL_IK) c *= ka;
     if (flags & MUL_IK2) c *= -ka * ka;
     if (flags & MUL_SYM) c *= symarr[go];
-    if (flags & MUL_NEGK2) {
-      T kk = ka * ka;
-      if (axis == 2) {
-        const int kyi = (int)(col / g.h0);
-        const int kxi = (int)(col - (long long)kyi * g.h0);
-        const T kx = (T)g.kfac[0] * (T)freq_tilde(kxi, g.n0);
-        const T ky = (T)g.kfac[1] * (T)freq_tilde(kyi, g.n1);
-        kk += kx * kx + ky * ky;
-      } else {
-        const T kx = (T)g.kfac[0] * (T)freq_tilde((int)col, g.n0);
-        kk += kx * kx;
-        if (g.ndim == 3) {
-          const T kz = (T)g.kfac[2] * (T)freq_tilde((int)o, g.n2);
-          kk += kz * kz;
-        }
-      }
-      c *= -kk;
-    }
+    if (flags & MUL_NEGK2) c *= -(ka * ka + kperp2);
     return c;
   };
 
-  cpx<T> acc[EPT];
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) acc[q] = mk<T>(T(0), T(0));
-
+  // Each transform writes its result straight to out[dst]; a transform that accumulates
+  // (first == 0) reads back the partial sum of the same elements, written earlier by this
+  // very thread, so no synchronisation is needed and the partial stays in L2.
+  const int nq = (n - ib + istep - 1) / istep;   // elements of this thread in its line
   for (int t = 0; t < P.nxf; ++t) {
     const Xf xf = P.xf[t];
-    const cpx<T>* __restrict__ src = reinterpret_cast<const cpx<T>*>(P.in[xf.src]);
-    const T scale = (T)xf.scale;
+    const void* src = P.in[xf.src];
+    void* dst = P.out[xf.dst];
+    const int cin = (P.conv_in >> xf.src) & 1, cout = (P.conv_out >> xf.dst) & 1;
+    const T scale = scale_t<T>(xf.scale, xf.scale_hi, xf.scale_lo);
     if (xf.nofft) {
-#pragma unroll
-      for (int q = 0; q < EPT; ++q) {
-        const int e = tid + q * kThreads;
-        const long long go = gofs(e);
-        cpx<T> v = mk<T>(T(0), T(0));
-        if (go >= 0) {
-          v = scal(src[go], mult(xf.pre, e, go, scale));
+      if (colok) {
+#pragma unroll 4
+        for (int q = 0; q < nq; ++q) {
+          const int i = ib + q * istep;
+          const int go = g0 + q * gstep;
+          cpx<T> v = scal(ld_el<T>(src, cin, go), mult(xf.pre, i, go, scale));
           if (xf.pre & MUL_IK) v = mul_i(v);
-        }
-        acc[q] = xf.first ? v : (acc[q] + v);
-      }
-    } else {
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < EPT; ++q) {
-        const int e = tid + q * kThreads;
-        if (e < tile_elems) {
-          const long long go = gofs(e);
-          cpx<T> v = mk<T>(T(0), T(0));
-          if (go >= 0) {
-            v = src[go];
-            if (xf.pre) {
-              v = scal(v, mult(xf.pre, e, go, T(1)));
-              if (xf.pre & MUL_IK) v = mul_i(v);
-            }
-          }
-          A[e] = v;
+          st_el<T>(dst, cout, go, v, xf.first);
         }
       }
-      cpx<T>* res = fft_pingpong<T, S, true>(A, B, W, 1, W, pl, tw, tid, kThreads);
-#pragma unroll
-      for (int q = 0; q < EPT; ++q) {
-        const int e = tid + q * kThreads;
-        cpx<T> v = mk<T>(T(0), T(0));
-        const long long go = gofs(e);
-        if (go >= 0) {
-          v = res[e];
-          if (xf.post) {
-            v = scal(v, mult(xf.post, e, go, scale));
-            if (xf.post & MUL_IK) v = mul_i(v);
-          } else {
-            v = scal(v, scale);
-          }
+      continue;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int q = 0; q < nq; ++q) {
+      const int i = ib + q * istep;
+      const int go = g0 + q * gstep;
+      cpx<T> v = mk<T>(T(0), T(0));
+      if (colok) v = ld_el<T>(src, cin, go);
+      if (xf.pre) {
+        v = scal(v, mult(xf.pre, i, go, T(1)));
+        if (xf.pre & MUL_IK) v = mul_i(v);
+      }
+      A[i * W + w] = v;
+    }
+    cpx<T>* res = fft_lines<T, S>(A, B, W, w, ib, istep, pl, tw);
+    if (colok) {
+#pragma unroll 4
+      for (int q = 0; q < nq; ++q) {
+        const int i = ib + q * istep;
+        const int go = g0 + q * gstep;
+        cpx<T> v = res[i * W + w];
+        if (xf.post) {
+          v = scal(v, mult(xf.post, i, go, scale));
+          if (xf.post & MUL_IK) v = mul_i(v);
+        } else {
+          v = scal(v, scale);
         }
-        acc[q] = xf.first ? v : (acc[q] + v);
+        st_el<T>(dst, cout, go, v, xf.first);
       }
     }
-    if (xf.last) {
-      cpx<T>* __restrict__ dst = reinterpret_cast<cpx<T>*>(P.out[xf.dst]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// strided axis pass, register-resident four-step transform for n = N1 * N2 (N1 = C * N2)
+//
+// With n = N2 n1 + n2 and k = k1 + N1 k2:
+//   X[k1 + N1 k2] = sum_{n2} W_{N2}^{n2 k2} W_n^{n2 k1} sum_{n1} x[N2 n1 + n2] W_{N1}^{n1 k1}.
+// Thread n2 of a line holds x[N2 n1 + n2] (the rows it loads), transforms over n1 in
+// registers, multiplies by W_n^{n2 k1}, and one shared-memory transpose hands column k1 to
+// thread k1 mod N2, which transforms over n2 and stores rows k1 + N1 k2.  16 lines (columns)
+// per block, line stride n + 1 in shared memory (conflict-free transposes).
+// ---------------------------------------------------------------------------------------
+
+constexpr int kRLines = 16;
+
+template <typename T, int S, int N1, int N2>
+__global__ void __launch_bounds__(kRLines * N2, (sizeof(T) == 4 ? 2 : 1)) k_axis_r(const AxisProg P, const GridDesc g,
+                                                        const cpx<T>* __restrict__ twg) {
+  constexpr int N = N1 * N2;
+  constexpr int C = N1 / N2;
+  constexpr int LS = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (P.done && *P.done) return;
+  const int axis = P.axis;
+  const FftPlan& pl = (axis == 2) ? g.pz : g.py;
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* Y = tw + N;
+  const int tid = threadIdx.x;
+  for (int j = tid; j < N; j += kRLines * N2) tw[j] = twg[pl.tw_off + j];
+
+  int line_stride, inner_n, outer_stride;
+  if (axis == 2) {
+    line_stride = g.n1 * g.h0;
+    inner_n = line_stride;
+    outer_stride = 0;
+  } else {
+    line_stride = g.h0;
+    inner_n = g.h0;
+    outer_stride = g.n1 * g.h0;
+  }
+  const int tiles = (inner_n + kRLines - 1) / kRLines;
+  const int o = blockIdx.x / tiles;
+  const int col0 = (blockIdx.x - o * tiles) * kRLines;
+  const int w = tid % kRLines;
+  const int t = tid / kRLines;   // n2 in the first step
+  const int col = col0 + w;
+  const bool colok = col < inner_n;
+  const int gbase = o * outer_stride + col;
+  const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr);
+  T kperp2;
+  if (axis == 2) {
+    const int kyi = col / g.h0;
+    const int kxi = col - kyi * g.h0;
+    const T kx = kfac_t<T>(g, 0) * (T)freq_tilde(kxi, g.n0);
+    const T ky = kfac_t<T>(g, 1) * (T)freq_tilde(kyi, g.n1);
+    kperp2 = kx * kx + ky * ky;
+  } else {
+    const T kx = kfac_t<T>(g, 0) * (T)freq_tilde(col, g.n0);
+    kperp2 = kx * kx;
+    if (g.ndim == 3) {
+      const T kz = kfac_t<T>(g, 2) * (T)freq_tilde(o, g.n2);
+      kperp2 += kz * kz;
+    }
+  }
+  const T kfa = kfac_t<T>(g, axis);
+  auto mult = [&](int flags, int i, int go, T base) -> T {
+    const T ka = kfa * (T)freq_tilde(i, N);
+    T c = base;
+    if (flags & MUL_IK) c *= ka;
+    if (flags & MUL_IK2) c *= -ka * ka;
+    if (flags & MUL_SYM) c *= symarr[go];
+    if (flags & MUL_NEGK2) c *= -(ka * ka + kperp2);
+    return c;
+  };
+  cpx<T>* Yl = Y + w * LS;
+
+  for (int x = 0; x < P.nxf; ++x) {
+    const Xf xf = P.xf[x];
+    const void* src = P.in[xf.src];
+    void* dst = P.out[xf.dst];
+    const int cin = (P.conv_in >> xf.src) & 1, cout = (P.conv_out >> xf.dst) & 1;
+    const T scale = scale_t<T>(xf.scale, xf.scale_hi, xf.scale_lo);
+    if (xf.nofft) {
+      if (colok) {
 #pragma unroll
-      for (int q = 0; q < EPT; ++q) {
-        const long long go = gofs(tid + q * kThreads);
-        if (go >= 0) dst[go] = acc[q];
+        for (int j = 0; j < N1; ++j) {
+          const int i = N2 * j + t;
+          const int go = gbase + i * line_stride;
+          cpx<T> v = scal(ld_el<T>(src, cin, go), mult(xf.pre, i, go, scale));
+          if (xf.pre & MUL_IK) v = mul_i(v);
+          st_el<T>(dst, cout, go, v, xf.first);
+        }
+      }
+      continue;
+    }
+    cpx<T> u[N1];
+#pragma unroll
+    for (int j = 0; j < N1; ++j) {
+      const int i = N2 * j + t;
+      const int go = gbase + i * line_stride;
+      u[j] = colok ? ld_el<T>(src, cin, go) : mk<T>(T(0), T(0));
+      if (xf.pre) {
+        u[j] = scal(u[j], mult(xf.pre, i, go, T(1)));
+        if (xf.pre & MUL_IK) u[j] = mul_i(u[j]);
+      }
+    }
+    dftR<T, S, N1>(u);
+#pragma unroll
+    for (int k1 = 1; k1 < N1; ++k1) {
+      const cpx<T> wv = tw[t * k1];
+      u[k1] = (S < 0) ? cmul(u[k1], wv) : cmulc(u[k1], wv);
+    }
+    __syncthreads();   // the previous transform has finished reading Y
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) Yl[t * N1 + k1] = u[k1];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int k1 = t + N2 * c;
+      cpx<T> v[N2];
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) v[n2] = Yl[n2 * N1 + k1];
+      dftR<T, S, N2>(v);
+      if (colok) {
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+          const int i = k1 + N1 * k2;
+          const int go = gbase + i * line_stride;
+          cpx<T> vv = v[k2];
+          if (xf.post) {
+            vv = scal(vv, mult(xf.post, i, go, scale));
+            if (xf.post & MUL_IK) vv = mul_i(vv);
+          } else {
+            vv = scal(vv, scale);
+          }
+          st_el<T>(dst, cout, go, vv, xf.first);
+        }
       }
     }
   }
@@ -168,11 +340,13 @@ __global__ void __launch_bounds__(kThreads) k_axis(const AxisProg P, const GridD
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_xpass(const XProg P, const GridDesc g,
-                                                    const cpx<T>* __restrict__ twg, int LPC) {
+                                                    const cpx<T>* __restrict__ twg, int llpc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (P.done && *P.done) return;
   const int m = g.n0 / 2;
   const int h0 = g.h0;
   const int ls = m + 1;
+  const int LPC = 1 << llpc;
   cpx<T>* twm = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* pk = twm + m;
   cpx<T>* A = pk + (m + 2);   // keep 16-byte alignment (m even)
@@ -184,83 +358,89 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const XProg P, const GridDes
   const long long nlines = (long long)g.n1 * g.n2;
   const long long line0 = (long long)blockIdx.x * LPC;
   const int nl = (int)min((long long)LPC, nlines - line0);
-  const T kfx = (T)g.kfac[0];
-  const T scale = (T)P.scale;
-  const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr) + line0 * h0;
-  if (P.done && *P.done) return;
+  // this thread's line and its position in the line
+  const int ltpl = 8 - llpc;   // log2(threads per line), kThreads = 256
+  const int TPL = 1 << ltpl;
+  const int line = tid >> ltpl;
+  const int t0 = tid & (TPL - 1);
+  const bool lok = line < nl;
+  const int lofs = line * ls;
+  const T kfx = kfac_t<T>(g, 0);
+  const T scale = scale_t<T>(P.scale, P.scale_hi, P.scale_lo);
+  const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr) + (line0 + line) * h0;
 
   for (int c = 0; c < P.ncomp; ++c) {
     cpx<T>* res;
     __syncthreads();
     if (P.mode == 1) {
-      const cpx<T>* __restrict__ src = reinterpret_cast<const cpx<T>*>(P.in[c]) + line0 * m;
-      for (int e = tid; e < nl * m; e += kThreads) {
-        const int line = e / m, j = e - line * m;
-        A[line * ls + j] = src[e];
-      }
-      res = fft_pingpong<T, -1, false>(A, B, 1, ls, nl, g.px, twm, tid, kThreads);
+      const cpx<T>* __restrict__ src = reinterpret_cast<const cpx<T>*>(P.in[c]) + (line0 + line) * m;
+      if (lok)
+        for (int j = t0; j < m; j += TPL) A[lofs + j] = src[j];
+      res = fft_lines<T, -1>(A, B, 1, lofs, t0, TPL, g.px, twm);
     } else {
-      const cpx<T>* __restrict__ src = reinterpret_cast<const cpx<T>*>(P.in[c]) + line0 * h0;
+      const int cin = (P.conv_in >> c) & 1;
+      const int lbase = (int)((line0 + line) * h0);
       const int pre = P.pre[c];
-      for (int e = tid; e < nl * h0; e += kThreads) {
-        const int line = e / h0, k = e - line * h0;
-        cpx<T> v = src[e];
-        if (pre) {
-          const T kx = kfx * (T)freq_tilde(k, g.n0);
-          T cc = T(1);
-          if (pre & MUL_IK) cc *= kx;
-          if (pre & MUL_SYM) cc *= symarr[e];
-          if (pre & (MUL_NEGK2 | MUL_IK2)) cc *= -kx * kx;
-          v = scal(v, cc);
-          if (pre & MUL_IK) v = mul_i(v);
+      if (lok) {
+        for (int k = t0; k < h0; k += TPL) {
+          cpx<T> v = ld_el<T>(P.in[c], cin, lbase + k);
+          if (pre) {
+            const T kx = kfx * (T)freq_tilde(k, g.n0);
+            T cc = T(1);
+            if (pre & MUL_IK) cc *= kx;
+            if (pre & MUL_SYM) cc *= symarr[k];
+            if (pre & (MUL_NEGK2 | MUL_IK2)) cc *= -kx * kx;
+            v = scal(v, cc);
+            if (pre & MUL_IK) v = mul_i(v);
+          }
+          B[lofs + k] = v;
         }
-        B[line * ls + k] = v;
       }
       __syncthreads();
       // pack the half spectrum into a length-m complex spectrum (inverse real transform)
-      for (int e = tid; e < nl * m; e += kThreads) {
-        const int line = e / m, k = e - line * m;
-        const cpx<T> X = B[line * ls + k];
-        const cpx<T> Xc = conjg(B[line * ls + (m - k)]);
-        A[line * ls + k] = (X + Xc) + mul_i(cmulc(X - Xc, pk[k]));
-      }
-      res = fft_pingpong<T, +1, false>(A, B, 1, ls, nl, g.px, twm, tid, kThreads);
-      if (P.mode == 2) {
-        cpx<T>* __restrict__ dst = reinterpret_cast<cpx<T>*>(P.out[c]) + line0 * m;
-        for (int e = tid; e < nl * m; e += kThreads) {
-          const int line = e / m, j = e - line * m;
-          dst[e] = scal(res[line * ls + j], scale);
+      if (lok) {
+        for (int k = t0; k < m; k += TPL) {
+          const cpx<T> X = B[lofs + k];
+          const cpx<T> Xc = conjg(B[lofs + (m - k)]);
+          A[lofs + k] = (X + Xc) + mul_i(cmulc(X - Xc, pk[k]));
         }
+      }
+      res = fft_lines<T, +1>(A, B, 1, lofs, t0, TPL, g.px, twm);
+      if (P.mode == 2) {
+        cpx<T>* __restrict__ dst = reinterpret_cast<cpx<T>*>(P.out[c]) + (line0 + line) * m;
+        if (lok)
+          for (int j = t0; j < m; j += TPL) dst[j] = scal(res[lofs + j], scale);
         continue;
       }
-      if (P.wfield) {
-        const cpx<T>* __restrict__ wf = reinterpret_cast<const cpx<T>*>(P.wfield) + line0 * m;
-        for (int e = tid; e < nl * m; e += kThreads) {
-          const int line = e / m, j = e - line * m;
-          const cpx<T> z = res[line * ls + j];
-          const cpx<T> w = wf[e];
-          res[line * ls + j] = mk<T>(z.x * w.x, z.y * w.y);
+      if (P.wfield && lok) {
+        const cpx<T>* __restrict__ wf = reinterpret_cast<const cpx<T>*>(P.wfield) + (line0 + line) * m;
+        for (int j = t0; j < m; j += TPL) {
+          const cpx<T> z = res[lofs + j];
+          const cpx<T> wv = wf[j];
+          res[lofs + j] = mk<T>(z.x * wv.x, z.y * wv.y);
         }
       }
       cpx<T>* other = (res == A) ? B : A;
-      res = fft_pingpong<T, -1, false>(res, other, 1, ls, nl, g.px, twm, tid, kThreads);
+      res = fft_lines<T, -1>(res, other, 1, lofs, t0, TPL, g.px, twm);
     }
     // unpack the length-m spectrum into the half spectrum of the real line
-    cpx<T>* __restrict__ dst = reinterpret_cast<cpx<T>*>(P.out[c]) + line0 * h0;
+    const int cout = (P.conv_out >> c) & 1;
+    const int obase = (int)((line0 + line) * h0);
     const int post = P.post[c];
-    for (int e = tid; e < nl * h0; e += kThreads) {
-      const int line = e / h0, k = e - line * h0;
-      const cpx<T> Z = res[line * ls + (k == m ? 0 : k)];
-      const cpx<T> Zc = conjg(res[line * ls + (k == 0 ? 0 : m - k)]);
-      cpx<T> X = (Z + Zc) - mul_i(cmul(Z - Zc, pk[k]));
-      T cc = scale;
-      const T kx = kfx * (T)freq_tilde(k, g.n0);
-      if (post & MUL_IK) cc *= kx;
-      if (post & MUL_SYM) cc *= symarr[e];
-      if (post & (MUL_NEGK2 | MUL_IK2)) cc *= -kx * kx;
-      X = scal(X, cc);
-      if (post & MUL_IK) X = mul_i(X);
-      dst[e] = X;
+    if (lok) {
+      for (int k = t0; k < h0; k += TPL) {
+        const cpx<T> Z = res[lofs + (k == m ? 0 : k)];
+        const cpx<T> Zc = conjg(res[lofs + (k == 0 ? 0 : m - k)]);
+        cpx<T> X = (Z + Zc) - mul_i(cmul(Z - Zc, pk[k]));
+        T cc = scale;
+        const T kx = kfx * (T)freq_tilde(k, g.n0);
+        if (post & MUL_IK) cc *= kx;
+        if (post & MUL_SYM) cc *= symarr[k];
+        if (post & (MUL_NEGK2 | MUL_IK2)) cc *= -kx * kx;
+        X = scal(X, cc);
+        if (post & MUL_IK) X = mul_i(X);
+        st_el<T>(P.out[c], cout, obase + k, X, true);
+      }
     }
   }
 }
@@ -292,8 +472,28 @@ static void set_axis_attr(size_t smem) {
   }
 }
 
+template <typename T, int S, int N1, int N2>
+static void launch_axis_r(const AxisProg& P, const GridDesc& g, const cpx<T>* tw, long long inner_n,
+                          long long outer_n, cudaStream_t st) {
+  const long long blocks = outer_n * ((inner_n + kRLines - 1) / kRLines);
+  const size_t smem = sizeof(cpx<T>) * (size_t)(N1 * N2 + kRLines * (N1 * N2 + 1));
+  static size_t done = 0;
+  if (smem > 48 * 1024 && smem > done) {
+    cudaFuncSetAttribute(k_axis_r<T, S, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    done = smem;
+  }
+  k_axis_r<T, S, N1, N2><<<(unsigned)blocks, kRLines * N2, smem, st>>>(P, g, tw);
+}
+
+static void split_scale(double s, float* hi, float* lo) {
+  *hi = (float)s;
+  *lo = (float)(s - (double)*hi);
+}
+
 template <typename T>
-void launch_axis(const AxisProg& P, int dir, const GridDesc& g, const void* tw, cudaStream_t st) {
+void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw, cudaStream_t st) {
+  AxisProg P = P0;
+  for (int t = 0; t < P.nxf; ++t) split_scale(P.xf[t].scale, &P.xf[t].scale_hi, &P.xf[t].scale_lo);
   const int n = (P.axis == 2) ? g.pz.n : g.py.n;
   const int W = tile_width(n, kEPT<T>);
   long long inner_n, outer_n;
@@ -320,18 +520,34 @@ void launch_axis(const AxisProg& P, int dir, const GridDesc& g, const void* tw, 
   const double fb = (double)g.ncplx * sizeof(cpx<T>);
   const double bytes = (__builtin_popcount(inmask) + __builtin_popcount(outmask)) * fb + (sym ? g.ncplx * sizeof(T) : 0);
   const double flops = (double)nfft * (double)g.ncplx * 5.0 * std::log2((double)n);
-  ProfScope ps(sizeof(T) == 8 ? PC_AXIS64 : PC_AXIS32, st, bytes, flops);
+  ProfScope ps(std::is_same<T, dd>::value ? PC_AXISDD : (sizeof(T) == 8 ? PC_AXIS64 : PC_AXIS32), st, bytes,
+               flops);
+  if constexpr (std::is_same<T, float>::value) {
+    // register-resident four-step kernel for the common lengths
+    if (n == 256 || n == 128) {
+      if (n == 256) {
+        if (dir < 0) launch_axis_r<T, -1, 16, 16>(P, g, twp, inner_n, outer_n, st);
+        else launch_axis_r<T, +1, 16, 16>(P, g, twp, inner_n, outer_n, st);
+      } else {
+        if (dir < 0) launch_axis_r<T, -1, 16, 8>(P, g, twp, inner_n, outer_n, st);
+        else launch_axis_r<T, +1, 16, 8>(P, g, twp, inner_n, outer_n, st);
+      }
+      return;
+    }
+  }
   if (dir < 0) {
     set_axis_attr<T, -1>(smem);
-    k_axis<T, -1><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, W);
+    k_axis<T, -1><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, ilog2(W));
   } else {
     set_axis_attr<T, +1>(smem);
-    k_axis<T, +1><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, W);
+    k_axis<T, +1><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, ilog2(W));
   }
 }
 
 template <typename T>
-void launch_xpass(const XProg& P, const GridDesc& g, const void* tw, cudaStream_t st) {
+void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream_t st) {
+  XProg P = P0;
+  split_scale(P.scale, &P.scale_hi, &P.scale_lo);
   const int m = g.n0 / 2;
   const int L = lines_per_cta(m, kEPT<T>);
   const long long nlines = (long long)g.n1 * g.n2;
@@ -355,15 +571,20 @@ void launch_xpass(const XProg& P, const GridDesc& g, const void* tw, cudaStream_
   bool sym = false;
   for (int c = 0; c < P.ncomp; ++c) sym = sym || ((P.pre[c] | P.post[c]) & MUL_SYM);
   if (sym) bytes += (double)g.ncplx * sizeof(T);
-  ProfScope ps(sizeof(T) == 8 ? PC_XPASS64 : PC_XPASS32, st, bytes, flops);
-  k_xpass<T><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, reinterpret_cast<const cpx<T>*>(tw), L);
+  ProfScope ps(std::is_same<T, dd>::value ? PC_XPASSDD : (sizeof(T) == 8 ? PC_XPASS64 : PC_XPASS32), st, bytes,
+               flops);
+  k_xpass<T><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, reinterpret_cast<const cpx<T>*>(tw), ilog2(L));
 }
 
+template void launch_axis<dd>(const AxisProg&, int, const GridDesc&, const void*, cudaStream_t);
+template void launch_xpass<dd>(const XProg&, const GridDesc&, const void*, cudaStream_t);
 template void launch_axis<double>(const AxisProg&, int, const GridDesc&, const void*, cudaStream_t);
 template void launch_axis<float>(const AxisProg&, int, const GridDesc&, const void*, cudaStream_t);
 template void launch_xpass<double>(const XProg&, const GridDesc&, const void*, cudaStream_t);
 template void launch_xpass<float>(const XProg&, const GridDesc&, const void*, cudaStream_t);
 template size_t axis_smem_bytes<double>(const GridDesc&, int);
+template size_t axis_smem_bytes<dd>(const GridDesc&, int);
+template size_t xpass_smem_bytes<dd>(const GridDesc&);
 template size_t axis_smem_bytes<float>(const GridDesc&, int);
 template size_t xpass_smem_bytes<double>(const GridDesc&);
 template size_t xpass_smem_bytes<float>(const GridDesc&);

@@ -25,6 +25,9 @@ constexpr int kMaxXf = 16;
 constexpr int kMaxIO = 16;
 
 // One transform of an axis pass: out[dst] (=|+=) scale * post( FFT( pre( in[src] ) ) ).
+// Every transform writes out[dst] (an accumulating one adds to what an earlier transform of
+// the same program wrote there), so a program must not read a buffer after one of its
+// transforms has overwritten it; `last` is informative only.
 // MUL_SYM reads the program's symbol array at the element's spectral index, so it is only
 // meaningful where every axis is in spectral space (first inverse / last forward pass).
 struct Xf {
@@ -34,6 +37,7 @@ struct Xf {
   int8_t nofft;   // skip the transform (pure diagonal multiply)
   int8_t pad;
   double scale;
+  float scale_hi, scale_lo;   // float-pair split of scale (set on the host)
 };
 
 struct AxisProg {
@@ -44,6 +48,8 @@ struct AxisProg {
   const void* symarr;   // real symbol array (ncplx, same layout as the spectral fields)
   const int* done;      // if non-null and *done != 0 the kernel returns at once
   int axis;   // 1 = y, 2 = z
+  int conv_in;          // float-pair kernels: bit i set -> in[i] holds doubles (split on load)
+  int conv_out;         // float-pair kernels: bit i set -> out[i] holds doubles (summed on store)
 };
 
 // Fused x pass: for every component c, in[c] (half spectrum) -> pre -> inverse real FFT ->
@@ -59,8 +65,11 @@ struct XProg {
   int post[4];
   const void* wfield;
   double scale;
+  float scale_hi, scale_lo;   // float-pair split of scale (set by launch_xpass)
   const void* symarr;
   const int* done;
+  int conv_in;          // float-pair kernels: bit c set -> in[c] holds doubles
+  int conv_out;         // float-pair kernels: bit c set -> out[c] holds doubles
 };
 
 template <typename T>

@@ -16,7 +16,9 @@ enum ProfClass : int {
   PC_XPASS64 = 2,  // contiguous x pass, double
   PC_XPASS32 = 3,  // contiguous x pass, float
   PC_OTHER = 4,    // reductions, vector updates, pointwise kernels
-  PC_N = 5
+  PC_AXISDD = 5,   // strided y/z pass, float-pair
+  PC_XPASSDD = 6,  // contiguous x pass, float-pair
+  PC_N = 7
 };
 
 void count_launch();

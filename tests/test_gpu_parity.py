@@ -245,3 +245,26 @@ def test_large_axis_2d_config2_shape():
     phi = inputs.smooth_random_field(n, L, 19, kmax=20)
     got = N(G.apply("pressure", T(phi)))
     assert relmax(got, op.apply_pressure(case.rho, phi, g)) < 1e-11
+
+
+@pytest.mark.parametrize("solver", ["cg", "gmres", "rmr"])
+@pytest.mark.parametrize("n,L", [((48, 40, 32), (2 * math.pi,) * 3), ((256,), (2 * math.pi,)),
+                                 ((64, 48), (2 * math.pi, 1.0))])
+def test_mixed_dd_residual_matches_fp64(solver, n, L):
+    """Refinement residual in float-pair arithmetic (~2^-48): the returned solution's double
+    residual, recomputed here with the double operator, must also meet the tolerance, and the
+    solution must match the FP64 oracle within kappa * tol."""
+    g = sp.Grid(n, L)
+    rho = inputs.slab_density(g.n, g.L, 2.0, g.ndim - 1, 0.5 * g.L[-1], 0.5 * g.L[-1], 4 * g.L[-1] / g.n[-1])
+    f = inputs.smooth_random_field(g.n, g.L, 21, kmax=5)
+    G = vd.Grid(n, L)
+    G.set_density(T(rho))
+    tol = 1e-10
+    x, info = G.solve("pressure", solver, T(f), tol=tol, max_it=500, precision="mixed_dd")
+    assert info["status"] == "converged" and info["relres_true"] <= tol
+    fb = sp.project_range(f, g)
+    r64 = fb - N(G.apply("pressure", x))
+    assert np.linalg.norm(r64) / np.linalg.norm(fb) <= 1.05 * tol
+    A, M = op.pressure_system(rho, g)
+    ref = sv.solve(solver, A, M, fb, tol=1e-12, maxit=500)
+    assert rel2(N(x), ref.x) < 2.5 * tol
