@@ -50,7 +50,7 @@ typedef enum {
   VD_ERR_CUDA = 3,           /* a CUDA runtime call failed; message has the CUDA error */
   VD_ERR_NOT_CONVERGED = 4,  /* max_it reached above tol (x holds the last iterate) */
   VD_ERR_BREAKDOWN = 5,      /* Krylov breakdown (zero curvature / zero search direction) */
-  VD_ERR_DIVERGED = 6,       /* monitored residual grew above 1e3 x the best value */
+  VD_ERR_DIVERGED = 6,       /* RMR: monitored residual grew above 1e3 x the best value */
   VD_ERR_NONFINITE = 7,      /* NaN or Inf met in a reduction */
   VD_ERR_NO_DENSITY = 8      /* an operator was used before vd_density_set */
 } vd_status;
@@ -172,6 +172,46 @@ vd_status vd_divergence(const vd_grid* grid, const double* u, double* out, void*
 /* out_j = D_j phi (spectral gradient; out holds ndim components). */
 vd_status vd_gradient(const vd_grid* grid, const double* phi, double* out, void* ws, size_t ws_bytes,
                       vd_stream stream);
+
+/*
+ * Semi-implicit second-order step (Sec. 2: Eqs. VDINSE.num.mass.proj, num.momentum.proj,
+ * Lrho.num, num.proj, num.gradp.update) on the grid: Crank--Nicolson + Adams--Bashforth 2
+ * mass update (diagonal in Fourier), rho_h = (rho^{n+1} + rho^n)/2, velocity predictor solved
+ * with V~_{rho_h} (a = dt/(2 Re); warm start u^n), pressure increment L~_{rho_h} phi = div(u*) / dt
+ * (warm start: previous phi), projection u = u* - dt grad(phi) / rho_h and the gradient-form
+ * pressure update.  Readings: Euler for the first step's advection terms; gravity along
+ * gravity_axis as the periodic body force -Fr^-1 (1 - <rho_h>/rho_h) (the paper's -Fr^-1 e_z
+ * with its mean weight removed); -1 for no gravity.
+ * Memory: vd_flow_bytes() device bytes (caller-owned) hold the state (rho, u, grad p, phi,
+ * Adams--Bashforth history), temporaries, the density data and the solve workspace.  The
+ * flow owns its grid's density slot while it steps (vd_flow_step calls vd_density_set).
+ * State fields are physical, layout as for every other call; u and grad p have ndim
+ * components.  vd_flow_step synchronises the stream (density checks, convergence flags).
+ * Errors as in vd_solve; a solve that stops unconverged is reported in info and in the
+ * returned status, the step is still completed.
+ */
+typedef struct vd_flow vd_flow;
+typedef struct {
+  double Re, Sc, Fr;
+  int gravity_axis;   /* axis of gravity (0..ndim-1), -1 for none */
+  int vel_solver;     /* VD_SOLVER_GMRES or VD_SOLVER_RMR */
+  int pres_solver;    /* any vd_solver */
+  double tol;         /* relative tolerance of both solves */
+  int max_it, restart, precision;
+} vd_flow_params;
+typedef struct {
+  int vel_iters, pres_iters, vel_status, pres_status;
+  double vel_relres, pres_relres;   /* true relative residuals of the two solves */
+} vd_step_info;
+size_t vd_flow_bytes(vd_grid* grid, const vd_flow_params* params);
+vd_status vd_flow_create(vd_grid* grid, const vd_flow_params* params, void* mem, size_t bytes, vd_flow** out);
+vd_status vd_flow_destroy(vd_flow* flow);
+/* initial state: rho (n points) and u (ndim fields); grad p and phi start at 0 */
+vd_status vd_flow_set_state(vd_flow* flow, const double* rho, const double* u, vd_stream stream);
+/* copy out any of rho, u, grad p, phi (null pointers are skipped) */
+vd_status vd_flow_get_state(const vd_flow* flow, double* rho, double* u, double* gradp, double* phi,
+                            vd_stream stream);
+vd_status vd_flow_step(vd_flow* flow, double dt, vd_step_info* info, vd_stream stream);
 
 /*
  * out = L~_rho(in) for callers that cannot allocate device memory (the paper has no

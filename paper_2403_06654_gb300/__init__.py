@@ -49,6 +49,18 @@ class vd_solve_params(ctypes.Structure):
                 ("check_every", ctypes.c_int)]
 
 
+class vd_flow_params(ctypes.Structure):
+    _fields_ = [("Re", ctypes.c_double), ("Sc", ctypes.c_double), ("Fr", ctypes.c_double),
+                ("gravity_axis", ctypes.c_int), ("vel_solver", ctypes.c_int), ("pres_solver", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_it", ctypes.c_int), ("restart", ctypes.c_int),
+                ("precision", ctypes.c_int)]
+
+
+class vd_step_info(ctypes.Structure):
+    _fields_ = [("vel_iters", ctypes.c_int), ("pres_iters", ctypes.c_int), ("vel_status", ctypes.c_int),
+                ("pres_status", ctypes.c_int), ("vel_relres", ctypes.c_double), ("pres_relres", ctypes.c_double)]
+
+
 class vd_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("status", ctypes.c_int),
                 ("relres", ctypes.c_double), ("relres_true", ctypes.c_double),
@@ -77,6 +89,12 @@ _SIGS = {
     "vd_divergence": (_I, [_P, _P, _P, _P, _SZ, _P]),
     "vd_gradient": (_I, [_P, _P, _P, _P, _SZ, _P]),
     "vd_apply_pressure_noalloc": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), _P, _P, _P, _P]),
+    "vd_flow_bytes": (_SZ, [_P, ctypes.POINTER(vd_flow_params)]),
+    "vd_flow_create": (_I, [_P, ctypes.POINTER(vd_flow_params), _P, _SZ, ctypes.POINTER(_P)]),
+    "vd_flow_destroy": (_I, [_P]),
+    "vd_flow_set_state": (_I, [_P, _P, _P, _P]),
+    "vd_flow_get_state": (_I, [_P, _P, _P, _P, _P, _P]),
+    "vd_flow_step": (_I, [_P, ctypes.c_double, ctypes.POINTER(vd_step_info), _P]),
     "vd_launch_count": (ctypes.c_longlong, []),
     "vd_profile_enable": (_I, [_I]),
     "vd_profile_reset": (_I, []),
@@ -187,6 +205,37 @@ def vd_apply_pressure_noalloc(n, L, rho, x, out, stream=None):
     nn = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - nd)))
     ll = (ctypes.c_double * 3)(*(list(L) + [1.0] * (3 - nd)))
     _check(lib().vd_apply_pressure_noalloc(nd, nn, ll, _ptr(rho), _ptr(x), _ptr(out), _stream(stream)))
+
+
+def vd_flow_bytes(h, params):
+    return int(lib().vd_flow_bytes(h, ctypes.byref(params)))
+
+
+def vd_flow_create(h, params, mem):
+    f = ctypes.c_void_p()
+    _check(lib().vd_flow_create(h, ctypes.byref(params), _ptr(mem), mem.numel(), ctypes.byref(f)))
+    return f
+
+
+def vd_flow_destroy(f):
+    _check(lib().vd_flow_destroy(f))
+
+
+def vd_flow_set_state(f, rho, u, stream=None):
+    _check(lib().vd_flow_set_state(f, _ptr(rho), _ptr(u), _stream(stream)))
+
+
+def vd_flow_get_state(f, rho=None, u=None, gradp=None, phi=None, stream=None):
+    p = lambda t: _ptr(t) if t is not None else None  # noqa: E731
+    _check(lib().vd_flow_get_state(f, p(rho), p(u), p(gradp), p(phi), _stream(stream)))
+
+
+def vd_flow_step(f, dt, info, stream=None):
+    """Returns the raw status (an unconverged solve is a result, not an error)."""
+    st = lib().vd_flow_step(f, ctypes.c_double(dt), ctypes.byref(info), _stream(stream))
+    if st in (VD_ERR_INVALID_ARG, VD_ERR_OOM, VD_ERR_CUDA, VD_ERR_NO_DENSITY):
+        _check(st)
+    return st
 
 
 def vd_launch_count():
@@ -346,3 +395,53 @@ class Grid:
         ws = self._workspace(16 * self.modes * 3 + 256)
         vd_gradient(self.h, phi, out, ws, stream)
         return out
+
+
+class Flow:
+    """Semi-implicit variable-density flow on a Grid (state on the device)."""
+
+    def __init__(self, grid: Grid, Re, Sc=1.0, Fr=1.0, gravity_axis=-1, vel_solver="rmr", pres_solver="gmres",
+                 tol=1e-10, max_it=200, restart=30, precision="fp64"):
+        import torch
+        self.grid = grid
+        self.params = vd_flow_params(Re=Re, Sc=Sc, Fr=Fr, gravity_axis=gravity_axis,
+                                     vel_solver=SOLVERS[vel_solver], pres_solver=SOLVERS[pres_solver], tol=tol,
+                                     max_it=max_it, restart=restart, precision=PRECISIONS[precision])
+        nb = vd_flow_bytes(grid.h, self.params)
+        if nb == 0:
+            raise VDError(VD_ERR_INVALID_ARG, lib().vd_last_error().decode())
+        self.mem = torch.empty(nb, dtype=torch.uint8, device=grid.device)
+        self.h = vd_flow_create(grid.h, self.params, self.mem)
+
+    def close(self):
+        if self.h:
+            vd_flow_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, rho, u, stream=None):
+        g = self.grid
+        vd_flow_set_state(self.h, g._field(rho, 0, "rho"), g._field(u, g.ndim, "u"), stream)
+
+    def state(self, stream=None):
+        import torch
+        g = self.grid
+        rho = torch.empty(g.shape, dtype=torch.float64, device=g.device)
+        u = torch.empty((g.ndim,) + g.shape, dtype=torch.float64, device=g.device)
+        gp = torch.empty_like(u)
+        phi = torch.empty_like(rho)
+        vd_flow_get_state(self.h, rho, u, gp, phi, stream)
+        return rho, u, gp, phi
+
+    def step(self, dt, stream=None):
+        info = vd_step_info()
+        st = vd_flow_step(self.h, dt, info, stream)
+        return {"status": STATUS_NAMES.get(st, st), "vel_iters": info.vel_iters, "pres_iters": info.pres_iters,
+                "vel_status": STATUS_NAMES.get(info.vel_status, info.vel_status),
+                "pres_status": STATUS_NAMES.get(info.pres_status, info.pres_status),
+                "vel_relres": info.vel_relres, "pres_relres": info.pres_relres}

@@ -179,7 +179,8 @@ __device__ void epilogue(int epi, const double (&t)[NV], KState* ks, double* his
         finish(ks, 0);
         return;
       }
-      if (rel > 1e3 * ks->best) {
+      // residual-growth divergence test: RMR only (CG's residual norm is not monotone)
+      if (epi == EPI_RMR_UPDATE && rel > 1e3 * ks->best) {
         finish(ks, VD_ERR_DIVERGED);
         return;
       }
