@@ -240,7 +240,8 @@ vd_status vd_apply_pressure_noalloc(int ndim, const int n[3], const double L[3],
  * and accumulate, per class, launches, elapsed ms, algorithmic bytes (every input and
  * output field once) and flops (5 n log2 n per complex line transform).  Classes:
  * 0 strided pass double, 1 strided pass float, 2 x pass double, 3 x pass float,
- * 5 strided pass float-pair, 6 x pass float-pair (4: unused).
+ * 5 strided pass float-pair, 6 x pass float-pair, 7 Krylov vector kernels on float vectors,
+ * 8 Krylov vector kernels on double vectors (4: unused).
  * vd_profile_read synchronises on the recorded events; vd_profile_reset clears the totals.
  */
 long long vd_launch_count(void);

@@ -250,7 +250,8 @@ def vd_profile_reset():
     _check(lib().vd_profile_reset())
 
 
-PROFILE_CLASSES = {0: "axis_f64", 1: "axis_f32", 2: "xpass_f64", 3: "xpass_f32", 5: "axis_dd", 6: "xpass_dd"}
+PROFILE_CLASSES = {0: "axis_f64", 1: "axis_f32", 2: "xpass_f64", 3: "xpass_f32", 5: "axis_dd", 6: "xpass_dd",
+                   7: "vec_f32", 8: "vec_f64"}
 
 
 def vd_profile_read(cls):

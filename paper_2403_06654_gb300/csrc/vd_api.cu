@@ -593,11 +593,15 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
   // the reduction ticket counter must start at zero (the workspace is uninitialised memory)
   VD_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned), st));
   fill_symbol<double>(G, symkind, opp ? opp->a : 0.0, L.sym, st);
-  // spectral right-hand side and initial guess
-  fwd_all(G, ncomp, b, L.bh, st);
+  // spectral right-hand side and initial guess (float-pair transforms in VD_PREC_MIXED_DD
+  // pressure solves, double otherwise)
+  const bool dd_io = prm->precision == VD_PREC_MIXED_DD && op == VD_OP_PRESSURE;
+  if (dd_io) fwd_transform_dd(G, b, L.bh, L.tmp, st);
+  else fwd_all(G, ncomp, b, L.bh, st);
   if (op == VD_OP_PRESSURE) spec_project<double>(G, 1, L.bh, st);
   if (prm->use_x0) {
-    fwd_all(G, ncomp, x, L.xh, st);
+    if (dd_io) fwd_transform_dd(G, x, L.xh, L.tmp, st);
+    else fwd_all(G, ncomp, x, L.xh, st);
     if (op == VD_OP_PRESSURE) spec_project<double>(G, 1, L.xh, st);
   } else {
     VD_CUDA(cudaMemsetAsync(L.xh, 0, sizeof(cpx<double>) * len, st));
@@ -694,7 +698,8 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
     if (info) info->hist_len = hlen;
   }
   // back to physical space
-  inv_all(G, ncomp, L.xh, x, L.tmp, st);
+  if (dd_io) inv_transform_dd(G, L.xh, x, L.tmp, st);
+  else inv_all(G, ncomp, L.xh, x, L.tmp, st);
   if (prm->precision == VD_PREC_FP64) {
     // true residual of the returned iterate
     const double bb = spec_norm2_host<double>(sys64, L.bh, kw, st);

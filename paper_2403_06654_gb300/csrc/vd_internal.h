@@ -82,6 +82,11 @@ void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const 
 void apply_pressure_spec_dd(const vd_grid* G, const cpx<double>* in, cpx<double>* out, void* tmp, const int* done,
                             cudaStream_t st);
 
+// Plain forward / inverse transforms with float-pair arithmetic (double fields in and out;
+// tmp: one spectral field of 16-byte elements).
+void fwd_transform_dd(const vd_grid* G, const double* in, cpx<double>* out, void* tmp, cudaStream_t st);
+void inv_transform_dd(const vd_grid* G, const cpx<double>* in, double* out, void* tmp, cudaStream_t st);
+
 // Velocity operator in spectral space: out_i = (S in)_i - a * F[rho^-1 (Lap u + Sc^-1 (...))]_i with u =
 // F^-1 (S in).  ncomp = ndim components stored back to back.  tmp: see velocity_tmp_fields().
 template <typename T>

@@ -638,7 +638,7 @@ void spec_axpy(long long len, double a, const void* x, void* y, cudaStream_t st)
 }
 template <typename T>
 void spec_sub(long long len, const void* b, const void* q, void* r, cudaStream_t st) {
-  { k_sub<T><<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<T>*)b, (const cpx<T>*)q, (cpx<T>*)r, nullptr); count_launch(); }
+  { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)3 * len * sizeof(cpx<T>), 0.0); k_sub<T><<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<T>*)b, (const cpx<T>*)q, (cpx<T>*)r, nullptr); }
 }
 void spec_d2f(long long len, const void* in, void* out, cudaStream_t st) {
   { k_d2f<<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<double>*)in, (cpx<float>*)out); count_launch(); }
@@ -656,7 +656,7 @@ double spec_norm2_host(const SpecSystem& sys, const void* v, const KWork& kw, cu
   RedArgs ra{kw.ks, kw.partials, kw.counter, kw.hist, 0.0};
   const int rb = red_blocks(sys.len);
   const Ix ix = mkix(sys.len, sys.h0, sys.G->g.ncplx, rb, kRedThreads);
-  { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ix, nullptr, (const cpx<T>*)v, EPI_NORM, ra, nullptr); count_launch(); }
+  { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)1 * sys.len * sizeof(cpx<T>), 0.0); k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ix, nullptr, (const cpx<T>*)v, EPI_NORM, ra, nullptr); }
   double rr = 0.0;
   cudaMemcpyAsync(&rr, &kw.ks->rr, sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
@@ -728,16 +728,16 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
       VD_CUDA(cudaMemcpyAsync(r, B, sizeof(cpx<T>) * len, cudaMemcpyDeviceToDevice, st));
     } else {
       sys.apply(sys, X, q, false, nullptr, st);
-      { k_sub<T><<<eb, 256, 0, st>>>(len, B, q, r, nullptr); count_launch(); }
+      { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)3 * len * sizeof(cpx<T>), 0.0); k_sub<T><<<eb, 256, 0, st>>>(len, B, q, r, nullptr); }
     }
-    { k_cg_init<T><<<rb, kRedThreads, 0, st>>>(ixr, B, r, p, sym, ra); count_launch(); }
+    { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)3 * len * sizeof(cpx<T>) + (double)nc * sizeof(T), 0.0); k_cg_init<T><<<rb, kRedThreads, 0, st>>>(ixr, B, r, p, sym, ra); }
     int it = 0;
     for (;;) {
       for (int c = 0; c < check && it < o.maxit; ++c, ++it) {
         sys.apply(sys, p, q, false, done, st);
-        { k_dot<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, p, q, EPI_CG_ALPHA, ra, done); count_launch(); }
-        { k_cg_update<T><<<rb, kRedThreads, 0, st>>>(ixr, X, p, r, q, sym, ra); count_launch(); }
-        { k_cg_p<T><<<eb, 256, 0, st>>>(ixe, p, r, sym, kw.ks); count_launch(); }
+        { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)2 * len * sizeof(cpx<T>), 0.0); k_dot<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, p, q, EPI_CG_ALPHA, ra, done); }
+        { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)6 * len * sizeof(cpx<T>) + (double)nc * sizeof(T), 0.0); k_cg_update<T><<<rb, kRedThreads, 0, st>>>(ixr, X, p, r, q, sym, ra); }
+        { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)3 * len * sizeof(cpx<T>) + (double)nc * sizeof(T), 0.0); k_cg_p<T><<<eb, 256, 0, st>>>(ixe, p, r, sym, kw.ks); }
       }
       vd_status e = read_head(kw, &hd, st);
       if (e != VD_OK) return e;
@@ -750,15 +750,15 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
       VD_CUDA(cudaMemcpyAsync(r, B, sizeof(cpx<T>) * len, cudaMemcpyDeviceToDevice, st));
     } else {
       sys.apply(sys, X, w, false, nullptr, st);
-      { k_sub<T><<<eb, 256, 0, st>>>(len, B, w, r, nullptr); count_launch(); }
+      { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)3 * len * sizeof(cpx<T>), 0.0); k_sub<T><<<eb, 256, 0, st>>>(len, B, w, r, nullptr); }
     }
-    { k_norms<T, 2><<<rb, kRedThreads, 0, st>>>(ixr, B, r, EPI_INIT_RMR, ra, nullptr); count_launch(); }
+    { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)2 * len * sizeof(cpx<T>), 0.0); k_norms<T, 2><<<rb, kRedThreads, 0, st>>>(ixr, B, r, EPI_INIT_RMR, ra, nullptr); }
     int it = 0;
     for (;;) {
       for (int c = 0; c < check && it < o.maxit; ++c, ++it) {
         sys.apply(sys, r, w, true, done, st);
-        { k_dot<T, 2><<<rb, kRedThreads, 0, st>>>(ixr, r, w, EPI_RMR_ALPHA, ra, done); count_launch(); }
-        { k_rmr_update<T><<<rb, kRedThreads, 0, st>>>(ixr, X, r, w, sym, ra); count_launch(); }
+        { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)2 * len * sizeof(cpx<T>), 0.0); k_dot<T, 2><<<rb, kRedThreads, 0, st>>>(ixr, r, w, EPI_RMR_ALPHA, ra, done); }
+        { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)5 * len * sizeof(cpx<T>) + (double)nc * sizeof(T), 0.0); k_rmr_update<T><<<rb, kRedThreads, 0, st>>>(ixr, X, r, w, sym, ra); }
       }
       vd_status e = read_head(kw, &hd, st);
       if (e != VD_OK) return e;
@@ -767,28 +767,28 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
   } else {
     cpx<T>* V = vb;
     cpx<T>* w = vb + (size_t)(m + 1) * len;
-    { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, nullptr, B, EPI_BB, ra, nullptr); count_launch(); }
+    { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)1 * len * sizeof(cpx<T>), 0.0); k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, nullptr, B, EPI_BB, ra, nullptr); }
     for (int cycle = 0;; ++cycle) {
       // r = b - A x into V_0 (unnormalised), then V_0 /= beta
       if (cycle == 0 && o.x_zero) {
         VD_CUDA(cudaMemcpyAsync(V, B, sizeof(cpx<T>) * len, cudaMemcpyDeviceToDevice, st));
       } else {
         sys.apply(sys, X, w, false, done, st);
-        { k_sub<T><<<eb, 256, 0, st>>>(len, B, w, V, done); count_launch(); }
+        { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)3 * len * sizeof(cpx<T>), 0.0); k_sub<T><<<eb, 256, 0, st>>>(len, B, w, V, done); }
       }
-      { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, nullptr, V, EPI_GM_BETA, ra, done); count_launch(); }
-      { k_gm_scale<T><<<eb, 256, 0, st>>>(ixe, V, V, kw.ks, 1); count_launch(); }
+      { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)1 * len * sizeof(cpx<T>), 0.0); k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, nullptr, V, EPI_GM_BETA, ra, done); }
+      { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)2 * len * sizeof(cpx<T>), 0.0); k_gm_scale<T><<<eb, 256, 0, st>>>(ixe, V, V, kw.ks, 1); }
       for (int j = 0; j < m; ++j) {
         cpx<T>* Vj = V + (size_t)j * len;
         sys.apply(sys, Vj, w, true, cdone, st);
         for (int pass = 0; pass < 2; ++pass) {
           for (int off = 0; off <= j; off += 8) {
             const int nv = std::min(8, j + 1 - off);
-            { k_gm_mdot<T><<<rb, kRedThreads, 0, st>>>(ixr, w, V, off, nv, pass ? EPI_GM_H2 : EPI_GM_H1, j, ra); count_launch(); }
+            { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)(nv + 1) * len * sizeof(cpx<T>), 0.0); k_gm_mdot<T><<<rb, kRedThreads, 0, st>>>(ixr, w, V, off, nv, pass ? EPI_GM_H2 : EPI_GM_H1, j, ra); }
           }
-          { k_gm_maxpy<T><<<rb, kRedThreads, 0, st>>>(ixr, w, V, j, pass, pass, ra); count_launch(); }
+          { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)(j + 3) * len * sizeof(cpx<T>), 0.0); k_gm_maxpy<T><<<rb, kRedThreads, 0, st>>>(ixr, w, V, j, pass, pass, ra); }
         }
-        { k_gm_scale<T><<<eb, 256, 0, st>>>(ixe, V + (size_t)(j + 1) * len, w, kw.ks, 0); count_launch(); }
+        { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)2 * len * sizeof(cpx<T>), 0.0); k_gm_scale<T><<<eb, 256, 0, st>>>(ixe, V + (size_t)(j + 1) * len, w, kw.ks, 0); }
         if ((j + 1) % check == 0 || j + 1 == m) {
           vd_status e = read_head(kw, &hd, st);
           if (e != VD_OK) return e;
@@ -796,7 +796,7 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
         }
       }
       { k_gm_solve<<<1, 1, 0, st>>>(kw.ks); count_launch(); }
-      { k_gm_update<T><<<eb, 256, 0, st>>>(ixe, X, V, sym, kw.ks); count_launch(); }
+      { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)(m + 2) * len * sizeof(cpx<T>) + (double)nc * sizeof(T), 0.0); k_gm_update<T><<<eb, 256, 0, st>>>(ixe, X, V, sym, kw.ks); }
       { k_gm_close<<<1, 1, 0, st>>>(kw.ks); count_launch(); }
       vd_status e = read_head(kw, &hd, st);
       if (e != VD_OK) return e;
@@ -804,8 +804,8 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
       if (hd.iters >= o.maxit) {
         // one more loop head forms the true residual and sets the final status
         sys.apply(sys, X, w, false, done, st);
-        { k_sub<T><<<eb, 256, 0, st>>>(len, B, w, V, done); count_launch(); }
-        { k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, nullptr, V, EPI_GM_BETA, ra, done); count_launch(); }
+        { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)3 * len * sizeof(cpx<T>), 0.0); k_sub<T><<<eb, 256, 0, st>>>(len, B, w, V, done); }
+        { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)1 * len * sizeof(cpx<T>), 0.0); k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, nullptr, V, EPI_GM_BETA, ra, done); }
         e = read_head(kw, &hd, st);
         if (e != VD_OK) return e;
         break;

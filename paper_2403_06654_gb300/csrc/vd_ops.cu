@@ -112,6 +112,84 @@ void inv_transform(const vd_grid* G, const cpx<T>* in, const Mult& mu, T* out, c
   launch_xpass<T>(X, g, twtab<T>(G), st);
 }
 
+// Plain transforms with float-pair arithmetic; double fields in and out, float-pair
+// intermediates in tmp (one spectral field of 16-byte elements).
+void fwd_transform_dd(const vd_grid* G, const double* in, cpx<double>* out, void* tmp, cudaStream_t st) {
+  const GridDesc& g = G->g;
+  cpx<dd>* t = reinterpret_cast<cpx<dd>*>(tmp);
+  XProg X{};
+  X.ncomp = 1;
+  X.mode = 1;
+  X.in[0] = in;
+  X.conv_in = 1;
+  X.scale = 0.5;
+  if (g.ndim == 1) {
+    X.out[0] = out;
+    X.conv_out = 1;
+    launch_xpass<dd>(X, g, G->tw_dd, st);
+    return;
+  }
+  X.out[0] = t;
+  launch_xpass<dd>(X, g, G->tw_dd, st);
+  AxisProg P{};
+  P.nxf = 1;
+  P.xf[0] = mkxf(0, 0, 0, 0, true, true);
+  P.in[0] = t;
+  P.axis = 1;
+  if (g.ndim == 2) {
+    P.out[0] = out;
+    P.conv_out = 1;
+    launch_axis<dd>(P, -1, g, G->tw_dd, st);
+    return;
+  }
+  P.out[0] = t;
+  launch_axis<dd>(P, -1, g, G->tw_dd, st);
+  P.axis = 2;
+  P.out[0] = out;
+  P.conv_out = 1;
+  launch_axis<dd>(P, -1, g, G->tw_dd, st);
+}
+
+void inv_transform_dd(const vd_grid* G, const cpx<double>* in, double* out, void* tmp, cudaStream_t st) {
+  const GridDesc& g = G->g;
+  cpx<dd>* t = reinterpret_cast<cpx<dd>*>(tmp);
+  const void* cur = in;
+  int conv = 1;
+  if (g.ndim == 3) {
+    AxisProg P{};
+    P.nxf = 1;
+    P.xf[0] = mkxf(0, 0, 0, 0, true, true);
+    P.in[0] = cur;
+    P.out[0] = t;
+    P.conv_in = conv;
+    P.axis = 2;
+    launch_axis<dd>(P, +1, g, G->tw_dd, st);
+    cur = t;
+    conv = 0;
+  }
+  if (g.ndim >= 2) {
+    AxisProg P{};
+    P.nxf = 1;
+    P.xf[0] = mkxf(0, 0, 0, 0, true, true);
+    P.in[0] = cur;
+    P.out[0] = t;
+    P.conv_in = conv;
+    P.axis = 1;
+    launch_axis<dd>(P, +1, g, G->tw_dd, st);
+    cur = t;
+    conv = 0;
+  }
+  XProg X{};
+  X.ncomp = 1;
+  X.mode = 2;
+  X.in[0] = cur;
+  X.conv_in = conv;
+  X.out[0] = out;
+  X.conv_out = 1;
+  X.scale = 1.0 / (double)g.nreal;
+  launch_xpass<dd>(X, g, G->tw_dd, st);
+}
+
 // ---------------------------------------------------------------------------------------
 // pressure operator
 // ---------------------------------------------------------------------------------------

@@ -373,9 +373,10 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const XProg P, const GridDes
     cpx<T>* res;
     __syncthreads();
     if (P.mode == 1) {
-      const cpx<T>* __restrict__ src = reinterpret_cast<const cpx<T>*>(P.in[c]) + (line0 + line) * m;
+      const int cin = (P.conv_in >> c) & 1;
+      const int rbase = (int)((line0 + line) * m);
       if (lok)
-        for (int j = t0; j < m; j += TPL) A[lofs + j] = src[j];
+        for (int j = t0; j < m; j += TPL) A[lofs + j] = ld_el<T>(P.in[c], cin, rbase + j);
       res = fft_lines<T, -1>(A, B, 1, lofs, t0, TPL, g.px, twm);
     } else {
       const int cin = (P.conv_in >> c) & 1;
@@ -407,9 +408,10 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const XProg P, const GridDes
       }
       res = fft_lines<T, +1>(A, B, 1, lofs, t0, TPL, g.px, twm);
       if (P.mode == 2) {
-        cpx<T>* __restrict__ dst = reinterpret_cast<cpx<T>*>(P.out[c]) + (line0 + line) * m;
+        const int cout = (P.conv_out >> c) & 1;
+        const int rbase = (int)((line0 + line) * m);
         if (lok)
-          for (int j = t0; j < m; j += TPL) dst[j] = scal(res[lofs + j], scale);
+          for (int j = t0; j < m; j += TPL) st_el<T>(P.out[c], cout, rbase + j, scal(res[lofs + j], scale), true);
         continue;
       }
       if (P.wfield && lok) {

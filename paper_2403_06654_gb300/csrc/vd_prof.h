@@ -18,7 +18,9 @@ enum ProfClass : int {
   PC_OTHER = 4,    // reductions, vector updates, pointwise kernels
   PC_AXISDD = 5,   // strided y/z pass, float-pair
   PC_XPASSDD = 6,  // contiguous x pass, float-pair
-  PC_N = 7
+  PC_VEC32 = 7,    // Krylov vector kernels on float vectors
+  PC_VEC64 = 8,    // Krylov vector kernels on double vectors
+  PC_N = 9
 };
 
 void count_launch();
