@@ -317,7 +317,9 @@ __device__ __forceinline__ T pweight(int kx, int h0) {
   return (kx == 0 || kx == h0 - 1) ? T(1) : T(2);
 }
 
-// Double-precision accumulator fed by short sub-sums in the vector precision (four terms)
+// Double-precision accumulator fed by short sub-sums in the vector precision (16 terms):
+// the FP64 pipe of GB300 runs at 1/69 of the float rate, so one double add per 16 elements
+// keeps the reductions at memory speed while every cross-element sum is done in double.
 template <typename T>
 struct Acc {
   double a = 0.0;
@@ -325,7 +327,7 @@ struct Acc {
   int c = 0;
   __device__ __forceinline__ void add(T v) {
     s += v;
-    if (++c == 4) {
+    if (++c == 16) {
       a += (double)s;
       s = T(0);
       c = 0;

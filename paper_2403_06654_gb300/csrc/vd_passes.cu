@@ -448,6 +448,169 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const XProg P, const GridDes
 }
 
 // ---------------------------------------------------------------------------------------
+// contiguous x pass, register-resident four-step transforms (m = n0/2 = M1 * M2, M1 = C M2)
+//
+// Each line is handled by M2 threads; thread t holds z[M2 q + t], q in [0, M1) (the
+// four-step input distribution).  A four-step transform leaves thread t with outputs
+// k1 + M1 k2 for k1 = t + M2 c, which is z[M2 (c + C k2) + t] -- the same distribution -- so
+// the inverse transform, the multiply by the weights and the forward transform chain in
+// registers.  Shared memory holds one line buffer per line: the spectral line for the
+// (un)packing of the real transform and the column transposes (row stride M1 + 1; line
+// stride LS chosen so the transposes are free of bank conflicts).
+// ---------------------------------------------------------------------------------------
+
+template <typename T, int M1, int M2>
+struct XR {
+  static constexpr int M = M1 * M2;
+  static constexpr int C = M1 / M2;
+  static constexpr int LINES = 256 / M2;
+  static constexpr int RS = M1 + 1;                      // row stride of the transpose
+  static constexpr int LS0 = (M2 * RS > M + 1) ? M2 * RS : M + 1;
+  static constexpr int LS = (sizeof(T) == 4) ? ((LS0 + 7) / 16 * 16 + 8) : LS0;   // float: LS = 8 mod 16
+};
+
+// one four-step transform of length M1*M2 on registers u[M1] (input z[M2 q + t] in u[q]);
+// on return u[c + C k2] = output[t + M2 c + M1 k2].  Yl: this line's buffer.
+template <typename T, int S, int M1, int M2>
+__device__ __forceinline__ void fourstep(cpx<T> (&u)[M1], cpx<T>* Yl, const cpx<T>* tw, int t) {
+  constexpr int RS = M1 + 1;
+  constexpr int C = M1 / M2;
+  dftR<T, S, M1>(u);
+#pragma unroll
+  for (int k1 = 1; k1 < M1; ++k1) {
+    const cpx<T> w = tw[t * k1];
+    u[k1] = (S < 0) ? cmul(u[k1], w) : cmulc(u[k1], w);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k1 = 0; k1 < M1; ++k1) Yl[t * RS + k1] = u[k1];
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    cpx<T> v[M2];
+#pragma unroll
+    for (int n2 = 0; n2 < M2; ++n2) v[n2] = Yl[n2 * RS + t + M2 * c];
+    dftR<T, S, M2>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2) u[c + C * k2] = v[k2];
+  }
+}
+
+template <typename T, int M1, int M2>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_xpass_r(const XProg P, const GridDesc g,
+                                                                          const cpx<T>* __restrict__ twg) {
+  using X = XR<T, M1, M2>;
+  constexpr int M = X::M, LINES = X::LINES, LS = X::LS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (P.done && *P.done) return;
+  const int h0 = g.h0;
+  cpx<T>* twm = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* pk = twm + M;
+  cpx<T>* buf = pk + (M + 2);
+  const int tid = threadIdx.x;
+  for (int j = tid; j < M; j += 256) twm[j] = twg[g.px.tw_off + j];
+  for (int j = tid; j <= M; j += 256) pk[j] = twg[g.pk_off + j];
+  const long long nlines = (long long)g.n1 * g.n2;
+  const long long line0 = (long long)blockIdx.x * LINES;
+  const int line = tid / M2;
+  const int t = tid % M2;
+  const bool lok = line0 + line < nlines;
+  cpx<T>* Yl = buf + line * LS;
+  const T kfx = kfac_t<T>(g, 0);
+  const T scale = scale_t<T>(P.scale, P.scale_hi, P.scale_lo);
+  const int lb = (int)((line0 + line) * h0);      // spectral line base
+  const int rb = (int)((line0 + line) * M);       // real line base (complex pairs)
+  const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr);
+  auto premul = [&](int flags, int k, cpx<T> v) -> cpx<T> {
+    if (!flags) return v;
+    const T kx = kfx * (T)freq_tilde(k, g.n0);
+    T cc = T(1);
+    if (flags & MUL_IK) cc *= kx;
+    if (flags & MUL_SYM) cc *= symarr[lb + k];
+    if (flags & (MUL_NEGK2 | MUL_IK2)) cc *= -kx * kx;
+    v = scal(v, cc);
+    if (flags & MUL_IK) v = mul_i(v);
+    return v;
+  };
+
+  for (int c = 0; c < P.ncomp; ++c) {
+    const int cin = (P.conv_in >> c) & 1, cout = (P.conv_out >> c) & 1;
+    cpx<T> u[M1];
+    __syncthreads();
+    if (P.mode == 1) {
+#pragma unroll
+      for (int q = 0; q < M1; ++q) u[q] = lok ? ld_el<T>(P.in[c], cin, rb + M2 * q + t) : mk<T>(T(0), T(0));
+    } else {
+      // stage the half spectrum, then pack it into the length-m complex spectrum
+      if (lok)
+        for (int k = t; k < h0; k += M2) Yl[k] = premul(P.pre[c], k, ld_el<T>(P.in[c], cin, lb + k));
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < M1; ++q) {
+        const int j = M2 * q + t;
+        const cpx<T> Xv = Yl[j];
+        const cpx<T> Xc = conjg(Yl[M - j]);
+        u[q] = (Xv + Xc) + mul_i(cmulc(Xv - Xc, pk[j]));
+      }
+      fourstep<T, +1, M1, M2>(u, Yl, twm, t);
+      if (P.mode == 2) {
+        if (lok) {
+#pragma unroll
+          for (int q = 0; q < M1; ++q) st_el<T>(P.out[c], cout, rb + M2 * q + t, scal(u[q], scale), true);
+        }
+        continue;
+      }
+      if (P.wfield && lok) {
+        const cpx<T>* __restrict__ wf = reinterpret_cast<const cpx<T>*>(P.wfield) + rb;
+#pragma unroll
+        for (int q = 0; q < M1; ++q) {
+          const cpx<T> wv = wf[M2 * q + t];
+          u[q] = mk<T>(u[q].x * wv.x, u[q].y * wv.y);
+        }
+      }
+    }
+    fourstep<T, -1, M1, M2>(u, Yl, twm, t);
+    // unpack the length-m spectrum into the half spectrum
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < M1; ++q) Yl[M2 * q + t] = u[q];
+    __syncthreads();
+    if (lok) {
+      const int post = P.post[c];
+      for (int k = t; k < h0; k += M2) {
+        const cpx<T> Z = Yl[k == M ? 0 : k];
+        const cpx<T> Zc = conjg(Yl[k == 0 ? 0 : M - k]);
+        cpx<T> Xv = (Z + Zc) - mul_i(cmul(Z - Zc, pk[k]));
+        T cc = scale;
+        if (post) {
+          const T kx = kfx * (T)freq_tilde(k, g.n0);
+          if (post & MUL_IK) cc *= kx;
+          if (post & MUL_SYM) cc *= symarr[lb + k];
+          if (post & (MUL_NEGK2 | MUL_IK2)) cc *= -kx * kx;
+        }
+        Xv = scal(Xv, cc);
+        if (post & MUL_IK) Xv = mul_i(Xv);
+        st_el<T>(P.out[c], cout, lb + k, Xv, true);
+      }
+    }
+  }
+}
+
+template <typename T, int M1, int M2>
+static void launch_xpass_r(const XProg& P, const GridDesc& g, const cpx<T>* tw, cudaStream_t st) {
+  using X = XR<T, M1, M2>;
+  const long long nlines = (long long)g.n1 * g.n2;
+  const long long blocks = (nlines + X::LINES - 1) / X::LINES;
+  const size_t smem = sizeof(cpx<T>) * (size_t)(X::M + (X::M + 2) + X::LINES * X::LS);
+  static size_t done = 0;
+  if (smem > 48 * 1024 && smem > done) {
+    cudaFuncSetAttribute(k_xpass_r<T, M1, M2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    done = smem;
+  }
+  k_xpass_r<T, M1, M2><<<(unsigned)blocks, 256, smem, st>>>(P, g, tw);
+}
+
+// ---------------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------------
 
@@ -575,6 +738,22 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
   if (sym) bytes += (double)g.ncplx * sizeof(T);
   ProfScope ps(std::is_same<T, dd>::value ? PC_XPASSDD : (sizeof(T) == 8 ? PC_XPASS64 : PC_XPASS32), st, bytes,
                flops);
+  if constexpr (std::is_same<T, float>::value) {
+    // register-resident kernel (float; the float-pair version needs too many registers)
+    const cpx<T>* twp = reinterpret_cast<const cpx<T>*>(tw);
+    if (m == 128) {
+      launch_xpass_r<T, 16, 8>(P, g, twp, st);
+      return;
+    }
+    if (m == 64) {
+      launch_xpass_r<T, 8, 8>(P, g, twp, st);
+      return;
+    }
+    if (m == 256) {
+      launch_xpass_r<T, 16, 16>(P, g, twp, st);
+      return;
+    }
+  }
   k_xpass<T><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, reinterpret_cast<const cpx<T>*>(tw), ilog2(L));
 }
 

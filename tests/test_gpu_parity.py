@@ -50,6 +50,9 @@ GRIDS = [
     ((64, 40), (1.0, 2.0)),
     ((20, 12, 30), (2 * math.pi, 1.0, 3.0)),
     ((32, 24, 16), (2 * math.pi,) * 3),
+    ((128, 16, 12), (2 * math.pi, 1.0, 2.0)),
+    ((256, 8, 10), (2 * math.pi,) * 3),
+    ((512, 24), (1.0, 2.0)),
 ]
 
 
@@ -249,7 +252,8 @@ def test_large_axis_2d_config2_shape():
 
 @pytest.mark.parametrize("solver", ["cg", "gmres", "rmr"])
 @pytest.mark.parametrize("n,L", [((48, 40, 32), (2 * math.pi,) * 3), ((256,), (2 * math.pi,)),
-                                 ((64, 48), (2 * math.pi, 1.0))])
+                                 ((64, 48), (2 * math.pi, 1.0)), ((128, 20, 24), (2 * math.pi,) * 3),
+                                 ((256, 16, 16), (2 * math.pi,) * 3)])
 def test_mixed_dd_residual_matches_fp64(solver, n, L):
     """Refinement residual in float-pair arithmetic (~2^-48): the returned solution's double
     residual, recomputed here with the double operator, must also meet the tolerance, and the
