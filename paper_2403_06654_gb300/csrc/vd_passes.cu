@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(kRLines * N2, (sizeof(T) == 4 ? 2 : 1)) k_axis
   cpx<T>* Y = tw + N;
   const int tid = threadIdx.x;
   for (int j = tid; j < N; j += kRLines * N2) tw[j] = twg[pl.tw_off + j];
+  __syncthreads();   // the twiddle table is read by every thread before the first transpose
 
   int line_stride, inner_n, outer_stride;
   if (axis == 2) {
