@@ -214,6 +214,57 @@ vd_status vd_flow_get_state(const vd_flow* flow, double* rho, double* u, double*
 vd_status vd_flow_step(vd_flow* flow, double dt, vd_step_info* info, vd_stream stream);
 
 /*
+ * Request server (continuous batching; not in the paper).  Pressure solves of different
+ * grids, densities and tolerances are submitted at any time, queue in FIFO order, and are
+ * admitted as soon as one of max_inflight execution slots is idle and the request's device
+ * memory (vd_server_request_bytes) fits in the HBM budget (hbm_budget bytes, 0 = 80% of the
+ * free memory at creation).  Admitted requests run concurrently, each on its slot's own CUDA
+ * stream; their Krylov state stays in their device workspace until they complete, when the
+ * memory returns to the server and the next requests are admitted.  The server allocates
+ * request memory itself (stream-ordered allocator).  rho, b and x are device buffers owned
+ * by the caller and must stay valid until the request's completion has been polled.
+ * Completions carry steady-clock timestamps (seconds) of submission, start and end.
+ * A request's result does not depend on the other requests in flight.
+ */
+typedef struct vd_server vd_server;
+typedef struct {
+  int max_inflight;    /* concurrent requests (1..64) */
+  size_t hbm_budget;   /* bytes available to admitted requests; 0 = 80% of free memory */
+} vd_server_params;
+typedef struct {
+  unsigned long long id;
+  int ndim;
+  int n[3];
+  double L[3];
+  const double* rho;   /* density (n0 n1 n2 doubles, device) */
+  const double* b;     /* right-hand side (device) */
+  double* x;           /* solution (device, written on completion) */
+  int solver;          /* vd_solver */
+  double tol;
+  int max_it, restart, precision;
+} vd_request;
+typedef struct {
+  unsigned long long id;
+  int status;          /* vd_status of the solve */
+  int iters;
+  double relres_true;
+  double t_submit, t_start, t_done;
+} vd_completion;
+vd_status vd_server_create(const vd_server_params* params, vd_server** out);
+/* device bytes a request will hold while running (density data + solve workspace); 0 on bad sizes */
+size_t vd_server_request_bytes(const vd_request* request);
+/* enqueue (the request is copied); bytes = vd_server_request_bytes(request) */
+vd_status vd_server_submit(vd_server* server, const vd_request* request, size_t bytes);
+/* move up to max completions into out; returns how many */
+int vd_server_poll(vd_server* server, vd_completion* out, int max);
+/* block until every submitted request has completed */
+vd_status vd_server_drain(vd_server* server);
+vd_status vd_server_stats(vd_server* server, long long* submitted, long long* completed, long long* inflight,
+                          size_t* reserved, size_t* budget);
+/* drains, then stops the workers */
+vd_status vd_server_destroy(vd_server* server);
+
+/*
  * out = L~_rho(in) for callers that cannot allocate device memory (the paper has no
  * counterpart; this is an integration convenience).  Such callers include code running
  * inside a host framework whose memory pool owns the device, plugins that must keep a

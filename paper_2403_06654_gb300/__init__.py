@@ -61,6 +61,23 @@ class vd_step_info(ctypes.Structure):
                 ("pres_status", ctypes.c_int), ("vel_relres", ctypes.c_double), ("pres_relres", ctypes.c_double)]
 
 
+class vd_server_params(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_int), ("hbm_budget", ctypes.c_size_t)]
+
+
+class vd_request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_ulonglong), ("ndim", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("L", ctypes.c_double * 3), ("rho", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("solver", ctypes.c_int), ("tol", ctypes.c_double), ("max_it", ctypes.c_int),
+                ("restart", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class vd_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_ulonglong), ("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("relres_true", ctypes.c_double), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
 class vd_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("status", ctypes.c_int),
                 ("relres", ctypes.c_double), ("relres_true", ctypes.c_double),
@@ -95,6 +112,14 @@ _SIGS = {
     "vd_flow_set_state": (_I, [_P, _P, _P, _P]),
     "vd_flow_get_state": (_I, [_P, _P, _P, _P, _P, _P]),
     "vd_flow_step": (_I, [_P, ctypes.c_double, ctypes.POINTER(vd_step_info), _P]),
+    "vd_server_create": (_I, [ctypes.POINTER(vd_server_params), ctypes.POINTER(_P)]),
+    "vd_server_request_bytes": (_SZ, [ctypes.POINTER(vd_request)]),
+    "vd_server_submit": (_I, [_P, ctypes.POINTER(vd_request), _SZ]),
+    "vd_server_poll": (_I, [_P, ctypes.POINTER(vd_completion), _I]),
+    "vd_server_drain": (_I, [_P]),
+    "vd_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
+    "vd_server_destroy": (_I, [_P]),
     "vd_launch_count": (ctypes.c_longlong, []),
     "vd_profile_enable": (_I, [_I]),
     "vd_profile_reset": (_I, []),
@@ -137,6 +162,9 @@ def _stream(stream=None):
 
 
 def _ptr(t):
+    # every pointer of the C interface addresses a dense row-major array
+    if not t.is_contiguous():
+        raise VDError(VD_ERR_INVALID_ARG, "tensor passed to the C interface must be contiguous")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -236,6 +264,63 @@ def vd_flow_step(f, dt, info, stream=None):
     if st in (VD_ERR_INVALID_ARG, VD_ERR_OOM, VD_ERR_CUDA, VD_ERR_NO_DENSITY):
         _check(st)
     return st
+
+
+def vd_server_create(max_inflight=4, hbm_budget=0):
+    h = ctypes.c_void_p()
+    _check(lib().vd_server_create(ctypes.byref(vd_server_params(max_inflight, hbm_budget)), ctypes.byref(h)))
+    return h
+
+
+def vd_server_request_bytes(req):
+    return int(lib().vd_server_request_bytes(ctypes.byref(req)))
+
+
+def vd_server_submit(h, req, nbytes):
+    _check(lib().vd_server_submit(h, ctypes.byref(req), nbytes))
+
+
+def vd_server_poll(h, max_n=256):
+    buf = (vd_completion * max_n)()
+    k = lib().vd_server_poll(h, buf, max_n)
+    return [buf[i] for i in range(k)]
+
+
+def vd_server_drain(h):
+    _check(lib().vd_server_drain(h))
+
+
+def vd_server_stats(h):
+    a, b, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    d, e = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().vd_server_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d),
+                                 ctypes.byref(e)))
+    return {"submitted": a.value, "completed": b.value, "inflight": c.value, "reserved": d.value, "budget": e.value}
+
+
+def vd_server_destroy(h):
+    _check(lib().vd_server_destroy(h))
+
+
+def make_request(rid, n, L, rho, b, x, solver="cg", tol=1e-10, max_it=500, restart=30, precision="mixed_dd"):
+    """Build a vd_request from device tensors (marshalling only)."""
+    nd = len(n)
+    r = vd_request()
+    r.id = rid
+    r.ndim = nd
+    r.n = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - nd)))
+    r.L = (ctypes.c_double * 3)(*(list(L) + [1.0] * (3 - nd)))
+    import torch
+    for name, t in (("rho", rho), ("b", b), ("x", x)):
+        if t.dtype != torch.float64 or not t.is_cuda or tuple(t.shape) != tuple(reversed(n)):
+            raise VDError(VD_ERR_INVALID_ARG, f"{name} must be a float64 CUDA tensor of shape {tuple(reversed(n))}")
+    r.rho, r.b, r.x = _ptr(rho).value, _ptr(b).value, _ptr(x).value
+    r.solver = SOLVERS[solver]
+    r.tol = tol
+    r.max_it = max_it
+    r.restart = restart
+    r.precision = PRECISIONS[precision]
+    return r
 
 
 def vd_launch_count():

@@ -85,9 +85,36 @@ struct Carver {
 using namespace vd;
 
 extern "C" {
-
 const char* vd_last_error(void) { return g_err.c_str(); }
 const char* vd_version(void) { return "vdspectral 0.1 (sm_103a)"; }
+}  // extern "C"
+
+namespace vd {
+// Fill the grid description (plans, sizes) without touching the device; false on bad sizes.
+bool grid_desc_only(int ndim, const int n[3], const double L[3], vd_grid* G) {
+  if (ndim < 1 || ndim > 3) return false;
+  int nn[3] = {1, 1, 1};
+  for (int j = 0; j < ndim; ++j) {
+    if (n[j] < 4 || n[j] > 1024 || (n[j] % 2) != 0 || !(L[j] > 0.0)) return false;
+    nn[j] = n[j];
+  }
+  GridDesc& g = G->g;
+  g.ndim = ndim;
+  g.n0 = nn[0];
+  g.n1 = nn[1];
+  g.n2 = nn[2];
+  g.h0 = nn[0] / 2 + 1;
+  g.nreal = (long long)nn[0] * nn[1] * nn[2];
+  g.ncplx = (long long)g.h0 * nn[1] * nn[2];
+  for (int j = 0; j < 3; ++j) G->L[j] = (j < ndim) ? L[j] : 1.0;
+  bool ok = make_plan(nn[0] / 2, &g.px);
+  if (ndim >= 2) ok = ok && make_plan(nn[1], &g.py);
+  if (ndim == 3) ok = ok && make_plan(nn[2], &g.pz);
+  return ok && g.ncplx * 3 < (1ll << 31);
+}
+}  // namespace vd
+
+extern "C" {
 
 vd_status vd_grid_create(int ndim, const int n[3], const double L[3], vd_grid** out) {
   if (!out || !n || !L) return fail(VD_ERR_INVALID_ARG, "null argument");

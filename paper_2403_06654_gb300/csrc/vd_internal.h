@@ -30,6 +30,10 @@ struct vd_grid {
 
 namespace vd {
 
+// fill the grid description (plans, sizes) of a stack/host vd_grid without device memory;
+// enough for the size queries (vd_density_bytes, vd_workspace_bytes)
+bool grid_desc_only(int ndim, const int n[3], const double L[3], vd_grid* G);
+
 // set the thread-local error message and return the status
 vd_status fail(vd_status st, const std::string& msg);
 vd_status cuda_fail(cudaError_t e, const char* what);

@@ -142,7 +142,7 @@ def slab_density(n, L, s, axis, centre, width, thick):
     La = L[axis]
     dist = (xa - centre + La / 2) % La - La / 2
     rho = 1.0 + (s - 1.0) / 2.0 * (np.tanh((dist + width / 2) / thick) - np.tanh((dist - width / 2) / thick))
-    return np.array(np.broadcast_to(rho, tuple(reversed(n))), copy=True)
+    return np.ascontiguousarray(np.broadcast_to(rho, tuple(reversed(n))))
 
 
 # ---------------------------------------------------------------------------------------

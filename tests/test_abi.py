@@ -51,3 +51,28 @@ def test_host_side_argument_checks_without_gpu():
     assert b"2, 3 and 5" in L.vd_last_error()
     assert L.vd_solve(None, 0, 0, None, None, None, None, None, None, 0, None) == vd.VD_ERR_INVALID_ARG
     assert L.vd_version().startswith(b"vdspectral")
+
+
+def test_pointer_marshalling_rejects_noncontiguous():
+    """Every pointer of the C interface addresses a dense row-major array: strided tensors are refused."""
+    import torch
+    t = torch.zeros((4, 6), dtype=torch.float64).t()
+    with pytest.raises(vd.VDError) as e:
+        vd._ptr(t)
+    assert e.value.status == vd.VD_ERR_INVALID_ARG
+    c = t.contiguous()
+    assert vd._ptr(c).value == c.data_ptr()
+
+
+def test_make_request_checks_tensors():
+    import torch
+    n, L = (8, 6), (1.0, 1.0)
+    good = torch.zeros((6, 8), dtype=torch.float64)
+    # host tensors are refused (the server reads device memory)
+    with pytest.raises(vd.VDError):
+        vd.make_request(0, n, L, good, good, good)
+    # wrong shape or dtype is refused before any device check matters
+    with pytest.raises(vd.VDError):
+        vd.make_request(0, n, L, good.t(), good, good)
+    with pytest.raises(vd.VDError):
+        vd.make_request(0, n, L, good.float(), good, good)
