@@ -50,6 +50,14 @@ def parse():
     ap.add_argument("--side-steps", type=int, default=10, help="timed solves of the other mixed mode")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the 1D and 2D workload measurements")
+    ap.add_argument("--rt-steps", type=int, default=100)
+    ap.add_argument("--mode", default="solve", choices=["solve", "serve"],
+                    help="solve: the 256^3 solve-rate line (with a short serving run); serve: the serving line")
+    ap.add_argument("--no-serve", action="store_true", help="skip the short serving run of the solve line")
+    ap.add_argument("--serve-count", type=int, default=None, help="requests of the serving trace")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrival rate (req/s)")
+    ap.add_argument("--serve-inflight", type=int, default=8, help="server execution slots")
     return ap.parse_args()
 
 
@@ -191,6 +199,303 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------------------------------
+# secondary workloads (reported beside the headline, outside its timed region)
+# ------------------------------------------------------------------------------------------
+
+def extra_tophat1d(dev):
+    """1D periodic N = 256 top-hat (r = 3, d = 0.05), 16-mode rhs: CG, GMRES(30), RMR to 1e-12."""
+    import numpy as np
+    import torch
+    import paper_2403_06654_gb300 as vd
+    from paper_2403_06654_gb300 import inputs
+
+    n = 256
+    G = vd.Grid((n,), (2 * math.pi,), device=dev)
+    G.set_density(torch.from_numpy(inputs.tophat_1d(n=n)).to(dev))
+    f = torch.from_numpy(inputs.modes_rhs_1d(n=n)).to(dev)
+    out = {}
+    for solver in ("cg", "gmres", "rmr"):
+        kw = dict(tol=1e-12, max_it=400, restart=30, check_every=8)
+        x, info = G.solve("pressure", solver, f, **kw)
+        ts = []
+        for _ in range(30):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            G.solve("pressure", solver, f, out=x, **kw)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        out[solver] = {"iters": info["iters"], "status": info["status"], "relres": info["relres"],
+                       "relres_true": info["relres_true"], "us_per_solve_median": float(np.median(ts))}
+    return {"workload": "1D periodic N=256 top-hat r=3 d=0.05, 16-mode rhs (seed 1), tol 1e-12, x0 = 0",
+            "dtype": "f64", "solvers": out}
+
+
+def extra_rt2d(dev, steps):
+    """2D 512 x 1024 Rayleigh--Taylor-like layer: semi-implicit steps (RMR velocity, GMRES pressure, FP64)."""
+    import numpy as np
+    import torch
+    import paper_2403_06654_gb300 as vd
+    from paper_2403_06654_gb300 import inputs
+
+    case = inputs.rt_2d()
+    G = vd.Grid(case.n, case.L, device=dev)
+    F = vd.Flow(G, Re=case.Re, Sc=case.Sc, Fr=case.Fr, gravity_axis=case.gravity_axis, vel_solver="rmr",
+                pres_solver="gmres", tol=1e-10, max_it=200, restart=30)
+    F.set_state(torch.from_numpy(case.rho).to(dev), torch.from_numpy(case.u).to(dev))
+    for _ in range(2):
+        F.step(case.dt)
+    F.set_state(torch.from_numpy(case.rho).to(dev), torch.from_numpy(case.u).to(dev))
+    infos = []
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        infos.append(F.step(case.dt))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rho, u, _, _ = F.state()
+    div = G.divergence(u)
+    ok = all(i["status"] == "converged" for i in infos)
+    return {"workload": "2D 512x1024 RT-like layer (s=3, interface 0.02, eta 0.05 cos, Re=1000, Sc=1, Fr=1, "
+                        "dt=1e-3, 1e-3 velocity noise seed 2), RMR velocity + GMRES pressure to 1e-10",
+            "dtype": "f64", "steps": steps, "ms_per_step": ms / steps, "all_converged": ok,
+            "vel_iters_mean": float(np.mean([i["vel_iters"] for i in infos])),
+            "pres_iters_mean": float(np.mean([i["pres_iters"] for i in infos])),
+            "pres_iters_first_last": [infos[0]["pres_iters"], infos[-1]["pres_iters"]],
+            "div_u_rel": float(torch.linalg.vector_norm(div) / torch.linalg.vector_norm(u)),
+            "mass_drift_rel": float(abs(rho.mean().item() - float(np.mean(case.rho))) / float(np.mean(case.rho)))}
+
+
+# ------------------------------------------------------------------------------------------
+# serving: Poisson request stream through the request server
+# ------------------------------------------------------------------------------------------
+
+SERVE_VARIANTS = 4   # distinct densities materialised per grid size (cycled over the trace)
+
+
+class _ServeInputs:
+    """Device inputs of a serving trace: per grid size, one band-limited rhs and the densities of
+    its first SERVE_VARIANTS trace instances; solution buffers come from a free list so that no
+    two in-flight requests write the same buffer."""
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.rhs, self.dens, self.free, self.count = {}, {}, {}, {}
+
+    def add(self, trace):
+        import torch
+        from paper_2403_06654_gb300 import inputs
+        dev = self.dev
+        for _, inst in trace:
+            key = tuple(inst.n)
+            if key not in self.rhs:
+                self.rhs[key] = torch.from_numpy(inputs.smooth_random_field(inst.n, inst.L, 900 + sum(inst.n),
+                                                                            kmax=5)).to(dev)
+                self.dens[key] = []
+                self.free[key] = []
+                self.count[key] = 0
+            if len(self.dens[key]) < SERVE_VARIANTS:
+                self.dens[key].append(torch.from_numpy(inst.density()).to(dev))
+
+    def reserve(self, trace, per_shape=64, big_bytes=64 << 20, per_big=32):
+        """Allocate solution buffers up front (at most the number of requests of each size), so
+        that no allocation happens on the submit path during the timed trace."""
+        import torch
+        need = {}
+        for _, inst in trace:
+            need[tuple(inst.n)] = need.get(tuple(inst.n), 0) + 1
+        for key, k in need.items():
+            ref = self.rhs[key]
+            cap = per_big if ref.numel() * 8 > big_bytes else per_shape
+            while len(self.free[key]) < min(k, cap):
+                self.free[key].append(torch.empty_like(ref))
+
+    def take(self, inst):
+        import torch
+        key = tuple(inst.n)
+        v = self.count[key] % len(self.dens[key])
+        self.count[key] += 1
+        x = self.free[key].pop() if self.free[key] else torch.empty_like(self.rhs[key])
+        return self.dens[key][v], self.rhs[key], x
+
+    def give(self, key, x):
+        self.free[key].append(x)
+
+
+def run_trace(vd, trace, src, max_inflight, precision, solver="cg"):
+    """Open-loop: request i is submitted at its arrival time (host monotonic clock) whatever the
+    server's state.  Returns per-request records and the makespan."""
+    import torch
+    torch.cuda.synchronize()
+    S = vd.vd_server_create(max_inflight=max_inflight, hbm_budget=0)
+    pending = {}
+    recs = []
+
+    def collect():
+        while True:
+            got = vd.vd_server_poll(S, 1024)
+            if not got:
+                return
+            for c in got:
+                take(c)
+
+    def take(c):
+        key, x, t_sched, tol = pending.pop(int(c.id))
+        src.give(key, x)
+        recs.append({"id": int(c.id), "n": key, "tol": tol, "status": int(c.status), "iters": int(c.iters),
+                     "relres_true": float(c.relres_true), "t_sched": t_sched, "t_submit": float(c.t_submit),
+                     "t_start": float(c.t_start), "t_done": float(c.t_done)})
+
+    try:
+        t0 = time.monotonic() + 0.05
+        for i, (ta, inst) in enumerate(trace):
+            t_sched = t0 + ta
+            while True:
+                dt = t_sched - time.monotonic()
+                if dt <= 0:
+                    break
+                collect()
+                if dt > 2e-4:
+                    time.sleep(min(dt - 1e-4, 1e-3))
+            rho, b, x = src.take(inst)
+            q = vd.make_request(i, inst.n, inst.L, rho, b, x, solver=solver, tol=inst.tol, max_it=500,
+                                precision=precision)
+            pending[i] = (tuple(inst.n), x, t_sched, inst.tol)
+            vd.vd_server_submit(S, q, vd.vd_server_request_bytes(q))
+        vd.vd_server_drain(S)
+        collect()
+    finally:
+        vd.vd_server_destroy(S)
+    return recs, t0
+
+
+def serve_summary(recs, t0, rate):
+    import numpy as np
+    lat = np.array([r["t_done"] - r["t_sched"] for r in recs]) * 1e3
+    wait = np.array([r["t_start"] - r["t_sched"] for r in recs]) * 1e3
+    svc = np.array([r["t_done"] - r["t_start"] for r in recs]) * 1e3
+    lag = np.array([r["t_submit"] - r["t_sched"] for r in recs]) * 1e3
+    span = max(r["t_sched"] for r in recs) - t0
+    makespan = max(r["t_done"] for r in recs) - t0
+    big = np.array([r["n"] == (256, 256, 256) for r in recs])
+    bad = [r for r in recs if not (r["status"] == 0 and r["relres_true"] <= r["tol"])]
+    ok = not bad
+    return {"offered_rate": rate, "requests": len(recs), "solves_per_s": len(recs) / makespan,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max()), "mean": float(lat.mean())},
+            "latency_ms_256cubed": ({"p50": float(np.percentile(lat[big], 50)),
+                                     "p99": float(np.percentile(lat[big], 99))} if big.any() else None),
+            "queue_wait_ms": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+            "service_ms": {"p50": float(np.percentile(svc, 50)), "p99": float(np.percentile(svc, 99))},
+            "submit_lag_ms_p99": float(np.percentile(lag, 99)),
+            "arrival_span_s": span, "makespan_s": makespan,
+            "keeps_up": bool(makespan <= 1.1 * span + 1.0), "all_converged": ok,
+            "failures": [{k: r[k] for k in ("id", "n", "tol", "status", "iters", "relres_true")} for r in bad[:8]],
+            "n_failures": len(bad)}
+
+
+def one_at_a_time(vd, trace, src, precision, dev):
+    """The same requests solved one after another on one stream through vd_solve (no server)."""
+    import torch
+    grids = {}
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _, inst in trace:
+        key = tuple(inst.n)
+        if key not in grids:
+            grids[key] = vd.Grid(inst.n, inst.L, device=dev)
+        G = grids[key]
+        rho, b, x = src.take(inst)
+        G.set_density(rho)
+        _, info = G.solve("pressure", "cg", b, out=x, tol=inst.tol, max_it=500, precision=precision)
+        src.give(key, x)
+        if info["status"] != "converged":
+            raise SystemExit(f"one-at-a-time solve failed: {info}")
+    torch.cuda.synchronize()
+    return len(trace) / (time.perf_counter() - t)
+
+
+def run_serving(vd, dev, count, rate, max_inflight, sweep=(), baseline_count=200, precision="mixed_dd"):
+    """Poisson trace (mean `rate` req/s) of pressure solves, 95% from the batched-instance size mix
+    and 5% 256^3, tolerances 1e-6 / 1e-8 / 1e-10 uniform, served open-loop; plus the first
+    `baseline_count` requests solved one at a time in FP64 and in the serving precision, and the
+    same requests submitted all at once to the server."""
+    from paper_2403_06654_gb300 import inputs
+    trace = inputs.serving_trace(count=count, rate=rate)
+    # each sweep point: about 4 s of arrivals
+    sweep_traces = [(r, inputs.serving_trace(count=int(min(count, max(500, 4 * r))), rate=r)) for r in sweep]
+    src = _ServeInputs(dev)
+    src.add(trace)
+    for _, tr in sweep_traces:
+        src.add(tr)
+    src.reserve(trace)
+    # warm-up: every worker meets most grid sizes; pools and plans are built outside the timed trace
+    warm = sorted({tuple(inst.n): (0.0, inst) for _, inst in trace}.values(), key=lambda p: p[1].n)
+    run_trace(vd, [(0.0, inst) for _ in range(max_inflight) for _, inst in warm], src, max_inflight, precision)
+    recs, t0 = run_trace(vd, trace, src, max_inflight, precision)
+    out = serve_summary(recs, t0, rate)
+    out["max_inflight"] = max_inflight
+    out["precision"] = precision
+    if sweep:
+        rows = []
+        for r, tr in sweep_traces:
+            rr, t0r = run_trace(vd, tr, src, max_inflight, precision)
+            s = serve_summary(rr, t0r, r)
+            rows.append({k: s[k] for k in ("offered_rate", "requests", "solves_per_s", "latency_ms", "keeps_up",
+                                           "makespan_s", "all_converged")})
+        out["rate_sweep"] = rows
+        kept = [row["offered_rate"] for row in rows if row["keeps_up"]]
+        out["sustainable_rate"] = max(kept) if kept else None
+    base = trace[:baseline_count]
+    out["one_at_a_time"] = {"requests": len(base),
+                            "fp64_solves_per_s": one_at_a_time(vd, base, src, "fp64", dev),
+                            precision + "_solves_per_s": one_at_a_time(vd, base, src, precision, dev)}
+    # the same requests all at once through the server (its capacity on this mix)
+    rb, t0b = run_trace(vd, [(0.0, inst) for _, inst in base], src, max_inflight, precision)
+    out["one_at_a_time"]["server_all_at_once_solves_per_s"] = len(rb) / (max(r["t_done"] for r in rb) - t0b)
+    return out
+
+
+SERVE_WORKLOAD = ("Poisson arrivals (seed 5) of pressure solves: 95% batched-instance mix (2D 64..512^2, "
+                  "3D 32..160^3, slab density ratio 2..50 log-uniform, interface 3 cells), 5% 256^3; "
+                  "tol 1e-6/1e-8/1e-10 uniform; CG, x0 = 0; open-loop submission")
+
+
+def serve_line(args, vd, dev, rank, world, pg):
+    """The serving line: the full trace at the configured rate, a rate sweep, and one-at-a-time runs."""
+    import torch
+    count = args.serve_count or 20000
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    l0 = vd.vd_launch_count()
+    s = run_serving(vd, dev, count, args.serve_rate, args.serve_inflight,
+                    sweep=(250.0, 500.0, 1000.0, 2000.0), baseline_count=200)
+    launches = vd.vd_launch_count() - l0
+    clocks = sampler.stop()
+    value = s["solves_per_s"]
+    if pg is not None:
+        t = torch.tensor([value], device=dev)
+        pg.all_reduce(t)
+        value = float(t.item())
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": s["requests"],
+           "warmup": args.serve_inflight, "ms_per_step": 1e3 / max(value, 1e-9), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": DTYPES["mixed_dd"], "data": "synthetic",
+           "config": {"workload": SERVE_WORKLOAD, "requests": count, "rate": args.serve_rate,
+                      "max_inflight": args.serve_inflight, "parallelism": f"replicas x{world}",
+                      "l2": "mixed: small requests are L2-resident, 256^3 inputs exceed L2"},
+           "latency_ms": s["latency_ms"], "serving": s, "gpu_launches": int(launches), "clocks": clocks,
+           "mode": "serve"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
 
@@ -220,6 +525,8 @@ def main():
         torch.cuda.synchronize()
 
     vd.lib()   # fails loudly when the library is missing
+    if args.mode == "serve":
+        return serve_line(args, vd, dev, rank, world, pg)
     n = args.n
     L = (2 * math.pi,) * 3
     case = inputs.jet_3d(n=n)
@@ -366,6 +673,15 @@ def main():
                                        "GB/s": prof[c]["alg_bytes"] / max(prof[c]["ms"], 1e-9) / 1e6}
                for c in prof}
 
+    # ---------------- secondary workloads ----------------
+    extras = None
+    if not args.no_extras:
+        extras = {"tophat1d": extra_tophat1d(dev), "rt2d": extra_rt2d(dev, args.rt_steps)}
+
+    serving = None
+    if not args.no_serve:
+        serving = run_serving(vd, dev, args.serve_count or 2000, args.serve_rate, args.serve_inflight)
+
     # ---------------- CPU oracle baseline (rank 0, N = 1) ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -406,6 +722,8 @@ def main():
         "kernel_classes": classes,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "workloads": extras,
+        "serving": serving,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
