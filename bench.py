@@ -178,7 +178,7 @@ def run_reference(args, rank, world):
         return 0
     import numpy as np  # noqa: F401
 
-    iters = 14   # CG iterations of the double-precision solve of this workload (measured on the GPU path)
+    iters = 13   # iterations of the oracle's own PCG on this workload to 1e-10 (true relres 2.87e-11)
     for _ in range(args.warmup):
         oracle_iteration_seconds(args.n)
     t = []
@@ -277,12 +277,12 @@ SERVE_VARIANTS = 4   # distinct densities materialised per grid size (cycled ove
 
 class _ServeInputs:
     """Device inputs of a serving trace: per grid size, one band-limited rhs and the densities of
-    its first SERVE_VARIANTS trace instances; solution buffers come from a free list so that no
-    two in-flight requests write the same buffer."""
+    its first SERVE_VARIANTS trace instances (cycled).  Solutions stay in server memory until
+    the client releases them, so nothing is allocated on the submit path."""
 
     def __init__(self, dev):
         self.dev = dev
-        self.rhs, self.dens, self.free, self.count = {}, {}, {}, {}
+        self.rhs, self.dens, self.count = {}, {}, {}
 
     def add(self, trace):
         import torch
@@ -294,39 +294,20 @@ class _ServeInputs:
                 self.rhs[key] = torch.from_numpy(inputs.smooth_random_field(inst.n, inst.L, 900 + sum(inst.n),
                                                                             kmax=5)).to(dev)
                 self.dens[key] = []
-                self.free[key] = []
                 self.count[key] = 0
             if len(self.dens[key]) < SERVE_VARIANTS:
                 self.dens[key].append(torch.from_numpy(inst.density()).to(dev))
 
-    def reserve(self, trace, per_shape=64, big_bytes=64 << 20, per_big=32):
-        """Allocate solution buffers up front (at most the number of requests of each size), so
-        that no allocation happens on the submit path during the timed trace."""
-        import torch
-        need = {}
-        for _, inst in trace:
-            need[tuple(inst.n)] = need.get(tuple(inst.n), 0) + 1
-        for key, k in need.items():
-            ref = self.rhs[key]
-            cap = per_big if ref.numel() * 8 > big_bytes else per_shape
-            while len(self.free[key]) < min(k, cap):
-                self.free[key].append(torch.empty_like(ref))
-
     def take(self, inst):
-        import torch
         key = tuple(inst.n)
         v = self.count[key] % len(self.dens[key])
         self.count[key] += 1
-        x = self.free[key].pop() if self.free[key] else torch.empty_like(self.rhs[key])
-        return self.dens[key][v], self.rhs[key], x
-
-    def give(self, key, x):
-        self.free[key].append(x)
+        return self.dens[key][v], self.rhs[key]
 
 
 def run_trace(vd, trace, src, max_inflight, precision, solver="cg"):
     """Open-loop: request i is submitted at its arrival time (host monotonic clock) whatever the
-    server's state.  Returns per-request records and the makespan."""
+    server's state; each completion is polled, recorded and its solution released."""
     import torch
     torch.cuda.synchronize()
     S = vd.vd_server_create(max_inflight=max_inflight, hbm_budget=0)
@@ -342,8 +323,9 @@ def run_trace(vd, trace, src, max_inflight, precision, solver="cg"):
                 take(c)
 
     def take(c):
-        key, x, t_sched, tol = pending.pop(int(c.id))
-        src.give(key, x)
+        key, t_sched, tol = pending.pop(int(c.id))
+        if c.x:
+            vd.vd_server_release(S, int(c.id))
         recs.append({"id": int(c.id), "n": key, "tol": tol, "status": int(c.status), "iters": int(c.iters),
                      "relres_true": float(c.relres_true), "t_sched": t_sched, "t_submit": float(c.t_submit),
                      "t_start": float(c.t_start), "t_done": float(c.t_done)})
@@ -359,10 +341,10 @@ def run_trace(vd, trace, src, max_inflight, precision, solver="cg"):
                 collect()
                 if dt > 2e-4:
                     time.sleep(min(dt - 1e-4, 1e-3))
-            rho, b, x = src.take(inst)
-            q = vd.make_request(i, inst.n, inst.L, rho, b, x, solver=solver, tol=inst.tol, max_it=500,
+            rho, b = src.take(inst)
+            q = vd.make_request(i, inst.n, inst.L, rho, b, None, solver=solver, tol=inst.tol, max_it=500,
                                 precision=precision)
-            pending[i] = (tuple(inst.n), x, t_sched, inst.tol)
+            pending[i] = (tuple(inst.n), t_sched, inst.tol)
             vd.vd_server_submit(S, q, vd.vd_server_request_bytes(q))
         vd.vd_server_drain(S)
         collect()
@@ -407,10 +389,9 @@ def one_at_a_time(vd, trace, src, precision, dev):
         if key not in grids:
             grids[key] = vd.Grid(inst.n, inst.L, device=dev)
         G = grids[key]
-        rho, b, x = src.take(inst)
+        rho, b = src.take(inst)
         G.set_density(rho)
-        _, info = G.solve("pressure", "cg", b, out=x, tol=inst.tol, max_it=500, precision=precision)
-        src.give(key, x)
+        _, info = G.solve("pressure", "cg", b, tol=inst.tol, max_it=500, precision=precision)
         if info["status"] != "converged":
             raise SystemExit(f"one-at-a-time solve failed: {info}")
     torch.cuda.synchronize()
@@ -430,7 +411,6 @@ def run_serving(vd, dev, count, rate, max_inflight, sweep=(), baseline_count=200
     src.add(trace)
     for _, tr in sweep_traces:
         src.add(tr)
-    src.reserve(trace)
     # warm-up: every worker meets most grid sizes; pools and plans are built outside the timed trace
     warm = sorted({tuple(inst.n): (0.0, inst) for _, inst in trace}.values(), key=lambda p: p[1].n)
     run_trace(vd, [(0.0, inst) for _ in range(max_inflight) for _, inst in warm], src, max_inflight, precision)
@@ -471,7 +451,7 @@ def serve_line(args, vd, dev, rank, world, pg):
     sampler.start()
     l0 = vd.vd_launch_count()
     s = run_serving(vd, dev, count, args.serve_rate, args.serve_inflight,
-                    sweep=(250.0, 500.0, 1000.0, 2000.0), baseline_count=200)
+                    sweep=(100.0, 150.0, 200.0, 250.0, 500.0, 1000.0, 2000.0), baseline_count=200)
     launches = vd.vd_launch_count() - l0
     clocks = sampler.stop()
     value = s["solves_per_s"]
@@ -562,11 +542,16 @@ def main():
     barrier()
     sampler.start()
     infos = []
+    nvtx = getattr(torch.cuda, "nvtx", None)
+    if nvtx is not None:
+        nvtx.range_push("timed")   # lets a profiler select exactly the timed solves
     ev[0].record(stream)
     for k in range(args.steps):
         infos.append(solve(head))
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
+    if nvtx is not None:
+        nvtx.range_pop()
     barrier()
     clocks = sampler.stop()
     vd.vd_profile_enable(False)

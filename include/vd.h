@@ -221,8 +221,12 @@ vd_status vd_flow_step(vd_flow* flow, double dt, vd_step_info* info, vd_stream s
  * free memory at creation).  Admitted requests run concurrently, each on its slot's own CUDA
  * stream; their Krylov state stays in their device workspace until they complete, when the
  * memory returns to the server and the next requests are admitted.  The server allocates
- * request memory itself (stream-ordered allocator).  rho, b and x are device buffers owned
- * by the caller and must stay valid until the request's completion has been polled.
+ * request memory itself (stream-ordered allocator).  rho and b are device buffers owned by
+ * the caller and must stay valid until the request's completion has been polled.  The
+ * solution goes to the caller's x when x is not null; with x null the server keeps it in
+ * its own device memory, counted in the request's bytes and in the HBM budget until the
+ * caller calls vd_server_fetch (copy out, then free) or vd_server_release (free) with the
+ * request's id, so a client never allocates on the submit path.
  * Completions carry steady-clock timestamps (seconds) of submission, start and end.
  * A request's result does not depend on the other requests in flight.
  */
@@ -238,7 +242,7 @@ typedef struct {
   double L[3];
   const double* rho;   /* density (n0 n1 n2 doubles, device) */
   const double* b;     /* right-hand side (device) */
-  double* x;           /* solution (device, written on completion) */
+  double* x;           /* solution (device, written on completion); null: server-owned */
   int solver;          /* vd_solver */
   double tol;
   int max_it, restart, precision;
@@ -249,14 +253,21 @@ typedef struct {
   int iters;
   double relres_true;
   double t_submit, t_start, t_done;
+  const double* x;     /* device address of the solution (the caller's x, or server-owned) */
 } vd_completion;
 vd_status vd_server_create(const vd_server_params* params, vd_server** out);
-/* device bytes a request will hold while running (density data + solve workspace); 0 on bad sizes */
+/* device bytes a request will hold while running (density data + solve workspace, plus the
+ * solution when x is null); 0 on bad sizes */
 size_t vd_server_request_bytes(const vd_request* request);
 /* enqueue (the request is copied); bytes = vd_server_request_bytes(request) */
 vd_status vd_server_submit(vd_server* server, const vd_request* request, size_t bytes);
 /* move up to max completions into out; returns how many */
 int vd_server_poll(vd_server* server, vd_completion* out, int max);
+/* server-owned solution of completed request id: copy it to dst (n0 n1 n2 doubles, device,
+ * ordered on stream) and free it / only free it.  INVALID_ARG if id holds no server-owned
+ * solution (unknown, not completed, caller-owned or already released). */
+vd_status vd_server_fetch(vd_server* server, unsigned long long id, double* dst, vd_stream stream);
+vd_status vd_server_release(vd_server* server, unsigned long long id);
 /* block until every submitted request has completed */
 vd_status vd_server_drain(vd_server* server);
 vd_status vd_server_stats(vd_server* server, long long* submitted, long long* completed, long long* inflight,

@@ -75,7 +75,7 @@ class vd_request(ctypes.Structure):
 class vd_completion(ctypes.Structure):
     _fields_ = [("id", ctypes.c_ulonglong), ("status", ctypes.c_int), ("iters", ctypes.c_int),
                 ("relres_true", ctypes.c_double), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
-                ("t_done", ctypes.c_double)]
+                ("t_done", ctypes.c_double), ("x", ctypes.c_void_p)]
 
 
 class vd_solve_info(ctypes.Structure):
@@ -116,6 +116,8 @@ _SIGS = {
     "vd_server_request_bytes": (_SZ, [ctypes.POINTER(vd_request)]),
     "vd_server_submit": (_I, [_P, ctypes.POINTER(vd_request), _SZ]),
     "vd_server_poll": (_I, [_P, ctypes.POINTER(vd_completion), _I]),
+    "vd_server_fetch": (_I, [_P, ctypes.c_ulonglong, _P, _P]),
+    "vd_server_release": (_I, [_P, ctypes.c_ulonglong]),
     "vd_server_drain": (_I, [_P]),
     "vd_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
@@ -286,6 +288,15 @@ def vd_server_poll(h, max_n=256):
     return [buf[i] for i in range(k)]
 
 
+def vd_server_fetch(h, rid, dst, stream=None):
+    """Copy the server-owned solution of request rid into dst (device tensor) and free it."""
+    _check(lib().vd_server_fetch(h, rid, _ptr(dst), _stream(stream)))
+
+
+def vd_server_release(h, rid):
+    _check(lib().vd_server_release(h, rid))
+
+
 def vd_server_drain(h):
     _check(lib().vd_server_drain(h))
 
@@ -302,8 +313,8 @@ def vd_server_destroy(h):
     _check(lib().vd_server_destroy(h))
 
 
-def make_request(rid, n, L, rho, b, x, solver="cg", tol=1e-10, max_it=500, restart=30, precision="mixed_dd"):
-    """Build a vd_request from device tensors (marshalling only)."""
+def make_request(rid, n, L, rho, b, x=None, solver="cg", tol=1e-10, max_it=500, restart=30, precision="mixed_dd"):
+    """Build a vd_request from device tensors (marshalling only); x None: server-owned solution."""
     nd = len(n)
     r = vd_request()
     r.id = rid
@@ -312,9 +323,12 @@ def make_request(rid, n, L, rho, b, x, solver="cg", tol=1e-10, max_it=500, resta
     r.L = (ctypes.c_double * 3)(*(list(L) + [1.0] * (3 - nd)))
     import torch
     for name, t in (("rho", rho), ("b", b), ("x", x)):
+        if t is None and name == "x":
+            continue
         if t.dtype != torch.float64 or not t.is_cuda or tuple(t.shape) != tuple(reversed(n)):
             raise VDError(VD_ERR_INVALID_ARG, f"{name} must be a float64 CUDA tensor of shape {tuple(reversed(n))}")
-    r.rho, r.b, r.x = _ptr(rho).value, _ptr(b).value, _ptr(x).value
+    r.rho, r.b = _ptr(rho).value, _ptr(b).value
+    r.x = _ptr(x).value if x is not None else None
     r.solver = SOLVERS[solver]
     r.tol = tol
     r.max_it = max_it

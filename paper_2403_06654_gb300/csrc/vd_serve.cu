@@ -7,8 +7,10 @@
 // concurrently, each on its worker's own non-blocking CUDA stream, so their kernels overlap
 // on the device.  Krylov state lives in the request's device workspace for the whole solve.
 // Memory is taken from the stream-ordered allocator of the worker's stream and returned when
-// the request completes, which admits the next ones.  Completions carry submit / start / done
-// timestamps (host steady clock, seconds) for latency statistics.
+// the request completes, which admits the next ones.  A request without an output buffer gets
+// its solution in server memory that stays reserved until the caller fetches or releases it.
+// Completions carry submit / start / done timestamps (host steady clock, seconds) for latency
+// statistics.
 //
 // Every solve is deterministic (fixed launch shapes, fixed-order reductions) and never shares
 // device data with another request, so a request's result does not depend on the mix it ran in.
@@ -35,8 +37,20 @@ double now_s() {
 struct Job {
   vd_request r;
   double t_submit;
-  size_t bytes;   // device bytes needed (density + workspace)
+  size_t bytes;   // device bytes needed (density + workspace, plus a server-owned solution)
 };
+
+struct Owned {    // server-owned solution of a completed request
+  void* p;
+  size_t bytes;   // bytes it keeps reserved in the budget
+  size_t size;    // bytes of the solution (n0 n1 n2 doubles)
+};
+
+size_t solution_size(const vd_request& r) {
+  const long long n = (long long)r.n[0] * (r.ndim > 1 ? r.n[1] : 1) * (r.ndim > 2 ? r.n[2] : 1);
+  return (size_t)n * sizeof(double);
+}
+size_t out_bytes(const vd_request& r) { return (solution_size(r) + 255) & ~(size_t)255; }
 
 struct GridKey {
   int ndim, n0, n1, n2;
@@ -57,7 +71,9 @@ struct vd_server {
   std::deque<Job> queue;             // submitted, not admitted
   std::deque<Job> ready;             // admitted, waiting for a worker
   std::vector<vd_completion> done;   // completed, not yet polled
-  size_t reserved = 0;               // bytes held by admitted jobs
+  std::map<unsigned long long, Owned> owned;   // server-owned solutions, by request id
+  cudaStream_t aux = nullptr;        // stream of fetch copies and releases
+  size_t reserved = 0;               // bytes held by admitted jobs and unreleased solutions
   size_t budget = 0;
   int idle = 0;                      // idle workers
   long long inflight = 0;            // admitted + running
@@ -99,11 +115,17 @@ struct vd_server {
       c.id = j.r.id;
       c.t_submit = j.t_submit;
       c.t_start = now_s();
-      c.status = run(j, st, grids, &c);
+      void* xo = nullptr;
+      c.status = run(j, st, grids, &c, &xo);
       c.t_done = now_s();
       {
         std::lock_guard<std::mutex> lk(mu);
-        reserved -= j.bytes;
+        size_t keep = 0;
+        if (xo) {   // the solution stays reserved until the caller fetches or releases it
+          keep = std::min(out_bytes(j.r), j.bytes);
+          owned[j.r.id] = Owned{xo, keep, solution_size(j.r)};
+        }
+        reserved -= j.bytes - keep;
         --inflight;
         ++completed;
         done.push_back(c);
@@ -115,7 +137,7 @@ struct vd_server {
     cudaStreamDestroy(st);
   }
 
-  int run(const Job& j, cudaStream_t st, std::map<GridKey, vd_grid*>& grids, vd_completion* c) {
+  int run(const Job& j, cudaStream_t st, std::map<GridKey, vd_grid*>& grids, vd_completion* c, void** xo) {
     const vd_request& r = j.r;
     GridKey key{r.ndim, r.n[0], r.ndim > 1 ? r.n[1] : 1, r.ndim > 2 ? r.n[2] : 1,
                 r.L[0], r.ndim > 1 ? r.L[1] : 1.0, r.ndim > 2 ? r.L[2] : 1.0};
@@ -131,19 +153,49 @@ struct vd_server {
     const size_t db = vd_density_bytes(G, VD_OP_PRESSURE);
     vd_solve_params sp = request_params(r);
     const size_t wb = vd_workspace_bytes(G, VD_OP_PRESSURE, (vd_solver)r.solver, &sp);
+    double* x = r.x;
+    if (!x) {
+      if (cudaMallocAsync(xo, out_bytes(r), st) != cudaSuccess) {
+        *xo = nullptr;
+        cudaGetLastError();
+        return VD_ERR_OOM;
+      }
+      x = static_cast<double*>(*xo);
+    }
+    c->x = x;
     void* mem = nullptr;
-    if (cudaMallocAsync(&mem, db + wb + 256, st) != cudaSuccess) return VD_ERR_OOM;
+    if (cudaMallocAsync(&mem, db + wb + 256, st) != cudaSuccess) {
+      cudaGetLastError();
+      return VD_ERR_OOM;
+    }
     char* base = static_cast<char*>(mem);
     vd_status e = vd_density_set(G, VD_OP_PRESSURE, r.rho, base, db, st);
     vd_solve_info info{};
     if (e == VD_OK)
-      e = vd_solve(G, VD_OP_PRESSURE, (vd_solver)r.solver, nullptr, &sp, r.b, r.x, &info,
+      e = vd_solve(G, VD_OP_PRESSURE, (vd_solver)r.solver, nullptr, &sp, r.b, x, &info,
                    base + ((db + 255) & ~(size_t)255), wb, st);
     cudaFreeAsync(mem, st);
     cudaStreamSynchronize(st);
     c->iters = info.iters;
     c->relres_true = info.relres_true;
     return e;
+  }
+
+  // remove a server-owned solution (mu held); optionally copy it out first
+  vd_status take_owned(unsigned long long id, double* dst, cudaStream_t st) {
+    auto it = owned.find(id);
+    if (it == owned.end()) return vd::fail(VD_ERR_INVALID_ARG, "no server-owned solution with this id");
+    cudaStream_t fs = aux;
+    if (dst) {   // the copy and the free are ordered on the caller's stream
+      if (cudaMemcpyAsync(dst, it->second.p, it->second.size, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return vd::fail(VD_ERR_CUDA, "copy of the solution failed");
+      fs = st;
+    }
+    cudaFreeAsync(it->second.p, fs);
+    reserved -= it->second.bytes;
+    owned.erase(it);
+    admit_locked();
+    return VD_OK;
   }
 
   static vd_solve_params request_params(const vd_request& r) {
@@ -176,6 +228,7 @@ vd_status vd_server_create(const vd_server_params* p, vd_server** out) {
     unsigned long long thr = ~0ull;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
+  cudaStreamCreateWithFlags(&S->aux, cudaStreamNonBlocking);
   for (int i = 0; i < p->max_inflight; ++i) S->workers.emplace_back([S] { S->worker_main(); });
   *out = S;
   return VD_OK;
@@ -187,11 +240,11 @@ size_t vd_server_request_bytes(const vd_request* r) {
   if (!vd::grid_desc_only(r->ndim, r->n, r->L, &G)) return 0;
   vd_solve_params sp = vd_server::request_params(*r);
   return vd_density_bytes(&G, VD_OP_PRESSURE) + vd_workspace_bytes(&G, VD_OP_PRESSURE, (vd_solver)r->solver, &sp) +
-         512;
+         512 + (r->x ? 0 : out_bytes(*r));
 }
 
 vd_status vd_server_submit(vd_server* S, const vd_request* r, size_t bytes) {
-  if (!S || !r || !r->rho || !r->b || !r->x) return vd::fail(VD_ERR_INVALID_ARG, "null argument");
+  if (!S || !r || !r->rho || !r->b) return vd::fail(VD_ERR_INVALID_ARG, "null argument");
   if (r->solver < 0 || r->solver > 2) return vd::fail(VD_ERR_INVALID_ARG, "unknown solver");
   if (bytes == 0) return vd::fail(VD_ERR_INVALID_ARG, "request size unknown (use vd_server_request_bytes)");
   std::lock_guard<std::mutex> lk(S->mu);
@@ -209,6 +262,18 @@ int vd_server_poll(vd_server* S, vd_completion* out, int max) {
   for (int i = 0; i < n; ++i) out[i] = S->done[i];
   S->done.erase(S->done.begin(), S->done.begin() + n);
   return n;
+}
+
+vd_status vd_server_fetch(vd_server* S, unsigned long long id, double* dst, vd_stream stream) {
+  if (!S || !dst) return vd::fail(VD_ERR_INVALID_ARG, "null argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  return S->take_owned(id, dst, (cudaStream_t)stream);
+}
+
+vd_status vd_server_release(vd_server* S, unsigned long long id) {
+  if (!S) return vd::fail(VD_ERR_INVALID_ARG, "null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  return S->take_owned(id, nullptr, nullptr);
 }
 
 vd_status vd_server_drain(vd_server* S) {
@@ -239,6 +304,9 @@ vd_status vd_server_destroy(vd_server* S) {
   }
   S->cv_work.notify_all();
   for (auto& t : S->workers) t.join();
+  for (auto& kv : S->owned) cudaFreeAsync(kv.second.p, S->aux);
+  cudaStreamSynchronize(S->aux);
+  cudaStreamDestroy(S->aux);
   delete S;
   return VD_OK;
 }

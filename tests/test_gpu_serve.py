@@ -123,3 +123,43 @@ def test_server_concurrent_identical_requests_bitwise(precision):
     assert all(c.status == 0 and c.iters == info["iters"] for c in comps)
     bad = [i for i, x in enumerate(xs) if not torch.equal(x, ref)]
     assert not bad, bad
+
+
+def test_server_owned_solutions_fetch_and_release():
+    """Requests without an output buffer: the solution stays in server memory (counted in
+    the budget) until fetched or released; fetched results equal the solves alone."""
+    cases = make_cases()[:6]
+    alone, dev = [], []
+    for (n, L, rho, f, tol, solver) in cases:
+        G = vd.Grid(n, L)
+        r = torch.from_numpy(rho).cuda()
+        b = torch.from_numpy(f).cuda()
+        G.set_density(r)
+        x, info = G.solve("pressure", solver, b, tol=tol, max_it=500, precision="mixed_dd")
+        alone.append(x.clone())
+        dev.append((r, b))
+    torch.cuda.synchronize()
+    S = vd.vd_server_create(max_inflight=3, hbm_budget=0)
+    try:
+        reqs = [vd.make_request(i, c[0], c[1], dev[i][0], dev[i][1], None, solver=c[5], tol=c[4])
+                for i, c in enumerate(cases)]
+        for q in reqs:
+            vd.vd_server_submit(S, q, vd.vd_server_request_bytes(q))
+        vd.vd_server_drain(S)
+        comps = vd.vd_server_poll(S, 64)
+        assert len(comps) == len(cases) and all(c.status == 0 and c.x for c in comps)
+        held = vd.vd_server_stats(S)["reserved"]
+        assert held >= sum(8 * int(np.prod(c[0])) for c in cases)
+        for i in range(len(cases) - 1):
+            out = torch.empty_like(alone[i])
+            vd.vd_server_fetch(S, i, out)
+            torch.cuda.synchronize()
+            assert torch.equal(out, alone[i]), i
+        last = len(cases) - 1
+        vd.vd_server_release(S, last)
+        assert vd.vd_server_stats(S)["reserved"] == 0
+        with pytest.raises(vd.VDError) as e:
+            vd.vd_server_release(S, last)
+        assert e.value.status == vd.VD_ERR_INVALID_ARG
+    finally:
+        vd.vd_server_destroy(S)
