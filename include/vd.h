@@ -55,7 +55,19 @@ typedef enum {
   VD_ERR_NO_DENSITY = 8      /* an operator was used before vd_density_set */
 } vd_status;
 
-typedef enum { VD_OP_PRESSURE = 0, VD_OP_VELOCITY = 1 } vd_op;
+/*
+ * Operators.  VD_OP_PRESSURE: L~_rho phi = sum_j D_j(rho^-1 D_j phi) (Eq. VDINSE.Lrho.num).
+ * VD_OP_VELOCITY: V~_rho (Eq. VDINSE.zeta with the Crank--Nicolson factor a).
+ * VD_OP_KRHO: the modified-Helmholtz form of the pressure equation (Sec. 4.2, Eq. VDINSE.Krho)
+ * for Phi = phi / sqrt(rho): K~ Phi = Lap Phi + c Phi with the full-wavenumber Laplacian
+ * (symbol -|k|^2, Nyquist kept) and c = -Lap(w) / w, w = rho^-1/2 -- the paper's coefficient
+ * Lap rho / (2 rho) - 3 |grad rho|^2 / (4 rho^2), formed so that K~ w = 0 holds exactly.  Its
+ * preconditioner is the pseudo-inverse of that Laplacian (the mean removed); a solve returns
+ * the zero-mean Phi for the right-hand side projected onto the w-orthogonal range (pass
+ * sqrt(rho) f to solve the pressure equation; phi = sqrt(rho) Phi).  Two scalar transforms
+ * per apply instead of 2 ndim.
+ */
+typedef enum { VD_OP_PRESSURE = 0, VD_OP_VELOCITY = 1, VD_OP_KRHO = 2 } vd_op;
 typedef enum { VD_SOLVER_CG = 0, VD_SOLVER_GMRES = 1, VD_SOLVER_RMR = 2 } vd_solver;
 typedef enum {
   VD_PREC_FP64 = 0,  /* every transform, product and reduction in IEEE double */
@@ -119,7 +131,9 @@ size_t vd_grid_modes(const vd_grid* grid);
  * Density data: bytes of the caller-owned device buffer that vd_density_set fills with
  * rho, 1/(N rho) (double and float) and, when `op` is VD_OP_VELOCITY, the spectral first
  * and second derivatives D_j rho and D_i D_j rho (reading: the paper does not say how
- * they are formed; they are the Fourier derivatives of the grid density).
+ * they are formed; they are the Fourier derivatives of the grid density).  With VD_OP_KRHO
+ * it also holds the coefficient c/N of K~ (double, float, float-pair) and the normalised
+ * spectrum of w = rho^-1/2; the pressure operator stays usable with that buffer.
  */
 size_t vd_density_bytes(const vd_grid* grid, vd_op op);
 
@@ -137,9 +151,9 @@ vd_status vd_density_set(vd_grid* grid, vd_op op, const double* rho, void* dens_
 size_t vd_workspace_bytes(const vd_grid* grid, vd_op op, vd_solver solver, const vd_solve_params* params);
 
 /*
- * out = A(in) on physical fields, A = L~_rho (pressure, scalar field) or V~_rho (velocity,
- * ndim-component field, params required).  in and out may not alias.  Forward transform,
- * spectral apply, inverse transform, all on `stream`.
+ * out = A(in) on physical fields, A = L~_rho (pressure, scalar field), K~ (VD_OP_KRHO, scalar
+ * field) or V~_rho (velocity, ndim-component field, params required).  in and out may not
+ * alias.  Forward transform, spectral apply, inverse transform, all on `stream`.
  */
 vd_status vd_apply_op(const vd_grid* grid, vd_op op, const vd_op_params* params, const double* in, double* out,
                       void* ws, size_t ws_bytes, vd_stream stream);
@@ -147,7 +161,8 @@ vd_status vd_apply_op(const vd_grid* grid, vd_op op, const vd_op_params* params,
 /*
  * out = M(in): the constant-density inverse, diagonal in Fourier space.
  * Pressure: multiply by -1/|k~|^2, 0 on the null-space modes (pseudo-inverse of the
- * Laplacian).  Velocity: multiply every component by 1/(1 + a |k~|^2) (Eq. VDINSE.V).
+ * Laplacian).  VD_OP_KRHO: multiply by -1/|k|^2 (full wavenumbers), 0 for the mean only.
+ * Velocity: multiply every component by 1/(1 + a |k~|^2) (Eq. VDINSE.V).
  */
 vd_status vd_apply_precond(const vd_grid* grid, vd_op op, const vd_op_params* params, const double* in, double* out,
                            void* ws, size_t ws_bytes, vd_stream stream);
@@ -156,7 +171,8 @@ vd_status vd_apply_precond(const vd_grid* grid, vd_op op, const vd_op_params* pa
  * Solve A x = b (physical fields) with the chosen Krylov method, right-preconditioned by
  * M (GMRES, RMR) or split-preconditioned (CG).  Pressure right-hand sides are first
  * projected onto the range of L~ (their null-space modes are removed); x is returned
- * orthogonal to the null space.  CG with VD_OP_VELOCITY is rejected (VD_ERR_INVALID_ARG:
+ * orthogonal to the null space.  VD_OP_KRHO right-hand sides lose their component along
+ * w = rho^-1/2 and x is returned zero-mean.  CG with VD_OP_VELOCITY is rejected (VD_ERR_INVALID_ARG:
  * V_rho is not symmetric, Sec. 3.1).  x is input (initial guess if use_x0) and output.
  * info (optional, host) receives iteration counts, residuals and history.  Returns the
  * solve status (VD_OK when converged).

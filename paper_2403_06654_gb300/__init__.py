@@ -25,10 +25,10 @@ VD_OK, VD_ERR_INVALID_ARG, VD_ERR_OOM, VD_ERR_CUDA = 0, 1, 2, 3
 VD_ERR_NOT_CONVERGED, VD_ERR_BREAKDOWN, VD_ERR_DIVERGED, VD_ERR_NONFINITE, VD_ERR_NO_DENSITY = 4, 5, 6, 7, 8
 STATUS_NAMES = {0: "converged", 1: "invalid_arg", 2: "oom", 3: "cuda", 4: "max_iter", 5: "breakdown",
                 6: "diverged", 7: "nonfinite", 8: "no_density"}
-VD_OP_PRESSURE, VD_OP_VELOCITY = 0, 1
+VD_OP_PRESSURE, VD_OP_VELOCITY, VD_OP_KRHO = 0, 1, 2
 VD_SOLVER_CG, VD_SOLVER_GMRES, VD_SOLVER_RMR = 0, 1, 2
 VD_PREC_FP64, VD_PREC_MIXED, VD_PREC_MIXED_DD = 0, 1, 2
-OPS = {"pressure": VD_OP_PRESSURE, "velocity": VD_OP_VELOCITY}
+OPS = {"pressure": VD_OP_PRESSURE, "velocity": VD_OP_VELOCITY, "krho": VD_OP_KRHO}
 SOLVERS = {"cg": VD_SOLVER_CG, "gmres": VD_SOLVER_GMRES, "rmr": VD_SOLVER_RMR}
 PRECISIONS = {"fp64": VD_PREC_FP64, "mixed": VD_PREC_MIXED, "mixed_dd": VD_PREC_MIXED_DD}
 

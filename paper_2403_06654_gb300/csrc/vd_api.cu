@@ -278,6 +278,12 @@ struct DensLayout {
   double* grho;     // d fields
   double* hrho;     // 6 fields, slot hidx(i, j)
   cpx<double>* s0;  // scratch spectral fields (2)
+  // K_rho data
+  double* kw;       // w = rho^-1/2
+  double* kc_s;     // c/N
+  float* kc_f;
+  dd* kc_dd;
+  cpx<double>* kw_hat;   // spectrum of w, unit Parseval norm
 };
 
 static DensLayout dens_layout(const vd_grid* G, vd_op op, void* base, size_t* bytes) {
@@ -292,13 +298,55 @@ static DensLayout dens_layout(const vd_grid* G, vd_op op, void* base, size_t* by
   L.stats = c.take<double>(3 * 1024 * 8);
   L.grho = L.hrho = nullptr;
   L.s0 = nullptr;
+  L.kw = L.kc_s = nullptr;
+  L.kc_f = nullptr;
+  L.kc_dd = nullptr;
+  L.kw_hat = nullptr;
   if (op == VD_OP_VELOCITY) {
     L.grho = c.take<double>(nr * 8 * g.ndim);
     L.hrho = c.take<double>(nr * 8 * 6);   // indexed by hidx(i, j) in [0, 6)
     L.s0 = c.take<cpx<double>>(nc * 16 * 2);
   }
+  if (op == VD_OP_KRHO) {
+    L.kw = c.take<double>(nr * 8);
+    L.kc_s = c.take<double>(nr * 8);
+    L.kc_f = c.take<float>(nr * 4);
+    L.kc_dd = c.take<dd>(nr * sizeof(dd));
+    L.kw_hat = c.take<cpx<double>>(nc * 16);
+    L.s0 = c.take<cpx<double>>(nc * 16 * 2);   // symbol + transform scratch of the preparation
+  }
   *bytes = c.off;
   return L;
+}
+
+// w = rho^-1/2 and per-block partial sums of w^2 (fixed grid: deterministic)
+__global__ void k_krho_w(long long n, const double* __restrict__ rho, double* __restrict__ w,
+                         double* __restrict__ part) {
+  __shared__ double sm[256];
+  double s = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double v = 1.0 / sqrt(rho[e]);
+    w[e] = v;
+    s += v * v;
+  }
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) sm[threadIdx.x] += sm[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// c = -Lap(w)/w; stored as c/N in double, float and float-pair (lapw may alias cs)
+__global__ void k_krho_coef(long long n, const double* __restrict__ w, const double* lapw, double invN, double* cs,
+                            float* __restrict__ cf, dd* __restrict__ cdd) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double c = -lapw[e] / w[e] * invN;
+    cs[e] = c;
+    cf[e] = (float)c;
+    cdd[e] = dd_from_double(c);
+  }
 }
 
 }  // namespace vd
@@ -314,7 +362,8 @@ size_t vd_density_bytes(const vd_grid* G, vd_op op) {
 
 vd_status vd_density_set(vd_grid* G, vd_op op, const double* rho, void* ws, size_t ws_bytes, vd_stream stream) {
   if (!G || !rho || !ws) return fail(VD_ERR_INVALID_ARG, "null argument");
-  if (op != VD_OP_PRESSURE && op != VD_OP_VELOCITY) return fail(VD_ERR_INVALID_ARG, "unknown operator");
+  if (op != VD_OP_PRESSURE && op != VD_OP_VELOCITY && op != VD_OP_KRHO)
+    return fail(VD_ERR_INVALID_ARG, "unknown operator");
   cudaStream_t st = (cudaStream_t)stream;
   size_t need = 0;
   DensLayout L = dens_layout(G, op, ws, &need);
@@ -371,6 +420,39 @@ vd_status vd_density_set(vd_grid* G, vd_op op, const double* rho, void* ws, size
     VD_CUDA(cudaGetLastError());
     G->has_velocity_data = 1;
   }
+  G->has_krho_data = 0;
+  G->kc_s = nullptr;
+  G->kc_f = nullptr;
+  G->kc_dd = nullptr;
+  G->kw_hat = nullptr;
+  if (op == VD_OP_KRHO) {
+    const size_t nc = (size_t)g.ncplx;
+    { k_krho_w<<<blocks, 256, 0, st>>>(g.nreal, rho, L.kw, L.stats); count_launch(); }
+    std::vector<double> part(blocks);
+    VD_CUDA(cudaMemcpyAsync(part.data(), L.stats, part.size() * 8, cudaMemcpyDeviceToHost, st));
+    VD_CUDA(cudaStreamSynchronize(st));
+    double ww = 0.0;
+    for (int b = 0; b < blocks; ++b) ww += part[b];
+    // Lap w with the full-wavenumber symbol, then c = -Lap(w)/w
+    cpx<double>* sym = L.s0;
+    cpx<double>* tmp = L.s0 + nc;
+    fwd_transform<double>(G, L.kw, L.kw_hat, st);
+    fill_symbol<double>(G, SYM_KLAP, 0.0, reinterpret_cast<double*>(sym), st);
+    Mult m;
+    m.sym = 1;
+    m.symarr = sym;
+    inv_transform<double>(G, L.kw_hat, m, L.kc_s, tmp, st);
+    { k_krho_coef<<<blocks, 256, 0, st>>>(g.nreal, L.kw, L.kc_s, 1.0 / (double)g.nreal, L.kc_s, L.kc_f, L.kc_dd);
+      count_launch(); }
+    // unit Parseval norm: sum over the half spectrum with weights = N sum_x w^2
+    spec_copy_scale<double>((long long)nc, L.kw_hat, 1.0 / std::sqrt((double)g.nreal * ww), L.kw_hat, st);
+    VD_CUDA(cudaGetLastError());
+    G->kc_s = L.kc_s;
+    G->kc_f = L.kc_f;
+    G->kc_dd = L.kc_dd;
+    G->kw_hat = L.kw_hat;
+    G->has_krho_data = 1;
+  }
   return VD_OK;
 }
 
@@ -401,7 +483,12 @@ struct SolveLayout {
 
 static int op_ncomp(const vd_grid* G, vd_op op) { return op == VD_OP_VELOCITY ? G->g.ndim : 1; }
 static int op_tmp_fields(const vd_grid* G, vd_op op) {
-  return op == VD_OP_VELOCITY ? velocity_tmp_fields(G->g.ndim) : pressure_tmp_fields(G->g.ndim);
+  if (op == VD_OP_VELOCITY) return velocity_tmp_fields(G->g.ndim);
+  if (op == VD_OP_KRHO) return krho_tmp_fields(G->g.ndim);
+  return pressure_tmp_fields(G->g.ndim);
+}
+static int op_symbol(vd_op op) {
+  return op == VD_OP_VELOCITY ? SYM_VELOCITY : (op == VD_OP_KRHO ? SYM_KLAP_INV : SYM_PRESSURE);
 }
 
 static SolveLayout solve_layout(const vd_grid* G, vd_op op, int solver, int restart, int maxit, int precision,
@@ -448,7 +535,9 @@ static void apply_cb(const SpecSystem& sys, const void* in, void* out, bool with
                      cudaStream_t st) {
   const vd_grid* G = sys.G;
   const T* sym = with_sym ? (const T*)sys.sym : nullptr;
-  if (sys.ncomp == 1 && sys.ctx[1] == nullptr) {
+  if (sys.ctx[1] == (void*)2) {
+    apply_krho_spec<T>(G, (const cpx<T>*)in, (cpx<T>*)out, sym, (const T*)sys.ctx[0], (cpx<T>*)sys.ctx[2], done, st);
+  } else if (sys.ncomp == 1 && sys.ctx[1] == nullptr) {
     apply_pressure_spec<T>(G, (const cpx<T>*)in, (cpx<T>*)out, sym, (const T*)sys.ctx[0], (cpx<T>*)sys.ctx[2], done, st);
   } else {
     apply_velocity_spec<T>(G, (const cpx<T>*)in, (cpx<T>*)out, sym, sys.a, sys.inv_sc, (cpx<T>*)sys.ctx[2], done, st);
@@ -465,8 +554,13 @@ static SpecSystem make_system(const vd_grid* G, vd_op op, const vd_op_params* p,
   s.sym = sym;
   s.is_float = sizeof(T) == 4;
   s.apply = &apply_cb<T>;
-  s.ctx[0] = (sizeof(T) == 8) ? (void*)G->rinv_s : (void*)G->rinv_s_f;
-  s.ctx[1] = (op == VD_OP_VELOCITY) ? (void*)1 : nullptr;
+  if (op == VD_OP_KRHO) {
+    s.ctx[0] = (sizeof(T) == 8) ? (void*)G->kc_s : (void*)G->kc_f;
+    s.ctx[1] = (void*)2;
+  } else {
+    s.ctx[0] = (sizeof(T) == 8) ? (void*)G->rinv_s : (void*)G->rinv_s_f;
+    s.ctx[1] = (op == VD_OP_VELOCITY) ? (void*)1 : nullptr;
+  }
   s.ctx[2] = tmp;
   s.a = p ? p->a : 0.0;
   s.inv_sc = p ? p->inv_sc : 1.0;
@@ -475,8 +569,11 @@ static SpecSystem make_system(const vd_grid* G, vd_op op, const vd_op_params* p,
 
 static vd_status check_op(const vd_grid* G, vd_op op, const vd_op_params* p) {
   if (!G) return fail(VD_ERR_INVALID_ARG, "null grid");
-  if (op != VD_OP_PRESSURE && op != VD_OP_VELOCITY) return fail(VD_ERR_INVALID_ARG, "unknown operator");
+  if (op != VD_OP_PRESSURE && op != VD_OP_VELOCITY && op != VD_OP_KRHO)
+    return fail(VD_ERR_INVALID_ARG, "unknown operator");
   if (!G->has_density) return fail(VD_ERR_NO_DENSITY, "vd_density_set has not been called");
+  if (op == VD_OP_KRHO && !G->has_krho_data)
+    return fail(VD_ERR_NO_DENSITY, "density was not set for the K_rho operator");
   if (op == VD_OP_VELOCITY) {
     if (!p) return fail(VD_ERR_INVALID_ARG, "velocity operator needs vd_op_params");
     if (!G->has_velocity_data) return fail(VD_ERR_NO_DENSITY, "density was set for the pressure operator only");
@@ -541,7 +638,9 @@ vd_status vd_apply_precond(const vd_grid* G, vd_op op, const vd_op_params* p, co
   SolveLayout L = solve_layout(G, op, VD_SOLVER_RMR, 1, 1, VD_PREC_FP64, ws, &need);
   if (ws_bytes < need) return fail(VD_ERR_OOM, "workspace too small");
   const int ncomp = op_ncomp(G, op);
-  fill_symbol<double>(G, op == VD_OP_PRESSURE ? SYM_PRESSURE : SYM_VELOCITY, p ? p->a : 0.0, L.sym, st);
+  if (op != VD_OP_PRESSURE && op != VD_OP_VELOCITY && op != VD_OP_KRHO)
+    return fail(VD_ERR_INVALID_ARG, "unknown operator");
+  fill_symbol<double>(G, op_symbol(op), p ? p->a : 0.0, L.sym, st);
   fwd_all(G, ncomp, in, L.bh, st);
   for (int c = 0; c < ncomp; ++c) {
     Mult m;
@@ -616,24 +715,34 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
   const GridDesc& g = G->g;
   const int ncomp = op_ncomp(G, op);
   const long long len = g.ncplx * ncomp;
-  const int symkind = (op == VD_OP_PRESSURE) ? SYM_PRESSURE : SYM_VELOCITY;
+  const int symkind = op_symbol(op);
   // the reduction ticket counter must start at zero (the workspace is uninitialised memory)
   VD_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned), st));
   fill_symbol<double>(G, symkind, opp ? opp->a : 0.0, L.sym, st);
   // spectral right-hand side and initial guess (float-pair transforms in VD_PREC_MIXED_DD
   // pressure solves, double otherwise)
-  const bool dd_io = prm->precision == VD_PREC_MIXED_DD && op == VD_OP_PRESSURE;
+  const bool dd_io = prm->precision == VD_PREC_MIXED_DD && op != VD_OP_VELOCITY;
   if (dd_io) fwd_transform_dd(G, b, L.bh, L.tmp, st);
   else fwd_all(G, ncomp, b, L.bh, st);
   if (op == VD_OP_PRESSURE) spec_project<double>(G, 1, L.bh, st);
+  KWork kw{L.ks, L.partials, L.counter, L.hist};
+  if (op == VD_OP_KRHO) {
+    // remove the component along w = rho^-1/2 (the range of K~ is w-orthogonal)
+    SpecSystem s1{};
+    s1.G = G;
+    s1.len = len;
+    s1.h0 = g.h0;
+    const double d = spec_dot_host<double>(s1, L.bh, G->kw_hat, kw, st);
+    spec_axpy<double>(len, -d, G->kw_hat, L.bh, st);
+  }
   if (prm->use_x0) {
     if (dd_io) fwd_transform_dd(G, x, L.xh, L.tmp, st);
     else fwd_all(G, ncomp, x, L.xh, st);
     if (op == VD_OP_PRESSURE) spec_project<double>(G, 1, L.xh, st);
+    if (op == VD_OP_KRHO) VD_CUDA(cudaMemsetAsync(L.xh, 0, sizeof(cpx<double>), st));   // zero mean
   } else {
     VD_CUDA(cudaMemsetAsync(L.xh, 0, sizeof(cpx<double>) * len, st));
   }
-  KWork kw{L.ks, L.partials, L.counter, L.hist};
   SolveOpts so;
   so.solver = solver;
   so.tol = prm->tol;
@@ -656,9 +765,10 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
     fill_symbol<float>(G, symkind, opp ? opp->a : 0.0, L.sym_f, st);
     SpecSystem sys32 = make_system<float>(G, op, opp, L.sym_f, L.tmp_f);
     // residual operator of the refinement: double, or float-pair transforms (pressure)
-    const bool use_dd = prm->precision == VD_PREC_MIXED_DD && op == VD_OP_PRESSURE;
+    const bool use_dd = prm->precision == VD_PREC_MIXED_DD && op != VD_OP_VELOCITY;
     auto resid_apply = [&](const cpx<double>* xin, cpx<double>* yout) {
-      if (use_dd) apply_pressure_spec_dd(G, xin, yout, L.tmp, nullptr, st);
+      if (use_dd && op == VD_OP_KRHO) apply_krho_spec_dd(G, xin, yout, L.tmp, nullptr, st);
+      else if (use_dd) apply_pressure_spec_dd(G, xin, yout, L.tmp, nullptr, st);
       else sys64.apply(sys64, xin, yout, false, nullptr, st);
     };
     const double bb = spec_norm2_host<double>(sys64, L.bh, kw, st);

@@ -101,6 +101,11 @@ enum SymbolKind : int {
   SYM_PRESSURE = 1,   // -1/|k~|^2, 0 where |k~| = 0   (pseudo-inverse of the Laplacian)
   SYM_VELOCITY = 2,   // 1/(1 + a |k~|^2)              (inverse of I - a Lap)
   SYM_PROJECT = 3,    // 1 except 0 on the 2^d corner modes (projection onto the range)
+  SYM_KLAP_INV = 4,   // -1/|k|^2 with full wavenumbers, 0 for the mean only (K_rho preconditioner)
+  SYM_KLAP = 5,       // -|k|^2 with full wavenumbers (Laplacian of the K_rho form)
 };
+
+// signed integer frequency of index m on an axis of n points (Nyquist index kept as -n/2)
+__host__ __device__ __forceinline__ int freq_full(int m, int n) { return (2 * m < n) ? m : m - n; }
 
 }  // namespace vd

@@ -23,9 +23,16 @@ struct vd_grid {
   const double* grho[3] = {nullptr, nullptr, nullptr};     // D_j rho
   const double* hrho[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // D_i D_j rho (i<=j)
   const double* rho = nullptr;       // copy of rho
+  // K_rho data (set by vd_density_set with VD_OP_KRHO): c/N with c = -Lap(w)/w, w = rho^-1/2,
+  // and the spectrum of w normalised to unit Parseval norm
+  const double* kc_s = nullptr;
+  const float* kc_f = nullptr;
+  const void* kc_dd = nullptr;
+  const void* kw_hat = nullptr;      // cpx<double>, ncplx
   double rho_min = 0, rho_max = 0;
   int has_density = 0;
   int has_velocity_data = 0;
+  int has_krho_data = 0;
 };
 
 namespace vd {
@@ -99,8 +106,20 @@ void apply_velocity_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const 
 int velocity_tmp_fields(int ndim);   // spectral-field-sized temporaries
 int pressure_tmp_fields(int ndim);
 
+// K_rho operator in spectral space: out = K~ (S in) = Lap S in + F(c F^-1(S in)); with S the
+// pseudo-inverse of Lap (symarr non-null) the local term is the mean-free part of `in`.
+// coef_s: c/N (physical, type T).  tmp: one spectral field (2D/3D), none (1D).
+template <typename T>
+void apply_krho_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, const T* coef_s,
+                     cpx<T>* tmp, const int* done, cudaStream_t st);
+// the same with float-pair transforms: double spectral fields in and out, no preconditioner
+void apply_krho_spec_dd(const vd_grid* G, const cpx<double>* in, cpx<double>* out, void* tmp, const int* done,
+                        cudaStream_t st);
+int krho_tmp_fields(int ndim);
+
 // symbol arrays (real, ncplx): pressure -1/|k~|^2 (0 on corners), velocity 1/(1+a|k~|^2),
-// projection 1 / 0 on corners
+// projection 1 / 0 on corners, K_rho preconditioner -1/|k|^2 (full k, 0 for the mean),
+// full-wavenumber Laplacian -|k|^2
 template <typename T>
 void fill_symbol(const vd_grid* G, int kind, double a, T* out, cudaStream_t st);
 

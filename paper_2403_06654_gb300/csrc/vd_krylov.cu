@@ -443,6 +443,20 @@ __global__ void __launch_bounds__(kRedThreads) k_norms(Ix ix, const cpx<T>* __re
     epilogue<NV>(epi, t, ra.ks, ra.hist, ra.tol, 0, 0);
 }
 
+// weighted (Parseval) inner product of two spectral vectors -> ks->rr
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_pdot(Ix ix, const cpx<T>* __restrict__ a,
+                                                      const cpx<T>* __restrict__ b, RedArgs ra) {
+  Acc<T> a0;
+  IX_LOOP(ix) {
+    const cpx<T> u = a[e], v = b[e];
+    a0.add(pweight<T>(kx, ix.h0) * (u.x * v.x + u.y * v.y));
+  }
+  double v[1] = {a0.total()};
+  double t[1];
+  if (reduce_last<1>(v, ra.partials, ra.counter, t) && threadIdx.x == 0) epilogue<1>(EPI_NORM, t, ra.ks, ra.hist, ra.tol, 0, 0);
+}
+
 // RMR: x += alpha S r, r -= alpha w; reduce [rr]
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_rmr_update(Ix ix, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r,
@@ -665,6 +679,18 @@ double spec_norm2_host(const SpecSystem& sys, const void* v, const KWork& kw, cu
   return rr;
 }
 
+template <typename T>
+double spec_dot_host(const SpecSystem& sys, const void* a, const void* b, const KWork& kw, cudaStream_t st) {
+  RedArgs ra{kw.ks, kw.partials, kw.counter, kw.hist, 0.0};
+  const int rb = red_blocks(sys.len);
+  const Ix ix = mkix(sys.len, sys.h0, sys.G->g.ncplx, rb, kRedThreads);
+  { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)2 * sys.len * sizeof(cpx<T>), 0.0); k_pdot<T><<<rb, kRedThreads, 0, st>>>(ix, (const cpx<T>*)a, (const cpx<T>*)b, ra); }
+  double rr = 0.0;
+  cudaMemcpyAsync(&rr, &kw.ks->rr, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  return rr;
+}
+
 // ---------------------------------------------------------------------------------------
 // host drivers
 // ---------------------------------------------------------------------------------------
@@ -843,6 +869,7 @@ template void spec_sub<double>(long long, const void*, const void*, void*, cudaS
 template void spec_sub<float>(long long, const void*, const void*, void*, cudaStream_t);
 template void spec_project<double>(const vd_grid*, int, void*, cudaStream_t);
 template void spec_project<float>(const vd_grid*, int, void*, cudaStream_t);
+template double spec_dot_host<double>(const SpecSystem&, const void*, const void*, const KWork&, cudaStream_t);
 template double spec_norm2_host<double>(const SpecSystem&, const void*, const KWork&, cudaStream_t);
 template double spec_norm2_host<float>(const SpecSystem&, const void*, const KWork&, cudaStream_t);
 

@@ -96,6 +96,9 @@ void spec_sub(long long len, const void* b, const void* q, void* r, cudaStream_t
 // weighted norm^2 of a spectral vector -> host (synchronises)
 template <typename T>
 double spec_norm2_host(const SpecSystem& sys, const void* v, const KWork& kw, cudaStream_t st);
+// weighted inner product (a, b) of two spectral vectors, returned to the host
+template <typename T>
+double spec_dot_host(const SpecSystem& sys, const void* a, const void* b, const KWork& kw, cudaStream_t st);
 // zero the 2^d null-space coefficients of each component
 template <typename T>
 void spec_project(const vd_grid* G, int ncomp, void* v, cudaStream_t st);

@@ -357,6 +357,158 @@ void apply_pressure_spec_dd(const vd_grid* G, const cpx<double>* in, cpx<double>
 }
 
 // ---------------------------------------------------------------------------------------
+// K_rho operator (Eq. VDINSE.Krho): two scalar transforms with the coefficient multiply
+// fused into the x pass, plus the pointwise local term
+// ---------------------------------------------------------------------------------------
+
+int krho_tmp_fields(int ndim) { return ndim >= 2 ? 1 : 0; }
+
+// out += Lap S in: with_inv (S = pseudo-inverse of Lap): the mean-free part of in; otherwise
+// -|k|^2 in.  Double I/O for the float-pair path (conv), else type T.
+template <typename T>
+__global__ void k_krho_local(GridDesc g, const cpx<T>* __restrict__ in, cpx<T>* __restrict__ out, int with_inv,
+                             const int* done) {
+  if (done && *done) return;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < g.ncplx;
+       e += (long long)gridDim.x * blockDim.x) {
+    const cpx<T> v = in[e];
+    cpx<T> o = out[e];
+    if (with_inv) {
+      if (e != 0) o = o + v;
+    } else {
+      const long long line = e / g.h0;
+      const int kxi = (int)(e - line * g.h0);
+      const int kyi = (int)(line % g.n1);
+      const int kzi = (int)(line / g.n1);
+      const T kx = (T)g.kfac[0] * (T)freq_full(kxi, g.n0);
+      T k2 = kx * kx;
+      if (g.ndim >= 2) {
+        const T ky = (T)g.kfac[1] * (T)freq_full(kyi, g.n1);
+        k2 += ky * ky;
+      }
+      if (g.ndim == 3) {
+        const T kz = (T)g.kfac[2] * (T)freq_full(kzi, g.n2);
+        k2 += kz * kz;
+      }
+      o = o - scal(v, k2);
+    }
+    out[e] = o;
+  }
+}
+
+template <typename U>
+static void krho_local(const vd_grid* G, const void* in, void* out, bool with_inv, const int* done, cudaStream_t st) {
+  const long long n = G->g.ncplx;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+  k_krho_local<U><<<blocks, 256, 0, st>>>(G->g, (const cpx<U>*)in, (cpx<U>*)out, with_inv ? 1 : 0, done);
+  count_launch();
+}
+
+// out = F(c F^-1(S in)) through the pass chain; conv: float-pair arithmetic on double fields
+template <typename T>
+static void krho_transforms(const vd_grid* G, const void* in, void* out, const T* symarr, const void* coef_s,
+                            cpx<T>* tmp, const int* done, cudaStream_t st, int conv) {
+  const GridDesc& g = G->g;
+  const int S = symarr ? MUL_SYM : 0;
+  const void* tw = twtab<T>(G);
+  if (g.ndim == 1) {
+    XProg X{};
+    X.ncomp = 1;
+    X.mode = 0;
+    X.in[0] = in;
+    X.out[0] = out;
+    X.pre[0] = S;
+    X.wfield = coef_s;
+    X.scale = 0.5;
+    X.symarr = symarr;
+    X.done = done;
+    X.conv_in = conv;
+    X.conv_out = conv;
+    launch_xpass<T>(X, g, tw, st);
+    return;
+  }
+  // inverse along z (3D) and y, in the order z, y: T0 = F_y^-1 F_z^-1 (S in)
+  const void* cur = in;
+  int cin = conv;
+  int pre = S;
+  if (g.ndim == 3) {
+    AxisProg P{};
+    P.nxf = 1;
+    P.xf[0] = mkxf(0, 0, pre, 0, true, true);
+    P.in[0] = cur;
+    P.out[0] = tmp;
+    P.symarr = symarr;
+    P.done = done;
+    P.axis = 2;
+    P.conv_in = cin;
+    launch_axis<T>(P, +1, g, tw, st);
+    cur = tmp;
+    cin = 0;
+    pre = 0;
+  }
+  {
+    AxisProg P{};
+    P.nxf = 1;
+    P.xf[0] = mkxf(0, 0, pre, 0, true, true);
+    P.in[0] = cur;
+    P.out[0] = tmp;
+    P.symarr = symarr;
+    P.done = done;
+    P.axis = 1;
+    P.conv_in = cin;
+    launch_axis<T>(P, +1, g, tw, st);
+  }
+  // x fused (in place): T0 <- R2C(c C2R(T0))
+  {
+    XProg X{};
+    X.ncomp = 1;
+    X.mode = 0;
+    X.in[0] = tmp;
+    X.out[0] = tmp;
+    X.wfield = coef_s;
+    X.scale = 0.5;
+    X.done = done;
+    launch_xpass<T>(X, g, tw, st);
+  }
+  // forward along y, then z
+  {
+    AxisProg P{};
+    P.nxf = 1;
+    P.xf[0] = mkxf(0, 0, 0, 0, true, true);
+    P.in[0] = tmp;
+    P.out[0] = (g.ndim == 3) ? (void*)tmp : out;
+    P.done = done;
+    P.axis = 1;
+    P.conv_out = (g.ndim == 3) ? 0 : conv;
+    launch_axis<T>(P, -1, g, tw, st);
+  }
+  if (g.ndim == 3) {
+    AxisProg P{};
+    P.nxf = 1;
+    P.xf[0] = mkxf(0, 0, 0, 0, true, true);
+    P.in[0] = tmp;
+    P.out[0] = out;
+    P.done = done;
+    P.axis = 2;
+    P.conv_out = conv;
+    launch_axis<T>(P, -1, g, tw, st);
+  }
+}
+
+template <typename T>
+void apply_krho_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, const T* coef_s,
+                     cpx<T>* tmp, const int* done, cudaStream_t st) {
+  krho_transforms<T>(G, in, out, symarr, coef_s, tmp, done, st, 0);
+  krho_local<T>(G, in, out, symarr != nullptr, done, st);
+}
+
+void apply_krho_spec_dd(const vd_grid* G, const cpx<double>* in, cpx<double>* out, void* tmp, const int* done,
+                        cudaStream_t st) {
+  krho_transforms<dd>(G, in, out, nullptr, G->kc_dd, reinterpret_cast<cpx<dd>*>(tmp), done, st, 1);
+  krho_local<double>(G, in, out, false, done, st);
+}
+
+// ---------------------------------------------------------------------------------------
 // velocity operator
 // ---------------------------------------------------------------------------------------
 
@@ -485,20 +637,24 @@ __global__ void k_fill_symbol(GridDesc g, int kind, double a, T* __restrict__ ou
     const int kxi = (int)(e - line * g.h0);
     const int kyi = (int)(line % g.n1);
     const int kzi = (int)(line / g.n1);
-    const double kx = g.kfac[0] * freq_tilde(kxi, g.n0);
+    // K_rho symbols use the full wavenumbers (Nyquist kept); the others k~
+    const bool full = (kind == SYM_KLAP_INV || kind == SYM_KLAP);
+    auto fq = [&](int m, int n) { return full ? freq_full(m, n) : freq_tilde(m, n); };
+    const double kx = g.kfac[0] * fq(kxi, g.n0);
     double k2 = kx * kx;
     if (g.ndim >= 2) {
-      const double ky = g.kfac[1] * freq_tilde(kyi, g.n1);
+      const double ky = g.kfac[1] * fq(kyi, g.n1);
       k2 += ky * ky;
     }
     if (g.ndim == 3) {
-      const double kz = g.kfac[2] * freq_tilde(kzi, g.n2);
+      const double kz = g.kfac[2] * fq(kzi, g.n2);
       k2 += kz * kz;
     }
     double v = 1.0;
-    if (kind == SYM_PRESSURE) v = (k2 == 0.0) ? 0.0 : -1.0 / k2;
+    if (kind == SYM_PRESSURE || kind == SYM_KLAP_INV) v = (k2 == 0.0) ? 0.0 : -1.0 / k2;
     else if (kind == SYM_VELOCITY) v = 1.0 / (1.0 + a * k2);
     else if (kind == SYM_PROJECT) v = (k2 == 0.0) ? 0.0 : 1.0;
+    else if (kind == SYM_KLAP) v = -k2;
     out[e] = (T)v;
   }
 }
@@ -515,6 +671,10 @@ template void fwd_transform<float>(const vd_grid*, const float*, cpx<float>*, cu
 template void inv_transform<double>(const vd_grid*, const cpx<double>*, const Mult&, double*, cpx<double>*,
                                     cudaStream_t);
 template void inv_transform<float>(const vd_grid*, const cpx<float>*, const Mult&, float*, cpx<float>*, cudaStream_t);
+template void apply_krho_spec<double>(const vd_grid*, const cpx<double>*, cpx<double>*, const double*,
+                                      const double*, cpx<double>*, const int*, cudaStream_t);
+template void apply_krho_spec<float>(const vd_grid*, const cpx<float>*, cpx<float>*, const float*, const float*,
+                                     cpx<float>*, const int*, cudaStream_t);
 template void apply_pressure_spec<double>(const vd_grid*, const cpx<double>*, cpx<double>*, const double*,
                                           const double*, cpx<double>*, const int*, cudaStream_t);
 template void apply_pressure_spec<float>(const vd_grid*, const cpx<float>*, cpx<float>*, const float*, const float*,
