@@ -292,6 +292,50 @@ vd_status vd_server_stats(vd_server* server, long long* submitted, long long* co
 vd_status vd_server_destroy(vd_server* server);
 
 /*
+ * Batched solves in one graph launch (not in the paper).  A batch holds `count` independent
+ * instances of any grids and densities; each carries a velocity system (V~_rho with its own a
+ * and 1/Sc, ndim components; b_vel/x_vel non-null), a pressure system (L~_rho; b_pres/x_pres
+ * non-null) or both.  vd_batch_create attaches every density (synchronising `stream`), lays
+ * every grid's density data and solve workspace out in the caller's device buffer `mem`
+ * (vd_batch_bytes bytes, caller-owned, alive until vd_batch_destroy) and records every solve
+ * (double precision) into one CUDA graph: each system is a branch of its own, and its Krylov
+ * loop a conditional WHILE node whose body is one iteration (one restart cycle for GMRES) and
+ * whose condition a kernel sets from the device-resident convergence flag.  vd_batch_run
+ * replays all solves with a single graph launch on `stream`, reading the right-hand sides
+ * and writing the solutions at each run (new right-hand sides need no rebuild; the buffers
+ * named at creation must stay valid).  x starts from 0.  vd_batch_info waits for the device
+ * and reports one instance's results (iterations, status, monitored and true relative
+ * residual).  CG is refused for the velocity system.  The event profiler must be off while
+ * recording.
+ */
+typedef struct vd_batch vd_batch;
+typedef struct {
+  int ndim;
+  int n[3];
+  double L[3];
+  const double* rho;     /* density (device) */
+  const double* b_vel;   /* velocity right-hand side, ndim fields (device), or null */
+  double* x_vel;         /* velocity solution, ndim fields (device) */
+  double a, inv_sc;      /* velocity operator parameters */
+  const double* b_pres;  /* pressure right-hand side (device), or null */
+  double* x_pres;        /* pressure solution (device) */
+} vd_batch_item;
+typedef struct {
+  int vel_solver;        /* VD_SOLVER_GMRES or VD_SOLVER_RMR */
+  int pres_solver;       /* any vd_solver */
+  double tol;
+  int max_it, restart;
+} vd_batch_params;
+size_t vd_batch_bytes(const vd_batch_item* items, int count, const vd_batch_params* params);
+vd_status vd_batch_create(const vd_batch_item* items, int count, const vd_batch_params* params, void* mem,
+                          size_t bytes, vd_stream stream, vd_batch** out);
+vd_status vd_batch_run(vd_batch* batch, vd_stream stream);
+vd_status vd_batch_info(vd_batch* batch, int index, vd_solve_info* vel, vd_solve_info* pres);
+/* number of nodes of the recorded graph (top level) */
+size_t vd_batch_graph_nodes(const vd_batch* batch);
+vd_status vd_batch_destroy(vd_batch* batch);
+
+/*
  * out = L~_rho(in) for callers that cannot allocate device memory (the paper has no
  * counterpart; this is an integration convenience).  Such callers include code running
  * inside a host framework whose memory pool owns the device, plugins that must keep a

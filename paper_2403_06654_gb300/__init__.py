@@ -78,6 +78,18 @@ class vd_completion(ctypes.Structure):
                 ("t_done", ctypes.c_double), ("x", ctypes.c_void_p)]
 
 
+class vd_batch_item(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("L", ctypes.c_double * 3),
+                ("rho", ctypes.c_void_p), ("b_vel", ctypes.c_void_p), ("x_vel", ctypes.c_void_p),
+                ("a", ctypes.c_double), ("inv_sc", ctypes.c_double),
+                ("b_pres", ctypes.c_void_p), ("x_pres", ctypes.c_void_p)]
+
+
+class vd_batch_params(ctypes.Structure):
+    _fields_ = [("vel_solver", ctypes.c_int), ("pres_solver", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_it", ctypes.c_int), ("restart", ctypes.c_int)]
+
+
 class vd_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("status", ctypes.c_int),
                 ("relres", ctypes.c_double), ("relres_true", ctypes.c_double),
@@ -105,6 +117,13 @@ _SIGS = {
                       ctypes.POINTER(vd_solve_info), _P, _SZ, _P]),
     "vd_divergence": (_I, [_P, _P, _P, _P, _SZ, _P]),
     "vd_gradient": (_I, [_P, _P, _P, _P, _SZ, _P]),
+    "vd_batch_bytes": (_SZ, [ctypes.POINTER(vd_batch_item), _I, ctypes.POINTER(vd_batch_params)]),
+    "vd_batch_create": (_I, [ctypes.POINTER(vd_batch_item), _I, ctypes.POINTER(vd_batch_params), _P, _SZ, _P,
+                             ctypes.POINTER(_P)]),
+    "vd_batch_run": (_I, [_P, _P]),
+    "vd_batch_info": (_I, [_P, _I, ctypes.POINTER(vd_solve_info), ctypes.POINTER(vd_solve_info)]),
+    "vd_batch_graph_nodes": (_SZ, [_P]),
+    "vd_batch_destroy": (_I, [_P]),
     "vd_apply_pressure_noalloc": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), _P, _P, _P, _P]),
     "vd_flow_bytes": (_SZ, [_P, ctypes.POINTER(vd_flow_params)]),
     "vd_flow_create": (_I, [_P, ctypes.POINTER(vd_flow_params), _P, _SZ, ctypes.POINTER(_P)]),
@@ -545,3 +564,66 @@ class Flow:
                 "vel_status": STATUS_NAMES.get(info.vel_status, info.vel_status),
                 "pres_status": STATUS_NAMES.get(info.pres_status, info.pres_status),
                 "vel_relres": info.vel_relres, "pres_relres": info.pres_relres}
+
+
+class Batch:
+    """Many uneven solves recorded into one CUDA graph (marshalling over vd_batch_*).
+
+    items: list of dicts with keys n, L, rho and optionally b_vel/x_vel (with a, inv_sc)
+    and b_pres/x_pres (device float64 tensors).  run() is a single graph launch."""
+
+    def __init__(self, items, vel_solver="gmres", pres_solver="cg", tol=1e-10, max_it=500, restart=30,
+                 device=None, stream=None):
+        import torch
+        self._keep = []
+        arr = (vd_batch_item * len(items))()
+        for i, it in enumerate(items):
+            n = tuple(it["n"])
+            nd = len(n)
+            arr[i].ndim = nd
+            arr[i].n = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - nd)))
+            arr[i].L = (ctypes.c_double * 3)(*(list(it["L"]) + [1.0] * (3 - nd)))
+            for key in ("rho", "b_vel", "x_vel", "b_pres", "x_pres"):
+                t = it.get(key)
+                if t is not None:
+                    want = ((nd,) if key.endswith("_vel") else ()) + tuple(reversed(n))
+                    if t.dtype != torch.float64 or not t.is_cuda or tuple(t.shape) != want:
+                        raise VDError(VD_ERR_INVALID_ARG, f"item {i}: {key} must be float64 CUDA of shape {want}")
+                    setattr(arr[i], key, _ptr(t).value)
+                    self._keep.append(t)
+            arr[i].a = float(it.get("a", 0.0))
+            arr[i].inv_sc = float(it.get("inv_sc", 1.0))
+        self.params = vd_batch_params(SOLVERS[vel_solver], SOLVERS[pres_solver], tol, max_it, restart)
+        self.items = arr
+        self.count = len(items)
+        nb = int(lib().vd_batch_bytes(arr, len(items), ctypes.byref(self.params)))
+        if nb == 0:
+            raise VDError(VD_ERR_INVALID_ARG, "unsupported batch")
+        self.mem = torch.empty(nb, dtype=torch.uint8, device=device or "cuda")
+        self.h = ctypes.c_void_p()
+        _check(lib().vd_batch_create(arr, len(items), ctypes.byref(self.params), _ptr(self.mem), nb,
+                                     _stream(stream), ctypes.byref(self.h)))
+
+    def run(self, stream=None):
+        _check(lib().vd_batch_run(self.h, _stream(stream)))
+
+    def info(self, i):
+        v, p = vd_solve_info(), vd_solve_info()
+        _check(lib().vd_batch_info(self.h, i, ctypes.byref(v), ctypes.byref(p)))
+        conv = lambda x: {"status": STATUS_NAMES.get(x.status, x.status), "iters": x.iters,  # noqa: E731
+                          "relres": x.relres, "relres_true": x.relres_true}
+        return conv(v), conv(p)
+
+    def graph_nodes(self):
+        return int(lib().vd_batch_graph_nodes(self.h))
+
+    def close(self):
+        if self.h:
+            lib().vd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -596,6 +596,42 @@ static void inv_all(const vd_grid* G, int ncomp, const cpx<double>* in, double* 
   }
 }
 
+// One FP64 solve as a capturable graph fragment on st (loop bodies captured on body_st):
+// transforms, range projection, the Krylov loop as a conditional node, inverse transform,
+// true residual and the result record info[0..4] (see krylov_graph_finish).
+vd_status enqueue_solve_graph(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_params* opp, double tol,
+                              int maxit, int restart, const double* b, double* x, void* ws, size_t ws_bytes,
+                              double* info, cudaStream_t st, cudaStream_t body_st) {
+  vd_status e = check_op(G, op, opp);
+  if (e != VD_OK) return e;
+  if (op == VD_OP_KRHO) return fail(VD_ERR_INVALID_ARG, "graph solves cover the pressure and velocity operators");
+  if (solver == VD_SOLVER_CG && op == VD_OP_VELOCITY)
+    return fail(VD_ERR_INVALID_ARG, "CG needs a symmetric operator; V_rho is not symmetric");
+  if (solver == VD_SOLVER_GMRES && restart > kMaxRestart) return fail(VD_ERR_INVALID_ARG, "GMRES restart must be <= 64");
+  size_t need = 0;
+  SolveLayout L = solve_layout(G, op, solver, restart, maxit, VD_PREC_FP64, ws, &need);
+  if (ws_bytes < need) return fail(VD_ERR_OOM, "workspace too small");
+  const int ncomp = op_ncomp(G, op);
+  const long long len = G->g.ncplx * ncomp;
+  VD_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned), st));
+  fill_symbol<double>(G, op_symbol(op), opp ? opp->a : 0.0, L.sym, st);
+  fwd_all(G, ncomp, b, L.bh, st);
+  if (op == VD_OP_PRESSURE) spec_project<double>(G, 1, L.bh, st);
+  VD_CUDA(cudaMemsetAsync(L.xh, 0, sizeof(cpx<double>) * len, st));
+  KWork kw{L.ks, L.partials, L.counter, L.hist};
+  SolveOpts so;
+  so.solver = solver;
+  so.tol = tol;
+  so.maxit = maxit;
+  so.restart = restart;
+  so.check_every = 1;
+  so.x_zero = 1;
+  SpecSystem sys = make_system<double>(G, op, opp, L.sym, L.tmp);
+  if ((e = krylov_enqueue_graph<double>(sys, so, L.bh, L.xh, L.vecs, kw, st, body_st)) != VD_OK) return e;
+  inv_all(G, ncomp, L.xh, x, L.tmp, st);
+  return krylov_graph_finish<double>(sys, L.bh, L.xh, L.vecs, kw, info, st);
+}
+
 }  // namespace vd
 
 extern "C" {

@@ -855,6 +855,205 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
   return VD_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// graph form: the same kernels, with the iteration loop as a conditional WHILE node whose
+// body ends in a kernel that sets the loop condition from the device `done` flag.  Nothing
+// in it synchronises with the host, so it can be captured and replayed as a whole.
+// ---------------------------------------------------------------------------------------
+
+__global__ void k_ks_reset(KState* ks, int maxit, int m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  KHead* h = reinterpret_cast<KHead*>(ks);
+  unsigned* w = reinterpret_cast<unsigned*>(h);
+  for (size_t i = 0; i < sizeof(KHead) / sizeof(unsigned); ++i) w[i] = 0u;
+  h->maxit = maxit;
+  h->status = KS_RUNNING;
+  h->m = m;
+}
+
+__global__ void k_graph_cond(cudaGraphConditionalHandle handle, const KState* ks) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(handle, ks->done ? 0u : 1u);
+}
+
+template <typename T>
+vd_status krylov_enqueue_graph(const SpecSystem& sys, const SolveOpts& o, const void* b, void* x, void* vecs,
+                               const KWork& kw, cudaStream_t st, cudaStream_t body_st) {
+  const long long len = sys.len;
+  const long long nc = sys.G->g.ncplx;
+  const int h0 = sys.h0;
+  const T* sym = (const T*)sys.sym;
+  const int rb = red_blocks(len);
+  const int eb = ew_blocks(len);
+  const Ix ixr = mkix(len, h0, nc, rb, kRedThreads);
+  const Ix ixe = mkix(len, h0, nc, eb, 256);
+  RedArgs ra{kw.ks, kw.partials, kw.counter, kw.hist, o.tol};
+  int* done = &kw.ks->done;
+  int* cdone = &kw.ks->cycle_done;
+  const int m = std::min(std::max(o.restart > 0 ? o.restart : 30, 1), kMaxRestart);
+  cpx<T>* X = (cpx<T>*)x;
+  const cpx<T>* B = (const cpx<T>*)b;
+  cpx<T>* vb = (cpx<T>*)vecs;
+
+  k_ks_reset<<<1, 1, 0, st>>>(kw.ks, o.maxit, m);
+  count_launch();
+  VD_CUDA(cudaMemsetAsync(kw.counter, 0, sizeof(unsigned), st));
+  // the while node: splice it into the capture of st, then capture its body on body_st
+  auto open_loop = [&](cudaGraphConditionalHandle* hnd) -> vd_status {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    VD_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return fail(VD_ERR_INVALID_ARG, "graph solve needs a capturing stream");
+    VD_CUDA(cudaGraphConditionalHandleCreate(hnd, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = *hnd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    VD_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+    VD_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    VD_CUDA(cudaStreamBeginCaptureToGraph(body_st, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed));
+    return VD_OK;
+  };
+  auto close_loop = [&](cudaGraphConditionalHandle hnd) -> vd_status {
+    k_graph_cond<<<1, 1, 0, body_st>>>(hnd, kw.ks);
+    count_launch();
+    cudaGraph_t body = nullptr;
+    VD_CUDA(cudaStreamEndCapture(body_st, &body));
+    return VD_OK;
+  };
+  cudaGraphConditionalHandle hnd;
+  vd_status e;
+  if (o.solver == VD_SOLVER_CG) {
+    cpx<T>* r = vb;
+    cpx<T>* p = vb + len;
+    cpx<T>* q = vb + 2 * len;
+    if (o.x_zero) {
+      VD_CUDA(cudaMemcpyAsync(r, B, sizeof(cpx<T>) * len, cudaMemcpyDeviceToDevice, st));
+    } else {
+      sys.apply(sys, X, q, false, nullptr, st);
+      k_sub<T><<<eb, 256, 0, st>>>(len, B, q, r, nullptr);
+      count_launch();
+    }
+    k_cg_init<T><<<rb, kRedThreads, 0, st>>>(ixr, B, r, p, sym, ra);
+    count_launch();
+    if ((e = open_loop(&hnd)) != VD_OK) return e;
+    sys.apply(sys, p, q, false, done, body_st);
+    k_dot<T, 1><<<rb, kRedThreads, 0, body_st>>>(ixr, p, q, EPI_CG_ALPHA, ra, done);
+    k_cg_update<T><<<rb, kRedThreads, 0, body_st>>>(ixr, X, p, r, q, sym, ra);
+    k_cg_p<T><<<eb, 256, 0, body_st>>>(ixe, p, r, sym, kw.ks);
+    count_launch();
+    count_launch();
+    count_launch();
+    if ((e = close_loop(hnd)) != VD_OK) return e;
+  } else if (o.solver == VD_SOLVER_RMR) {
+    cpx<T>* r = vb;
+    cpx<T>* w = vb + len;
+    if (o.x_zero) {
+      VD_CUDA(cudaMemcpyAsync(r, B, sizeof(cpx<T>) * len, cudaMemcpyDeviceToDevice, st));
+    } else {
+      sys.apply(sys, X, w, false, nullptr, st);
+      k_sub<T><<<eb, 256, 0, st>>>(len, B, w, r, nullptr);
+      count_launch();
+    }
+    k_norms<T, 2><<<rb, kRedThreads, 0, st>>>(ixr, B, r, EPI_INIT_RMR, ra, nullptr);
+    count_launch();
+    if ((e = open_loop(&hnd)) != VD_OK) return e;
+    sys.apply(sys, r, w, true, done, body_st);
+    k_dot<T, 2><<<rb, kRedThreads, 0, body_st>>>(ixr, r, w, EPI_RMR_ALPHA, ra, done);
+    k_rmr_update<T><<<rb, kRedThreads, 0, body_st>>>(ixr, X, r, w, sym, ra);
+    count_launch();
+    count_launch();
+    if ((e = close_loop(hnd)) != VD_OK) return e;
+  } else {
+    cpx<T>* V = vb;
+    cpx<T>* w = vb + (size_t)(m + 1) * len;
+    k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, nullptr, B, EPI_BB, ra, nullptr);
+    count_launch();
+    if ((e = open_loop(&hnd)) != VD_OK) return e;
+    // one restart cycle: r = b - A x, V_0 = r / beta, m Arnoldi steps, update x
+    sys.apply(sys, X, w, false, done, body_st);
+    k_sub<T><<<eb, 256, 0, body_st>>>(len, B, w, V, done);
+    k_norms<T, 1><<<rb, kRedThreads, 0, body_st>>>(ixr, nullptr, V, EPI_GM_BETA, ra, done);
+    k_gm_scale<T><<<eb, 256, 0, body_st>>>(ixe, V, V, kw.ks, 1);
+    count_launch();
+    count_launch();
+    count_launch();
+    for (int j = 0; j < m; ++j) {
+      cpx<T>* Vj = V + (size_t)j * len;
+      sys.apply(sys, Vj, w, true, cdone, body_st);
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int off = 0; off <= j; off += 8) {
+          const int nv = std::min(8, j + 1 - off);
+          k_gm_mdot<T><<<rb, kRedThreads, 0, body_st>>>(ixr, w, V, off, nv, pass ? EPI_GM_H2 : EPI_GM_H1, j, ra);
+          count_launch();
+        }
+        k_gm_maxpy<T><<<rb, kRedThreads, 0, body_st>>>(ixr, w, V, j, pass, pass, ra);
+        count_launch();
+      }
+      k_gm_scale<T><<<eb, 256, 0, body_st>>>(ixe, V + (size_t)(j + 1) * len, w, kw.ks, 0);
+      count_launch();
+    }
+    k_gm_solve<<<1, 1, 0, body_st>>>(kw.ks);
+    k_gm_update<T><<<eb, 256, 0, body_st>>>(ixe, X, V, sym, kw.ks);
+    k_gm_close<<<1, 1, 0, body_st>>>(kw.ks);
+    count_launch();
+    count_launch();
+    count_launch();
+    if ((e = close_loop(hnd)) != VD_OK) return e;
+  }
+  VD_CUDA(cudaGetLastError());
+  return VD_OK;
+}
+
+// result record of a graph solve: info[0] iterations, [1] status, [2] monitored relres,
+// [3] |b|^2, [4] true relres
+__global__ void k_graph_info(const KState* ks, double* info, int phase) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (phase == 0) {
+    info[0] = (double)ks->iters;
+    const int st = ks->done ? (ks->status < 0 ? VD_ERR_NOT_CONVERGED : ks->status) : VD_ERR_NOT_CONVERGED;
+    info[1] = (double)st;
+    info[2] = ks->relres;
+  } else if (phase == 1) {
+    info[3] = ks->rr;
+  } else {
+    info[4] = info[3] > 0.0 ? sqrt(ks->rr / info[3]) : 0.0;
+  }
+}
+
+template <typename T>
+vd_status krylov_graph_finish(const SpecSystem& sys, const void* b, const void* x, void* vecs, const KWork& kw,
+                              double* info, cudaStream_t st) {
+  const long long len = sys.len;
+  const int rb = red_blocks(len);
+  const int eb = ew_blocks(len);
+  const Ix ixr = mkix(len, sys.h0, sys.G->g.ncplx, rb, kRedThreads);
+  RedArgs ra{kw.ks, kw.partials, kw.counter, kw.hist, 0.0};
+  const cpx<T>* B = (const cpx<T>*)b;
+  cpx<T>* W = (cpx<T>*)vecs;
+  k_graph_info<<<1, 1, 0, st>>>(kw.ks, info, 0);
+  k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, nullptr, B, EPI_NORM, ra, nullptr);
+  k_graph_info<<<1, 1, 0, st>>>(kw.ks, info, 1);
+  sys.apply(sys, x, W, false, nullptr, st);
+  k_sub<T><<<eb, 256, 0, st>>>(len, B, W, W, nullptr);
+  k_norms<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, nullptr, W, EPI_NORM, ra, nullptr);
+  k_graph_info<<<1, 1, 0, st>>>(kw.ks, info, 2);
+  for (int i = 0; i < 6; ++i) count_launch();
+  VD_CUDA(cudaGetLastError());
+  return VD_OK;
+}
+template vd_status krylov_graph_finish<double>(const SpecSystem&, const void*, const void*, void*, const KWork&,
+                                               double*, cudaStream_t);
+
+template vd_status krylov_enqueue_graph<double>(const SpecSystem&, const SolveOpts&, const void*, void*, void*,
+                                                const KWork&, cudaStream_t, cudaStream_t);
+template vd_status krylov_enqueue_graph<float>(const SpecSystem&, const SolveOpts&, const void*, void*, void*,
+                                               const KWork&, cudaStream_t, cudaStream_t);
+
 template vd_status krylov_solve<double>(const SpecSystem&, const SolveOpts&, const void*, void*, void*, const KWork&,
                                         double*, int, SolveOut*, cudaStream_t);
 template vd_status krylov_solve<float>(const SpecSystem&, const SolveOpts&, const void*, void*, void*, const KWork&,

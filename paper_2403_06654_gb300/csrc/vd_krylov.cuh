@@ -86,6 +86,18 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
 template <typename T>
 size_t krylov_vec_bytes(const SpecSystem& sys, int solver, int restart);
 
+// The same solve as a capturable graph fragment: `st` must be capturing; the iteration loop
+// becomes a conditional WHILE node (its body captured on body_st).  No host synchronisation:
+// the result stays in the KState (iters, status, relres, done).
+template <typename T>
+vd_status krylov_enqueue_graph(const SpecSystem& sys, const SolveOpts& o, const void* b, void* x, void* vecs,
+                               const KWork& kw, cudaStream_t st, cudaStream_t body_st);
+// After a graph solve: true residual of x and the result record info[0..4] (iterations,
+// status, monitored relres, |b|^2, true relres), all on the device.  vecs: scratch.
+template <typename T>
+vd_status krylov_graph_finish(const SpecSystem& sys, const void* b, const void* x, void* vecs, const KWork& kw,
+                              double* info, cudaStream_t st);
+
 // helpers shared with the API layer
 template <typename T>
 void spec_copy_scale(long long len, const void* x, double s, void* y, cudaStream_t st);   // y = s x

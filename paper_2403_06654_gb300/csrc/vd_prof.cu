@@ -11,6 +11,8 @@ namespace vd {
 static std::atomic<long long> g_launches{0};
 static std::atomic<int> g_prof_on{0};
 
+bool vd_profile_is_on() { return g_prof_on.load(std::memory_order_relaxed) != 0; }
+
 struct Pending {
   int cls;
   cudaEvent_t a, b;

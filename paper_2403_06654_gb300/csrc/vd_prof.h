@@ -24,6 +24,7 @@ enum ProfClass : int {
 };
 
 void count_launch();
+bool vd_profile_is_on();   // event timing enabled (events cannot be recorded into a graph)
 
 // RAII bracket of one launch; records events only when profiling is on
 struct ProfScope {

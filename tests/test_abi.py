@@ -76,3 +76,24 @@ def test_make_request_checks_tensors():
         vd.make_request(0, n, L, good.t(), good, good)
     with pytest.raises(vd.VDError):
         vd.make_request(0, n, L, good.float(), good, good)
+
+
+def test_batch_size_query_host_only():
+    """vd_batch_bytes is a host computation: positive for supported grids, 0 for a length with
+    a prime factor above 5 or an empty batch."""
+    import math
+    shapes = [(64, 48), (24, 20, 16)]
+    arr = (vd.vd_batch_item * 2)()
+    for i, n in enumerate(shapes):
+        nd = len(n)
+        arr[i].ndim = nd
+        arr[i].n = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - nd)))
+        arr[i].L = (ctypes.c_double * 3)(*([2 * math.pi] * 3))
+        arr[i].rho = arr[i].b_vel = arr[i].x_vel = arr[i].b_pres = arr[i].x_pres = 1
+    p = vd.vd_batch_params(vd.VD_SOLVER_GMRES, vd.VD_SOLVER_CG, 1e-10, 400, 20)
+    both = vd.lib().vd_batch_bytes(arr, 2, ctypes.byref(p))
+    one = vd.lib().vd_batch_bytes(arr, 1, ctypes.byref(p))
+    assert both > one > 0
+    arr[1].n = (ctypes.c_int * 3)(24, 20, 28)
+    assert vd.lib().vd_batch_bytes(arr, 2, ctypes.byref(p)) == 0
+    assert vd.lib().vd_batch_bytes(arr, 0, ctypes.byref(p)) == 0
