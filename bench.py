@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the 1D and 2D workload measurements")
     ap.add_argument("--rt-steps", type=int, default=100)
-    ap.add_argument("--mode", default="solve", choices=["solve", "serve"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "serve", "batch"],
                     help="solve: the 256^3 solve-rate line (with a short serving run); serve: the serving line")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving run of the solve line")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched graph run of the solve line")
     ap.add_argument("--serve-count", type=int, default=None, help="requests of the serving trace")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrival rate (req/s)")
     ap.add_argument("--serve-inflight", type=int, default=8, help="server execution slots")
@@ -264,7 +265,10 @@ def extra_krho(dev, G, rho_d, f, x_l, reps=5):
     return {"workload": "same 256^3 jet as the headline; K~ Phi = sqrt(rho) f, phi = sqrt(rho) Phi, tol 1e-10",
             "solvers": out,
             "phi_vs_lrho_rel2": float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)),
-            "note": "K~ and L~ are different discretisations of the same equation; the difference is discretisation error"}
+            "note": ("K~ and L~ are different discretisations of the same equation.  This rhs is the divergence of "
+                     "the 1e-3 white noise on a divergence-free base flow, so it lives at the grid scale, where the "
+                     "two differ at O(1) (the oracle shows 0.4 relative on a noise-dominated 2D case and 1e-6 for a "
+                     "smooth rhs with the same 2-cell interface)")}
 
 
 def extra_rt2d(dev, steps):
@@ -474,6 +478,77 @@ def run_serving(vd, dev, count, rate, max_inflight, sweep=(), baseline_count=200
     return out
 
 
+BATCH_WORKLOAD = ("96 uneven instances (seed 4): 2D 64..512^2 / 3D 32..160^3, slab density ratio 2..50 "
+                  "log-uniform, interface 3 cells; per instance the coupled velocity system (a = 1e-3, Sc = 1, "
+                  "GMRES(30)) and the pressure system (CG), tol 1e-10, x0 = 0; band-limited rhs")
+
+
+def run_batch(vd, dev, count=96, tol=1e-10, reps=2, precision="mixed_dd"):
+    """All solves of the batch in one graph launch vs the same solves one at a time through vd_solve."""
+    import numpy as np
+    import torch
+    from paper_2403_06654_gb300 import inputs
+    insts = inputs.batch_instances(count=count)
+    items = []
+    for i, inst in enumerate(insts):
+        nd = len(inst.n)
+        rho = torch.from_numpy(inst.density()).to(dev)
+        bp = torch.from_numpy(inputs.smooth_random_field(inst.n, inst.L, 300 + i, kmax=5)).to(dev)
+        bv = torch.from_numpy(np.stack([inputs.smooth_random_field(inst.n, inst.L, 400 + 3 * i + c, kmax=5)
+                                        for c in range(nd)])).to(dev)
+        items.append({"n": inst.n, "L": inst.L, "rho": rho, "a": 1e-3, "inv_sc": 1.0, "b_vel": bv,
+                      "x_vel": torch.zeros_like(bv), "b_pres": bp, "x_pres": torch.zeros_like(bp)})
+    t0 = time.perf_counter()
+    B = vd.Batch(items, vel_solver="gmres", pres_solver="cg", tol=tol, max_it=500, restart=30, precision=precision,
+                 device=dev)
+    t_build = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    B.run()   # warm-up
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    l0 = vd.vd_launch_count()
+    ev[0].record(stream)
+    for _ in range(reps):
+        B.run(stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    host_launches = vd.vd_launch_count() - l0
+    t_graph = ev[0].elapsed_time(ev[1]) / 1e3 / reps
+    infos = [B.info(i) for i in range(count)]
+    ok = all(v["status"] == "converged" and p["status"] == "converged" for v, p in infos)
+    nodes = B.graph_nodes()
+    B.close()
+    # the same solves one at a time (host-driven loop), with the profiler for algorithmic bytes
+    vd.vd_profile_reset()
+    vd.vd_profile_enable(True)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for it in items:
+        G = vd.Grid(it["n"], it["L"], device=dev)
+        G.set_density(it["rho"], op="velocity")
+        G.solve("velocity", "gmres", it["b_vel"], a=1e-3, inv_sc=1.0, out=it["x_vel"], tol=tol, max_it=500,
+                precision=precision)
+        G.solve("pressure", "cg", it["b_pres"], out=it["x_pres"], tol=tol, max_it=500, precision=precision)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t1
+    vd.vd_profile_enable(False)
+    prof = {c: vd.vd_profile_read(c) for c in vd.PROFILE_CLASSES}
+    alg_bytes = sum(p["alg_bytes"] for p in prof.values())
+    ncomp = sum(len(it["n"]) + 1 for it in items)
+    return {"workload": BATCH_WORKLOAD, "precision": precision, "instances": count, "systems": 2 * count,
+            "component_solves": ncomp,
+            "graph_launches_per_run": 1, "host_kernel_launches_per_run": host_launches // reps,
+            "graph_nodes_top_level": nodes, "build_s": t_build,
+            "graph_s_per_run": t_graph, "systems_per_s": 2 * count / t_graph,
+            "component_solves_per_s": ncomp / t_graph,
+            "one_at_a_time_s": t_seq, "one_at_a_time_systems_per_s": 2 * count / t_seq,
+            "graph_speedup": t_seq / t_graph,
+            "alg_bytes_per_run": alg_bytes, "alg_gbs": alg_bytes / t_graph / 1e9,
+            "vel_iters": [v["iters"] for v, _ in infos], "pres_iters": [p["iters"] for _, p in infos],
+            "max_relres_true": max(max(v["relres_true"], p["relres_true"]) for v, p in infos),
+            "all_converged": ok}
+
+
 SERVE_WORKLOAD = ("Poisson arrivals (seed 5) of pressure solves: 95% batched-instance mix (2D 64..512^2, "
                   "3D 32..160^3, slab density ratio 2..50 log-uniform, interface 3 cells), 5% 256^3; "
                   "tol 1e-6/1e-8/1e-10 uniform; CG, x0 = 0; open-loop submission")
@@ -543,6 +618,15 @@ def main():
     vd.lib()   # fails loudly when the library is missing
     if args.mode == "serve":
         return serve_line(args, vd, dev, rank, world, pg)
+    if args.mode == "batch":
+        res = run_batch(vd, dev, precision="mixed_dd")
+        res64 = run_batch(vd, dev, precision="fp64", reps=1)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "mode": "batch", "value": res["systems_per_s"], "unit": "systems/s",
+                              "n_gpus": world, "higher_is_better": True, "dtype": DTYPES["mixed_dd"],
+                              "data": "synthetic", "config": {"workload": BATCH_WORKLOAD}, "batch": res,
+                              "batch_fp64": res64}), flush=True)
+        return 0
     n = args.n
     L = (2 * math.pi,) * 3
     case = inputs.jet_3d(n=n)
@@ -700,6 +784,10 @@ def main():
         extras = {"tophat1d": extra_tophat1d(dev), "rt2d": extra_rt2d(dev, args.rt_steps),
                   "krho256": extra_krho(dev, G, rho_d, f, x)}
 
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(vd, dev, precision="mixed_dd")
+        batch = {k: v for k, v in batch.items() if k not in ("vel_iters", "pres_iters")}
     serving = None
     if not args.no_serve:
         serving = run_serving(vd, dev, args.serve_count or 2000, args.serve_rate, args.serve_inflight)
@@ -746,6 +834,7 @@ def main():
         "cpu_baseline": cpu,
         "workloads": extras,
         "serving": serving,
+        "batch": batch,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

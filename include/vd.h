@@ -298,7 +298,7 @@ vd_status vd_server_destroy(vd_server* server);
  * non-null) or both.  vd_batch_create attaches every density (synchronising `stream`), lays
  * every grid's density data and solve workspace out in the caller's device buffer `mem`
  * (vd_batch_bytes bytes, caller-owned, alive until vd_batch_destroy) and records every solve
- * (double precision) into one CUDA graph: each system is a branch of its own, and its Krylov
+ * into one CUDA graph: each system is a branch of its own, and its Krylov
  * loop a conditional WHILE node whose body is one iteration (one restart cycle for GMRES) and
  * whose condition a kernel sets from the device-resident convergence flag.  vd_batch_run
  * replays all solves with a single graph launch on `stream`, reading the right-hand sides
@@ -325,6 +325,8 @@ typedef struct {
   int pres_solver;       /* any vd_solver */
   double tol;
   int max_it, restart;
+  int precision;         /* vd_precision: FP64, or the refinement loop recorded into the graph as
+                            a conditional WHILE node around the float inner solve */
 } vd_batch_params;
 size_t vd_batch_bytes(const vd_batch_item* items, int count, const vd_batch_params* params);
 vd_status vd_batch_create(const vd_batch_item* items, int count, const vd_batch_params* params, void* mem,

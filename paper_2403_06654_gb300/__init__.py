@@ -87,7 +87,7 @@ class vd_batch_item(ctypes.Structure):
 
 class vd_batch_params(ctypes.Structure):
     _fields_ = [("vel_solver", ctypes.c_int), ("pres_solver", ctypes.c_int), ("tol", ctypes.c_double),
-                ("max_it", ctypes.c_int), ("restart", ctypes.c_int)]
+                ("max_it", ctypes.c_int), ("restart", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 class vd_solve_info(ctypes.Structure):
@@ -573,7 +573,7 @@ class Batch:
     and b_pres/x_pres (device float64 tensors).  run() is a single graph launch."""
 
     def __init__(self, items, vel_solver="gmres", pres_solver="cg", tol=1e-10, max_it=500, restart=30,
-                 device=None, stream=None):
+                 precision="fp64", device=None, stream=None):
         import torch
         self._keep = []
         arr = (vd_batch_item * len(items))()
@@ -593,7 +593,8 @@ class Batch:
                     self._keep.append(t)
             arr[i].a = float(it.get("a", 0.0))
             arr[i].inv_sc = float(it.get("inv_sc", 1.0))
-        self.params = vd_batch_params(SOLVERS[vel_solver], SOLVERS[pres_solver], tol, max_it, restart)
+        self.params = vd_batch_params(SOLVERS[vel_solver], SOLVERS[pres_solver], tol, max_it, restart,
+                                      PRECISIONS[precision])
         self.items = arr
         self.count = len(items)
         nb = int(lib().vd_batch_bytes(arr, len(items), ctypes.byref(self.params)))
@@ -611,7 +612,7 @@ class Batch:
         v, p = vd_solve_info(), vd_solve_info()
         _check(lib().vd_batch_info(self.h, i, ctypes.byref(v), ctypes.byref(p)))
         conv = lambda x: {"status": STATUS_NAMES.get(x.status, x.status), "iters": x.iters,  # noqa: E731
-                          "relres": x.relres, "relres_true": x.relres_true}
+                          "outer_iters": x.outer_iters, "relres": x.relres, "relres_true": x.relres_true}
         return conv(v), conv(p)
 
     def graph_nodes(self):

@@ -466,6 +466,7 @@ namespace vd {
 
 struct SolveLayout {
   KState* ks;
+  OState* ost;           // refinement state of graph solves
   double* partials;
   unsigned* counter;
   double* hist;
@@ -502,6 +503,7 @@ static SolveLayout solve_layout(const vd_grid* G, vd_op op, int solver, int rest
   L.partials = c.take<double>(sizeof(double) * kRedBlocks * 8);
   L.counter = c.take<unsigned>(sizeof(unsigned) * 4);
   L.hist = c.take<double>(sizeof(double) * (size_t)(std::max(maxit, 1) + 2));
+  L.ost = c.take<OState>(sizeof(OState));
   L.sym = c.take<double>(nc * 8);
   L.sym_f = nullptr;
   L.bh = c.take<cpx<double>>(len * 16);
@@ -599,26 +601,67 @@ static void inv_all(const vd_grid* G, int ncomp, const cpx<double>* in, double* 
 // One FP64 solve as a capturable graph fragment on st (loop bodies captured on body_st):
 // transforms, range projection, the Krylov loop as a conditional node, inverse transform,
 // true residual and the result record info[0..4] (see krylov_graph_finish).
+struct ResidCtx {
+  const vd_grid* G;
+  vd_op op;
+  bool dd;
+  const SpecSystem* sys64;
+  void* tmp;
+};
+static void resid_cb(const void* c, const void* x, void* y, cudaStream_t st) {
+  const ResidCtx& r = *static_cast<const ResidCtx*>(c);
+  const cpx<double>* xi = (const cpx<double>*)x;
+  cpx<double>* yo = (cpx<double>*)y;
+  if (r.dd && r.op == VD_OP_KRHO) apply_krho_spec_dd(r.G, xi, yo, r.tmp, nullptr, st);
+  else if (r.dd) apply_pressure_spec_dd(r.G, xi, yo, r.tmp, nullptr, st);
+  else r.sys64->apply(*r.sys64, xi, yo, false, nullptr, st);
+}
+
 vd_status enqueue_solve_graph(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_params* opp, double tol,
-                              int maxit, int restart, const double* b, double* x, void* ws, size_t ws_bytes,
-                              double* info, cudaStream_t st, cudaStream_t body_st) {
+                              int maxit, int restart, int precision, const double* b, double* x, void* ws,
+                              size_t ws_bytes, double* info, cudaStream_t st, cudaStream_t const* body) {
+  cudaStream_t body_st = body[0];
   vd_status e = check_op(G, op, opp);
   if (e != VD_OK) return e;
   if (op == VD_OP_KRHO) return fail(VD_ERR_INVALID_ARG, "graph solves cover the pressure and velocity operators");
   if (solver == VD_SOLVER_CG && op == VD_OP_VELOCITY)
     return fail(VD_ERR_INVALID_ARG, "CG needs a symmetric operator; V_rho is not symmetric");
   if (solver == VD_SOLVER_GMRES && restart > kMaxRestart) return fail(VD_ERR_INVALID_ARG, "GMRES restart must be <= 64");
+  if (precision != VD_PREC_FP64 && precision != VD_PREC_MIXED && precision != VD_PREC_MIXED_DD)
+    return fail(VD_ERR_INVALID_ARG, "unknown precision mode");
   size_t need = 0;
-  SolveLayout L = solve_layout(G, op, solver, restart, maxit, VD_PREC_FP64, ws, &need);
+  SolveLayout L = solve_layout(G, op, solver, restart, maxit, precision, ws, &need);
   if (ws_bytes < need) return fail(VD_ERR_OOM, "workspace too small");
   const int ncomp = op_ncomp(G, op);
   const long long len = G->g.ncplx * ncomp;
   VD_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned), st));
   fill_symbol<double>(G, op_symbol(op), opp ? opp->a : 0.0, L.sym, st);
-  fwd_all(G, ncomp, b, L.bh, st);
+  const bool dd = precision == VD_PREC_MIXED_DD && op != VD_OP_VELOCITY;
+  if (dd) fwd_transform_dd(G, b, L.bh, L.tmp, st);
+  else fwd_all(G, ncomp, b, L.bh, st);
   if (op == VD_OP_PRESSURE) spec_project<double>(G, 1, L.bh, st);
   VD_CUDA(cudaMemsetAsync(L.xh, 0, sizeof(cpx<double>) * len, st));
   KWork kw{L.ks, L.partials, L.counter, L.hist};
+  if (precision != VD_PREC_FP64) {
+    fill_symbol<float>(G, op_symbol(op), opp ? opp->a : 0.0, L.sym_f, st);
+    SpecSystem sys64 = make_system<double>(G, op, opp, L.sym, L.tmp);
+    SpecSystem sys32 = make_system<float>(G, op, opp, L.sym_f, L.tmp_f);
+    ResidCtx rc{G, op, dd, &sys64, L.tmp};
+    SolveOpts si;
+    si.solver = solver;
+    si.tol = 0.0;
+    si.maxit = maxit;
+    si.restart = restart;
+    si.check_every = 1;
+    si.x_zero = 1;
+    e = refine_enqueue_graph(sys64, sys32, &resid_cb, &rc, si, tol, 1e-5, maxit, L.bh, L.xh, L.rh, L.bh_f, L.xh_f,
+                             L.vecs, kw, L.ost, info, st, body[0], body[1], body[2]);
+    if (e != VD_OK) return e;
+    if (dd) inv_transform_dd(G, L.xh, x, L.tmp, st);
+    else inv_all(G, ncomp, L.xh, x, L.tmp, st);
+    VD_CUDA(cudaGetLastError());
+    return VD_OK;
+  }
   SolveOpts so;
   so.solver = solver;
   so.tol = tol;

@@ -34,7 +34,7 @@ vd_solve_params solve_params(const vd_batch_params& p) {
   s.tol = p.tol;
   s.max_it = p.max_it;
   s.restart = p.restart > 0 ? p.restart : 30;
-  s.precision = VD_PREC_FP64;
+  s.precision = p.precision;
   return s;
 }
 
@@ -84,6 +84,8 @@ vd_status vd_batch_create(const vd_batch_item* items, int count, const vd_batch_
   if (params->vel_solver < 0 || params->vel_solver > 2 || params->pres_solver < 0 || params->pres_solver > 2)
     return fail(VD_ERR_INVALID_ARG, "unknown solver");
   if (!(params->tol >= 0.0) || params->max_it < 0) return fail(VD_ERR_INVALID_ARG, "tol >= 0 and max_it >= 0");
+  if (params->precision != VD_PREC_FP64 && params->precision != VD_PREC_MIXED && params->precision != VD_PREC_MIXED_DD)
+    return fail(VD_ERR_INVALID_ARG, "unknown precision mode");
   if (vd_profile_is_on()) return fail(VD_ERR_INVALID_ARG, "disable the profiler while recording a batch");
   const size_t need = vd_batch_bytes(items, count, params);
   if (need == 0) return fail(VD_ERR_INVALID_ARG, "unsupported grid in the batch");
@@ -129,12 +131,12 @@ vd_status vd_batch_create(const vd_batch_item* items, int count, const vd_batch_
   VD_CUDA(cudaStreamSynchronize(st));
 
   // record: fork one branch per item from the capturing stream, join them at the end
-  cudaStream_t body = nullptr;
+  cudaStream_t body[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> joins(2 * count, nullptr);
   std::vector<cudaStream_t> branches(2 * count, nullptr);   // one capture stream per system
   for (auto& s : branches) VD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-  VD_CUDA(cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking));
+  for (auto& b : body) VD_CUDA(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
   VD_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
   for (auto& j : joins) VD_CUDA(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
   vd_status err = VD_OK;
@@ -158,11 +160,12 @@ vd_status vd_batch_create(const vd_batch_item* items, int count, const vd_batch_
     if (vel) {
       vd_op_params op{it.in.a, it.in.inv_sc};
       err = enqueue_solve_graph(it.G, VD_OP_VELOCITY, (vd_solver)params->vel_solver, &op, params->tol, sp.max_it,
-                                sp.restart, it.in.b_vel, it.in.x_vel, it.ws_vel, it.ws_vel_bytes, rec, branch, body);
+                                sp.restart, sp.precision, it.in.b_vel, it.in.x_vel, it.ws_vel, it.ws_vel_bytes, rec,
+                                branch, body);
     } else {
       err = enqueue_solve_graph(it.G, VD_OP_PRESSURE, (vd_solver)params->pres_solver, nullptr, params->tol, sp.max_it,
-                                sp.restart, it.in.b_pres, it.in.x_pres, it.ws_pres, it.ws_pres_bytes, rec + kInfo,
-                                branch, body);
+                                sp.restart, sp.precision, it.in.b_pres, it.in.x_pres, it.ws_pres, it.ws_pres_bytes,
+                                rec + kInfo, branch, body);
     }
     if (err == VD_OK && cudaEventRecord(joins[k], branch) != cudaSuccess) err = fail(VD_ERR_CUDA, "join record");
     if (err == VD_OK && cudaStreamWaitEvent(cap, joins[k], 0) != cudaSuccess) err = fail(VD_ERR_CUDA, "join wait");
@@ -182,7 +185,7 @@ vd_status vd_batch_create(const vd_batch_item* items, int count, const vd_batch_
   }
   cudaStreamDestroy(cap);
   for (auto& s : branches) cudaStreamDestroy(s);
-  cudaStreamDestroy(body);
+  for (auto& b : body) cudaStreamDestroy(b);
   cudaEventDestroy(fork);
   for (auto& j : joins) cudaEventDestroy(j);
   if (err != VD_OK) return cleanup(err);
@@ -207,6 +210,7 @@ vd_status vd_batch_info(vd_batch* B, int index, vd_solve_info* vel, vd_solve_inf
     o->status = (int)r[1];
     o->relres = r[2];
     o->relres_true = r[4];
+    o->outer_iters = (int)r[5];
     o->hist_len = 0;
   };
   if (B->items[index].in.b_vel) fill(rec, vel);

@@ -123,9 +123,10 @@ int krho_tmp_fields(int ndim);
 template <typename T>
 void fill_symbol(const vd_grid* G, int kind, double a, T* out, cudaStream_t st);
 
-// one FP64 solve recorded into the capture of st (see vd_api.cu)
+// one solve recorded into the capture of st (see vd_api.cu); body: 3 streams for the
+// conditional bodies (one is enough in FP64)
 vd_status enqueue_solve_graph(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_params* opp, double tol,
-                              int maxit, int restart, const double* b, double* x, void* ws, size_t ws_bytes,
-                              double* info, cudaStream_t st, cudaStream_t body_st);
+                              int maxit, int restart, int precision, const double* b, double* x, void* ws,
+                              size_t ws_bytes, double* info, cudaStream_t st, cudaStream_t const* body);
 
 }  // namespace vd

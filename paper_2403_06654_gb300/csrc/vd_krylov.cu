@@ -126,6 +126,7 @@ enum Epi : int {
 
 template <int NV>
 __device__ void epilogue(int epi, const double (&t)[NV], KState* ks, double* hist, double tol, int off, int j) {
+  if (tol < 0.0) tol = ks->dtol;
   switch (epi) {
     case EPI_INIT_CG:
     case EPI_INIT_RMR: {
@@ -861,14 +862,29 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
 // in it synchronises with the host, so it can be captured and replayed as a whole.
 // ---------------------------------------------------------------------------------------
 
-__global__ void k_ks_reset(KState* ks, int maxit, int m) {
+__global__ void k_ks_reset(KState* ks, int maxit, int m, cudaGraphConditionalHandle loop) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // a loop nested in another conditional body keeps its last condition value: arm it here
+  cudaGraphSetConditional(loop, 1u);
   KHead* h = reinterpret_cast<KHead*>(ks);
   unsigned* w = reinterpret_cast<unsigned*>(h);
   for (size_t i = 0; i < sizeof(KHead) / sizeof(unsigned); ++i) w[i] = 0u;
   h->maxit = maxit;
   h->status = KS_RUNNING;
   h->m = m;
+}
+
+// inner solve of a refinement sweep: budget and tolerance from the refinement state
+__global__ void k_ks_reset_dev(KState* ks, const OState* o, int m, cudaGraphConditionalHandle loop) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  cudaGraphSetConditional(loop, 1u);
+  KHead* h = reinterpret_cast<KHead*>(ks);
+  unsigned* w = reinterpret_cast<unsigned*>(h);
+  for (size_t i = 0; i < sizeof(KHead) / sizeof(unsigned); ++i) w[i] = 0u;
+  h->maxit = o->maxit - o->total;
+  h->status = KS_RUNNING;
+  h->m = m;
+  ks->dtol = o->itol;
 }
 
 __global__ void k_graph_cond(cudaGraphConditionalHandle handle, const KState* ks) {
@@ -886,7 +902,7 @@ vd_status krylov_enqueue_graph(const SpecSystem& sys, const SolveOpts& o, const 
   const int eb = ew_blocks(len);
   const Ix ixr = mkix(len, h0, nc, rb, kRedThreads);
   const Ix ixe = mkix(len, h0, nc, eb, 256);
-  RedArgs ra{kw.ks, kw.partials, kw.counter, kw.hist, o.tol};
+  RedArgs ra{kw.ks, kw.partials, kw.counter, kw.hist, o.dev_outer ? -1.0 : o.tol};
   int* done = &kw.ks->done;
   int* cdone = &kw.ks->cycle_done;
   const int m = std::min(std::max(o.restart > 0 ? o.restart : 30, 1), kMaxRestart);
@@ -894,21 +910,30 @@ vd_status krylov_enqueue_graph(const SpecSystem& sys, const SolveOpts& o, const 
   const cpx<T>* B = (const cpx<T>*)b;
   cpx<T>* vb = (cpx<T>*)vecs;
 
-  k_ks_reset<<<1, 1, 0, st>>>(kw.ks, o.maxit, m);
+  // the loop's condition handle belongs to the graph being captured on st
+  cudaGraphConditionalHandle hnd;
+  {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    VD_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) return fail(VD_ERR_INVALID_ARG, "graph solve needs a capturing stream");
+    VD_CUDA(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
+  }
+  if (o.dev_outer) k_ks_reset_dev<<<1, 1, 0, st>>>(kw.ks, o.dev_outer, m, hnd);
+  else k_ks_reset<<<1, 1, 0, st>>>(kw.ks, o.maxit, m, hnd);
   count_launch();
   VD_CUDA(cudaMemsetAsync(kw.counter, 0, sizeof(unsigned), st));
   // the while node: splice it into the capture of st, then capture its body on body_st
-  auto open_loop = [&](cudaGraphConditionalHandle* hnd) -> vd_status {
+  auto open_loop = [&](cudaGraphConditionalHandle* h) -> vd_status {
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
     const cudaGraphNode_t* deps = nullptr;
     size_t nd = 0;
     VD_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
     if (cs != cudaStreamCaptureStatusActive) return fail(VD_ERR_INVALID_ARG, "graph solve needs a capturing stream");
-    VD_CUDA(cudaGraphConditionalHandleCreate(hnd, g, 1, cudaGraphCondAssignDefault));
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = *hnd;
+    cp.conditional.handle = *h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     cudaGraphNode_t node;
@@ -925,7 +950,6 @@ vd_status krylov_enqueue_graph(const SpecSystem& sys, const SolveOpts& o, const 
     VD_CUDA(cudaStreamEndCapture(body_st, &body));
     return VD_OK;
   };
-  cudaGraphConditionalHandle hnd;
   vd_status e;
   if (o.solver == VD_SOLVER_CG) {
     cpx<T>* r = vb;
@@ -1048,6 +1072,199 @@ vd_status krylov_graph_finish(const SpecSystem& sys, const void* b, const void* 
 }
 template vd_status krylov_graph_finish<double>(const SpecSystem&, const void*, const void*, void*, const KWork&,
                                                double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------
+// iterative refinement as a graph fragment
+// ---------------------------------------------------------------------------------------
+
+__global__ void k_out_init(OState* o, const KState* ks, double tol, double itol0, int maxit,
+                           cudaGraphConditionalHandle loop) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  cudaGraphSetConditional(loop, 1u);
+  o->bb = ks->rr;   // |b|^2, and the first residual is b
+  o->rr = ks->rr;
+  o->rnorm = o->rel = o->scale = 0.0;
+  o->tol = tol;
+  o->itol0 = itol0;
+  o->itol = itol0;
+  o->total = o->outer = 0;
+  o->maxit = maxit;
+  o->maxouter = 20;
+  o->done = 0;
+  o->status = VD_ERR_NOT_CONVERGED;
+  o->force = 0;
+}
+
+// top of a refinement sweep: the same decisions as the host loop of vd_solve
+__global__ void k_out_check(OState* o, cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_sweep) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double rnorm = sqrt(o->rr);
+  const double bnorm = sqrt(o->bb);
+  const double rel = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+  o->rnorm = rnorm;
+  o->rel = rel;
+  if (o->force) {
+    o->done = 1;
+    o->status = o->force;
+  } else if (!isfinite(rel)) {
+    o->done = 1;
+    o->status = VD_ERR_NONFINITE;
+  } else if (rel <= o->tol) {
+    o->done = 1;
+    o->status = VD_OK;
+  } else if (o->total >= o->maxit || o->outer >= o->maxouter) {
+    o->done = 1;
+    o->status = VD_ERR_NOT_CONVERGED;
+  } else {
+    o->scale = 1.0 / rnorm;
+    o->itol = fmax(o->itol0, 0.5 * o->tol / rel);
+  }
+  cudaGraphSetConditional(h_loop, o->done ? 0u : 1u);
+  cudaGraphSetConditional(h_sweep, o->done ? 0u : 1u);
+}
+
+__global__ void k_out_after_inner(OState* o, const KState* ks) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  o->total += ks->iters;
+  o->outer += 1;
+  const int st = ks->done ? ks->status : VD_ERR_NOT_CONVERGED;
+  if (st == VD_ERR_NONFINITE) o->force = VD_ERR_NONFINITE;
+  else if (ks->iters == 0 && st != VD_OK) o->force = VD_ERR_NOT_CONVERGED;
+}
+
+__global__ void k_out_rr(OState* o, const KState* ks) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) o->rr = ks->rr;
+}
+
+__global__ void k_out_info(const OState* o, double* info) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  info[0] = (double)o->total;
+  info[1] = (double)(o->done ? o->status : VD_ERR_NOT_CONVERGED);
+  info[2] = o->rel;
+  info[3] = o->bb;
+  info[4] = o->rel;   // the refinement residual is the accurately computed true residual
+  info[5] = (double)o->outer;
+}
+
+// v *= 1/|r| and x += |r| d with the scalars read from the refinement state
+__global__ void k_scale_out(long long n, const OState* o, cpx<double>* v) {
+  const double s = o->scale;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    v[e] = scal(v[e], s);
+}
+__global__ void k_axpy_out(long long n, const OState* o, const cpx<double>* x, cpx<double>* y) {
+  const double a = o->rnorm;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] = y[e] + scal(x[e], a);
+}
+
+static vd_status open_cond(cudaStream_t st, cudaGraphConditionalNodeType type, cudaGraphConditionalHandle hnd,
+                           cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  VD_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return fail(VD_ERR_INVALID_ARG, "graph solve needs a capturing stream");
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hnd;
+  cp.conditional.type = type;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  VD_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+  VD_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  *body = cp.conditional.phGraph_out[0];
+  return VD_OK;
+}
+
+vd_status refine_enqueue_graph(const SpecSystem& sys64, const SpecSystem& sys32,
+                               void (*resid)(const void* ctx, const void* x, void* y, cudaStream_t st),
+                               const void* resid_ctx, const SolveOpts& inner, double tol, double itol0, int maxit,
+                               void* bh, void* xh, void* rh, void* bh_f, void* xh_f, void* vecs, const KWork& kw,
+                               OState* ost, double* info, cudaStream_t st, cudaStream_t s1, cudaStream_t s2,
+                               cudaStream_t s3) {
+  const long long len = sys64.len;
+  const int rb = red_blocks(len);
+  const int eb = ew_blocks(len);
+  const Ix ixr = mkix(len, sys64.h0, sys64.G->g.ncplx, rb, kRedThreads);
+  RedArgs ra{kw.ks, kw.partials, kw.counter, kw.hist, 0.0};
+  cpx<double>* BH = (cpx<double>*)bh;
+  cpx<double>* XH = (cpx<double>*)xh;
+  cpx<double>* RH = (cpx<double>*)rh;
+  // |b|^2, x = 0, r = b
+  cudaGraphConditionalHandle h_loop, h_sweep;
+  {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g0 = nullptr;
+    VD_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g0, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) return fail(VD_ERR_INVALID_ARG, "graph solve needs a capturing stream");
+    VD_CUDA(cudaGraphConditionalHandleCreate(&h_loop, g0, 1, cudaGraphCondAssignDefault));
+  }
+  VD_CUDA(cudaMemsetAsync(kw.counter, 0, sizeof(unsigned), st));
+  k_norms<double, 1><<<rb, kRedThreads, 0, st>>>(ixr, nullptr, BH, EPI_NORM, ra, nullptr);
+  k_out_init<<<1, 1, 0, st>>>(ost, kw.ks, tol, itol0, maxit, h_loop);
+  VD_CUDA(cudaMemsetAsync(XH, 0, sizeof(cpx<double>) * len, st));
+  VD_CUDA(cudaMemcpyAsync(RH, BH, sizeof(cpx<double>) * len, cudaMemcpyDeviceToDevice, st));
+  count_launch();
+  count_launch();
+  // while (not done) { check; if (sweep) { ... } }
+  cudaGraph_t loop_body = nullptr, sweep_body = nullptr;
+  vd_status e;
+  if ((e = open_cond(st, cudaGraphCondTypeWhile, h_loop, &loop_body)) != VD_OK) return e;
+  VD_CUDA(cudaStreamBeginCaptureToGraph(s1, loop_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g1 = nullptr;
+    VD_CUDA(cudaStreamGetCaptureInfo(s1, &cs, nullptr, &g1, nullptr, nullptr, nullptr));
+    VD_CUDA(cudaGraphConditionalHandleCreate(&h_sweep, g1, 0, cudaGraphCondAssignDefault));
+  }
+  k_out_check<<<1, 1, 0, s1>>>(ost, h_loop, h_sweep);
+  count_launch();
+  {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g1 = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    VD_CUDA(cudaStreamGetCaptureInfo(s1, &cs, nullptr, &g1, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h_sweep;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    VD_CUDA(cudaGraphAddNode(&node, g1, deps, nullptr, nd, &cp));
+    VD_CUDA(cudaStreamUpdateCaptureDependencies(s1, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    sweep_body = cp.conditional.phGraph_out[0];
+  }
+  VD_CUDA(cudaStreamBeginCaptureToGraph(s2, sweep_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  // the sweep: d solves A32 d = r/|r| in float, x += |r| d, r = b - A x, |r|^2
+  k_scale_out<<<eb, 256, 0, s2>>>(len, ost, RH);
+  count_launch();
+  spec_d2f(len, RH, bh_f, s2);
+  VD_CUDA(cudaMemsetAsync(xh_f, 0, sizeof(cpx<float>) * len, s2));
+  SolveOpts si = inner;
+  si.x_zero = 1;
+  si.dev_outer = ost;
+  if ((e = krylov_enqueue_graph<float>(sys32, si, bh_f, xh_f, vecs, kw, s2, s3)) != VD_OK) return e;
+  k_out_after_inner<<<1, 1, 0, s2>>>(ost, kw.ks);
+  spec_f2d(len, xh_f, RH, s2);
+  k_axpy_out<<<eb, 256, 0, s2>>>(len, ost, RH, XH);
+  resid(resid_ctx, XH, RH, s2);
+  k_sub<double><<<eb, 256, 0, s2>>>(len, BH, RH, RH, nullptr);
+  VD_CUDA(cudaMemsetAsync(kw.counter, 0, sizeof(unsigned), s2));
+  k_norms<double, 1><<<rb, kRedThreads, 0, s2>>>(ixr, nullptr, RH, EPI_NORM, ra, nullptr);
+  k_out_rr<<<1, 1, 0, s2>>>(ost, kw.ks);
+  for (int i = 0; i < 5; ++i) count_launch();
+  cudaGraph_t tmp = nullptr;
+  VD_CUDA(cudaStreamEndCapture(s2, &tmp));
+  VD_CUDA(cudaStreamEndCapture(s1, &tmp));
+  k_out_info<<<1, 1, 0, st>>>(ost, info);
+  count_launch();
+  (void)sys64;
+  VD_CUDA(cudaGetLastError());
+  return VD_OK;
+}
 
 template vd_status krylov_enqueue_graph<double>(const SpecSystem&, const SolveOpts&, const void*, void*, void*,
                                                 const KWork&, cudaStream_t, cudaStream_t);

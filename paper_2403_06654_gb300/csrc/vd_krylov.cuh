@@ -31,6 +31,13 @@ struct KState {
   double H[(kMaxRestart + 1) * kMaxRestart];   // column-major: H[i + j*(m+1)]
   double cs[kMaxRestart], sn[kMaxRestart], gv[kMaxRestart + 1], y[kMaxRestart];
   double h1[kMaxRestart + 1], h2[kMaxRestart + 1];
+  double dtol;     // tolerance read by the epilogues when the launch passes a negative one
+};
+
+// device-resident state of an iterative-refinement loop recorded into a graph
+struct OState {
+  double bb, rr, rnorm, rel, tol, itol0, itol, scale;
+  int total, outer, maxit, maxouter, done, status, force, pad;
 };
 
 struct KWork {
@@ -69,6 +76,7 @@ struct SolveOpts {
   int restart;
   int check_every;
   int x_zero;   // x is known to be zero on entry: the first residual is b (no operator apply)
+  const OState* dev_outer = nullptr;   // graph form: tolerance and iteration budget from the device
 };
 
 struct SolveOut {
@@ -92,6 +100,17 @@ size_t krylov_vec_bytes(const SpecSystem& sys, int solver, int restart);
 template <typename T>
 vd_status krylov_enqueue_graph(const SpecSystem& sys, const SolveOpts& o, const void* b, void* x, void* vecs,
                                const KWork& kw, cudaStream_t st, cudaStream_t body_st);
+// Iterative refinement as a graph fragment (see vd_krylov.cu): x += |r| d with the inner
+// float solve A32 d = r/|r| and r = b - A x from `resid` (double or float-pair operator).
+// bh, xh, rh: double spectral vectors (bh holds the projected rhs; xh is zeroed here);
+// bh_f, xh_f, vecs: float inner vectors.  Streams: st capturing, s1..s3 for the bodies.
+vd_status refine_enqueue_graph(const SpecSystem& sys64, const SpecSystem& sys32,
+                               void (*resid)(const void* ctx, const void* x, void* y, cudaStream_t st),
+                               const void* resid_ctx, const SolveOpts& inner, double tol, double itol0, int maxit,
+                               void* bh, void* xh, void* rh, void* bh_f, void* xh_f, void* vecs, const KWork& kw,
+                               OState* ost, double* info, cudaStream_t st, cudaStream_t s1, cudaStream_t s2,
+                               cudaStream_t s3);
+
 // After a graph solve: true residual of x and the result record info[0..4] (iterations,
 // status, monitored relres, |b|^2, true relres), all on the device.  vecs: scratch.
 template <typename T>

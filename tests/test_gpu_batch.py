@@ -41,10 +41,13 @@ def make_items(seed=0):
     return items, meta
 
 
-@pytest.mark.parametrize("vel_solver,pres_solver", [("gmres", "cg"), ("rmr", "gmres")])
-def test_batch_matches_single_solves(vel_solver, pres_solver):
+@pytest.mark.parametrize("vel_solver,pres_solver,precision", [("gmres", "cg", "fp64"), ("rmr", "gmres", "fp64"),
+                                                              ("gmres", "cg", "mixed_dd"), ("gmres", "rmr", "mixed")])
+def test_batch_matches_single_solves(vel_solver, pres_solver, precision):
+    """The graph replays the host loop's decisions (refinement sweeps included) on the device."""
     items, meta = make_items()
-    B = vd.Batch(items, vel_solver=vel_solver, pres_solver=pres_solver, tol=1e-10, max_it=400, restart=20)
+    B = vd.Batch(items, vel_solver=vel_solver, pres_solver=pres_solver, tol=1e-10, max_it=400, restart=20,
+                 precision=precision)
     try:
         l0 = vd.vd_launch_count()
         B.run()
@@ -55,11 +58,13 @@ def test_batch_matches_single_solves(vel_solver, pres_solver):
             G = vd.Grid(n, L)
             G.set_density(items[i]["rho"], op="velocity")
             xv, sv_ = G.solve("velocity", vel_solver, items[i]["b_vel"], a=1e-3, inv_sc=1.0, tol=1e-10, max_it=400,
-                              restart=20)
-            xp, sp_ = G.solve("pressure", pres_solver, items[i]["b_pres"], tol=1e-10, max_it=400, restart=20)
+                              restart=20, precision=precision)
+            xp, sp_ = G.solve("pressure", pres_solver, items[i]["b_pres"], tol=1e-10, max_it=400, restart=20,
+                              precision=precision)
             assert iv["status"] == sv_["status"] == "converged", (i, iv, sv_)
             assert ip["status"] == sp_["status"] == "converged", (i, ip, sp_)
-            assert iv["iters"] == sv_["iters"] and ip["iters"] == sp_["iters"]
+            assert iv["iters"] == sv_["iters"] and ip["iters"] == sp_["iters"], (i, iv, sv_, ip, sp_)
+            assert iv["outer_iters"] == sv_["outer_iters"] and ip["outer_iters"] == sp_["outer_iters"]
             assert iv["relres_true"] <= 1e-10 * 1.01 and ip["relres_true"] <= 1e-10 * 1.01
             for got, ref in ((items[i]["x_vel"], xv), (items[i]["x_pres"], xp)):
                 err = float((got - ref).abs().max() / ref.abs().max())

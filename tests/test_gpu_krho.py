@@ -50,6 +50,8 @@ GRIDS = [
     ((32, 24, 16), (2 * math.pi,) * 3),
     ((128, 16, 12), (2 * math.pi, 1.0, 2.0)),
     ((256, 8, 10), (2 * math.pi,) * 3),
+    ((32, 128, 16), (2 * math.pi, 2 * math.pi, 1.0)),    # y pass on the register kernel (float)
+    ((16, 24, 256), (1.0, 2 * math.pi, 2 * math.pi)),    # z pass on the register kernel (float)
 ]
 
 
@@ -114,7 +116,7 @@ def test_solve_fp64(n, L, solver):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "mixed_dd"])
-@pytest.mark.parametrize("n,L", [GRIDS[3], GRIDS[5], GRIDS[7]])
+@pytest.mark.parametrize("n,L", [GRIDS[3], GRIDS[5], GRIDS[7], GRIDS[8], GRIDS[9]])
 def test_solve_mixed(n, L, precision):
     g, G, rho = setup(n, L)
     f = inputs.smooth_random_field(n, L, 9, kmax=5)
