@@ -338,6 +338,29 @@ size_t vd_batch_graph_nodes(const vd_batch* batch);
 vd_status vd_batch_destroy(vd_batch* batch);
 
 /*
+ * Launch-shape autotuner of the transform passes (not in the paper).  For this grid and each
+ * arithmetic type in `precisions` (bit 0 double, bit 1 float, bit 2 float-pair), every pass
+ * the solvers use (y and z passes in both directions; the x pass forward, inverse and fused)
+ * is timed with CUDA events on `scratch` (device, vd_autotune_bytes(grid) bytes, caller-owned,
+ * overwritten) for each candidate shape: the register-resident four-step kernel where one
+ * exists, and the shared-memory Stockham engine with 1, 2, 4, ... lines per block up to the
+ * shared-memory limit.  The fastest shape goes into a process-wide table keyed by (pass, type,
+ * length, axis, direction or x-pass form) that every later launch on any grid consults; with
+ * the environment variable VD_TUNE_FILE set the table is written to that file, and read from
+ * it at the first launch or query of a later process.  Synchronises `stream`.  Shapes change
+ * the work distribution only; results stay within the parity bounds.  The event profiler must
+ * be off while tuning.
+ */
+size_t vd_autotune_bytes(const vd_grid* grid);
+vd_status vd_autotune(const vd_grid* grid, int precisions, void* scratch, size_t bytes, vd_stream stream);
+/* entries of the table, 6 ints each (kind 0 y/z pass or 1 x pass, type 0 double / 1 float /
+ * 2 float-pair, length, axis, direction or x-pass form, choice: 0 register kernel, > 0 lines per
+ * block); writes at most max entries to out (may be null) and returns the total count */
+int vd_autotune_table(int* out, int max);
+/* set one entry by hand (choice < 0 erases it); INVALID_ARG on a bad key or choice */
+vd_status vd_autotune_set(int kind, int type, int n, int axis, int dir, int choice);
+
+/*
  * out = L~_rho(in) for callers that cannot allocate device memory (the paper has no
  * counterpart; this is an integration convenience).  Such callers include code running
  * inside a host framework whose memory pool owns the device, plugins that must keep a

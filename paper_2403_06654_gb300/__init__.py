@@ -117,6 +117,10 @@ _SIGS = {
                       ctypes.POINTER(vd_solve_info), _P, _SZ, _P]),
     "vd_divergence": (_I, [_P, _P, _P, _P, _SZ, _P]),
     "vd_gradient": (_I, [_P, _P, _P, _P, _SZ, _P]),
+    "vd_autotune_bytes": (_SZ, [_P]),
+    "vd_autotune": (_I, [_P, _I, _P, _SZ, _P]),
+    "vd_autotune_table": (_I, [ctypes.POINTER(_I), _I]),
+    "vd_autotune_set": (_I, [_I, _I, _I, _I, _I, _I]),
     "vd_batch_bytes": (_SZ, [ctypes.POINTER(vd_batch_item), _I, ctypes.POINTER(vd_batch_params)]),
     "vd_batch_create": (_I, [ctypes.POINTER(vd_batch_item), _I, ctypes.POINTER(vd_batch_params), _P, _SZ, _P,
                              ctypes.POINTER(_P)]),
@@ -628,3 +632,27 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def vd_autotune(grid, precisions=("fp64", "mixed", "mixed_dd"), stream=None):
+    """Tune the transform launch shapes for this grid (Grid object) and the arithmetic types the
+    precision modes use: fp64 -> double, mixed -> float, mixed_dd -> float + float-pair."""
+    import torch
+    bits = 0
+    for p in precisions:
+        bits |= {"fp64": 1, "mixed": 2, "mixed_dd": 6}[p]
+    nb = int(lib().vd_autotune_bytes(grid.h))
+    scratch = torch.empty(nb, dtype=torch.uint8, device=grid.device)
+    _check(lib().vd_autotune(grid.h, bits, _ptr(scratch), nb, _stream(stream)))
+
+
+def vd_autotune_table():
+    """List of (kind, type, length, axis, dir, choice) entries of the launch-shape table."""
+    n = lib().vd_autotune_table(None, 0)
+    buf = (ctypes.c_int * (6 * max(n, 1)))()
+    n = lib().vd_autotune_table(buf, n)
+    return [tuple(buf[6 * i:6 * i + 6]) for i in range(n)]
+
+
+def vd_autotune_set(kind, type_, n, axis, dir_, choice):
+    _check(lib().vd_autotune_set(kind, type_, n, axis, dir_, choice))

@@ -8,6 +8,14 @@
 #include <type_traits>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+
+namespace vd {
+static void ensure_smem(const void* func, size_t smem);
+}
 
 namespace vd {
 
@@ -603,17 +611,110 @@ static void launch_xpass_r(const XProg& P, const GridDesc& g, const cpx<T>* tw, 
   const long long nlines = (long long)g.n1 * g.n2;
   const long long blocks = (nlines + X::LINES - 1) / X::LINES;
   const size_t smem = sizeof(cpx<T>) * (size_t)(X::M + (X::M + 2) + X::LINES * X::LS);
-  static size_t done = 0;
-  if (smem > 48 * 1024 && smem > done) {
-    cudaFuncSetAttribute(k_xpass_r<T, M1, M2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    done = smem;
-  }
+  ensure_smem(reinterpret_cast<const void*>(k_xpass_r<T, M1, M2>), smem);
   k_xpass_r<T, M1, M2><<<(unsigned)blocks, 256, smem, st>>>(P, g, tw);
 }
 
 // ---------------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------------
+
+// ---------------------------------------------------------------------------------------
+// launch-shape table, filled by the autotuner (vd_autotune) and consulted by every launch:
+// choice 0 = register-resident four-step kernel, > 0 = lines per block of the Stockham
+// engine; absent = the built-in heuristic.  Optionally persisted in the file named by the
+// environment variable VD_TUNE_FILE (one entry per line: kind type length axis dir choice).
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+constexpr int type_code() {
+  return std::is_same<T, dd>::value ? 2 : (sizeof(T) == 4 ? 1 : 0);
+}
+
+static std::mutex g_tune_mu;
+static std::map<long long, int> g_tune;
+static bool g_tune_loaded = false;
+
+static long long tune_key(int kind, int type, int n, int axis, int dir) {
+  return ((long long)kind << 48) | ((long long)type << 40) | ((long long)(axis & 0xff) << 32) |
+         ((long long)((dir + 4) & 0xff) << 24) | (long long)(n & 0xffffff);
+}
+
+static void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("VD_TUNE_FILE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  int kind, type, n, axis, dir, choice;
+  while (std::fscanf(f, "%d %d %d %d %d %d", &kind, &type, &n, &axis, &dir, &choice) == 6)
+    g_tune[tune_key(kind, type, n, axis, dir)] = choice;
+  std::fclose(f);
+}
+
+int tune_get(int kind, int type, int n, int axis, int dir) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  auto it = g_tune.find(tune_key(kind, type, n, axis, dir));
+  return it == g_tune.end() ? -1 : it->second;
+}
+
+void tune_set(int kind, int type, int n, int axis, int dir, int choice) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  if (choice < 0) g_tune.erase(tune_key(kind, type, n, axis, dir));
+  else g_tune[tune_key(kind, type, n, axis, dir)] = choice;
+}
+
+int tune_table(int* out, int max) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  int k = 0;
+  for (const auto& kv : g_tune) {
+    if (out && k < max) {
+      const long long key = kv.first;
+      int* e = out + 6 * k;
+      e[0] = (int)(key >> 48);
+      e[1] = (int)((key >> 40) & 0xff);
+      e[2] = (int)(key & 0xffffff);
+      e[3] = (int)((key >> 32) & 0xff);
+      e[4] = (int)((key >> 24) & 0xff) - 4;
+      e[5] = kv.second;
+    }
+    ++k;
+  }
+  return k;
+}
+
+void tune_save() {
+  const char* path = std::getenv("VD_TUNE_FILE");
+  if (!path) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  FILE* f = std::fopen(path, "w");
+  if (!f) return;
+  for (const auto& kv : g_tune) {
+    const long long key = kv.first;
+    std::fprintf(f, "%d %d %d %d %d %d\n", (int)(key >> 48), (int)((key >> 40) & 0xff), (int)(key & 0xffffff),
+                 (int)((key >> 32) & 0xff), (int)((key >> 24) & 0xff) - 4, kv.second);
+  }
+  std::fclose(f);
+}
+
+// Opt a kernel into more than 48 KB of dynamic shared memory.  The limit only grows, under a
+// lock: launches from several host threads (server slots) must never lower it below the
+// size another thread is about to launch with.
+static void ensure_smem(const void* func, size_t smem) {
+  if (smem <= 48 * 1024) return;
+  static std::mutex mu;
+  static std::map<const void*, size_t> set;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = set[func];
+  if (smem > cur) {
+    cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cur = smem;
+  }
+}
 
 template <typename T>
 size_t axis_smem_bytes(const GridDesc& g, int axis) {
@@ -631,11 +732,7 @@ size_t xpass_smem_bytes(const GridDesc& g) {
 
 template <typename T, int S>
 static void set_axis_attr(size_t smem) {
-  static size_t done = 0;
-  if (smem > 48 * 1024 && smem > done) {
-    cudaFuncSetAttribute(k_axis<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    done = smem;
-  }
+  ensure_smem(reinterpret_cast<const void*>(k_axis<T, S>), smem);
 }
 
 template <typename T, int S, int N1, int N2>
@@ -643,11 +740,7 @@ static void launch_axis_r(const AxisProg& P, const GridDesc& g, const cpx<T>* tw
                           long long outer_n, cudaStream_t st) {
   const long long blocks = outer_n * ((inner_n + kRLines - 1) / kRLines);
   const size_t smem = sizeof(cpx<T>) * (size_t)(N1 * N2 + kRLines * (N1 * N2 + 1));
-  static size_t done = 0;
-  if (smem > 48 * 1024 && smem > done) {
-    cudaFuncSetAttribute(k_axis_r<T, S, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    done = smem;
-  }
+  ensure_smem(reinterpret_cast<const void*>(k_axis_r<T, S, N1, N2>), smem);
   k_axis_r<T, S, N1, N2><<<(unsigned)blocks, kRLines * N2, smem, st>>>(P, g, tw);
 }
 
@@ -661,7 +754,8 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
   AxisProg P = P0;
   for (int t = 0; t < P.nxf; ++t) split_scale(P.xf[t].scale, &P.xf[t].scale_hi, &P.xf[t].scale_lo);
   const int n = (P.axis == 2) ? g.pz.n : g.py.n;
-  const int W = tile_width(n, kEPT<T>);
+  const int choice = tune_get(0, type_code<T>(), n, P.axis, dir);
+  const int W = choice > 0 ? choice : tile_width(n, kEPT<T>);
   long long inner_n, outer_n;
   if (P.axis == 2) {
     inner_n = (long long)g.n1 * g.h0;
@@ -671,7 +765,7 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
     outer_n = g.n2;
   }
   const long long blocks = outer_n * ((inner_n + W - 1) / W);
-  const size_t smem = axis_smem_bytes<T>(g, P.axis);
+  const size_t smem = sizeof(cpx<T>) * (size_t)(n + 2 * W * n);
   const cpx<T>* twp = reinterpret_cast<const cpx<T>*>(tw);
   // algorithmic traffic: every distinct input and output field once, the symbol array once
   unsigned inmask = 0, outmask = 0;
@@ -689,8 +783,8 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
   ProfScope ps(std::is_same<T, dd>::value ? PC_AXISDD : (sizeof(T) == 8 ? PC_AXIS64 : PC_AXIS32), st, bytes,
                flops);
   if constexpr (std::is_same<T, float>::value) {
-    // register-resident four-step kernel for the common lengths
-    if (n == 256 || n == 128) {
+    // register-resident four-step kernel for the common lengths (unless tuned otherwise)
+    if ((n == 256 || n == 128) && choice <= 0) {
       if (n == 256) {
         if (dir < 0) launch_axis_r<T, -1, 16, 16>(P, g, twp, inner_n, outer_n, st);
         else launch_axis_r<T, +1, 16, 16>(P, g, twp, inner_n, outer_n, st);
@@ -715,15 +809,12 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
   XProg P = P0;
   split_scale(P.scale, &P.scale_hi, &P.scale_lo);
   const int m = g.n0 / 2;
-  const int L = lines_per_cta(m, kEPT<T>);
+  const int choice = tune_get(1, type_code<T>(), m, 0, P.mode);
+  const int L = choice > 0 ? choice : lines_per_cta(m, kEPT<T>);
   const long long nlines = (long long)g.n1 * g.n2;
   const long long blocks = (nlines + L - 1) / L;
-  const size_t smem = xpass_smem_bytes<T>(g);
-  static size_t done = 0;
-  if (smem > 48 * 1024 && smem > done) {
-    cudaFuncSetAttribute(k_xpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    done = smem;
-  }
+  const size_t smem = sizeof(cpx<T>) * (size_t)(m + (m + 2) + 2 * L * (m + 1));
+  ensure_smem(reinterpret_cast<const void*>(k_xpass<T>), smem);
   const double fc = (double)g.ncplx * sizeof(cpx<T>), fr = (double)g.nreal * sizeof(T);
   double bytes = 0, flops = 0;
   const double real_fft = (double)g.nreal * 2.5 * std::log2((double)g.n0);   // one real transform of every line
@@ -740,17 +831,18 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
   ProfScope ps(std::is_same<T, dd>::value ? PC_XPASSDD : (sizeof(T) == 8 ? PC_XPASS64 : PC_XPASS32), st, bytes,
                flops);
   if constexpr (std::is_same<T, float>::value) {
-    // register-resident kernel (float; the float-pair version needs too many registers)
+    // register-resident kernel (float; the float-pair version needs too many registers),
+    // unless the tuner chose the Stockham engine for this length
     const cpx<T>* twp = reinterpret_cast<const cpx<T>*>(tw);
-    if (m == 128) {
+    if (choice <= 0 && m == 128) {
       launch_xpass_r<T, 16, 8>(P, g, twp, st);
       return;
     }
-    if (m == 64) {
+    if (choice <= 0 && m == 64) {
       launch_xpass_r<T, 8, 8>(P, g, twp, st);
       return;
     }
-    if (m == 256) {
+    if (choice <= 0 && m == 256) {
       launch_xpass_r<T, 16, 16>(P, g, twp, st);
       return;
     }

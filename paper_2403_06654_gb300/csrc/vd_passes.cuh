@@ -78,6 +78,14 @@ void launch_axis(const AxisProg& P, int dir, const GridDesc& g, const void* tw, 
 template <typename T>
 void launch_xpass(const XProg& P, const GridDesc& g, const void* tw, cudaStream_t st);
 
+// launch-shape table (vd_passes.cu).  kind 0: y/z pass (key: type, length, axis, direction);
+// kind 1: x pass (key: type, n0/2, axis 0, mode).  type: 0 double, 1 float, 2 float-pair.
+// choice: 0 register four-step kernel, > 0 lines per block, < 0 (get) absent / (set) erase.
+int tune_get(int kind, int type, int n, int axis, int dir);
+void tune_set(int kind, int type, int n, int axis, int dir, int choice);
+int tune_table(int* out, int max);   // 6 ints per entry; returns the entry count
+void tune_save();                    // write the table to $VD_TUNE_FILE (if set)
+
 // shared memory footprint (bytes) of the pass kernels, for the attribute setup
 template <typename T>
 size_t axis_smem_bytes(const GridDesc& g, int axis);
