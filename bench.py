@@ -56,6 +56,7 @@ def parse():
                     help="solve: the 256^3 solve-rate line (with a short serving run); serve: the serving line")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving run of the solve line")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched graph run of the solve line")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     ap.add_argument("--serve-count", type=int, default=None, help="requests of the serving trace")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrival rate (req/s)")
     ap.add_argument("--serve-inflight", type=int, default=8, help="server execution slots")
@@ -647,6 +648,12 @@ def main():
 
     head = args.precision
     side = "mixed" if head == "mixed_dd" else "mixed_dd"
+    tuned = None
+    if not args.no_autotune:
+        t_tune = time.perf_counter()
+        vd.vd_autotune(G, ("fp64", "mixed", "mixed_dd"))
+        tuned = {"seconds": time.perf_counter() - t_tune,
+                 "table": [e for e in vd.vd_autotune_table() if e[2] in (n, n // 2)]}
     # warm-up
     for _ in range(args.warmup):
         solve(head)
@@ -809,7 +816,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic",
         "config": {"workload": WORKLOAD, "solver": args.solver, "precision": head, "tol": args.tol,
                    "grid": [n, n, n], "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (each 256^3 field 134 MB; working set ~1.6 GB)"},
+                   "l2": "inputs larger than L2 (each 256^3 field 134 MB; working set ~1.6 GB)",
+                   "launch_shapes": "autotuned before the timed region" if tuned else "built-in"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "mean": float(np.mean(lat))},
         "iters": infos[-1]["iters"], "outer_iters": infos[-1]["outer_iters"],
@@ -835,6 +843,7 @@ def main():
         "workloads": extras,
         "serving": serving,
         "batch": batch,
+        "autotune": tuned,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
