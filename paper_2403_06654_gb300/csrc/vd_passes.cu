@@ -82,7 +82,7 @@ static inline int lines_per_cta(int m, int ept) {
 // ---------------------------------------------------------------------------------------
 
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 ? 2 : 3)) k_axis(const AxisProg P, const GridDesc g,
+__global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 : 3)) k_axis(const AxisProg P, const GridDesc g,
                                                    const cpx<T>* __restrict__ twg, int lw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (P.done && *P.done) return;
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kRLines * N2, (sizeof(T) == 4 ? 2 : 1)) k_axis
 // ---------------------------------------------------------------------------------------
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_xpass(const XProg P, const GridDesc g,
+__global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 4 : 1)) k_xpass(const XProg P, const GridDesc g,
                                                     const cpx<T>* __restrict__ twg, int llpc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (P.done && *P.done) return;
@@ -665,6 +665,12 @@ void tune_set(int kind, int type, int n, int axis, int dir, int choice) {
   tune_load_locked();
   if (choice < 0) g_tune.erase(tune_key(kind, type, n, axis, dir));
   else g_tune[tune_key(kind, type, n, axis, dir)] = choice;
+}
+
+int default_shape(int kind, int type, int n) {
+  const int ept = (type == 1) ? 16 : 8;
+  if (kind == 0) return (type == 1 && (n == 128 || n == 256)) ? 0 : tile_width(n, ept);
+  return (type == 1 && (n == 64 || n == 128 || n == 256)) ? 0 : lines_per_cta(n, ept);
 }
 
 int tune_table(int* out, int max) {

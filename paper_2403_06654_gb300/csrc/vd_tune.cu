@@ -3,9 +3,10 @@
 // For a grid and each requested arithmetic type, every pass the solver uses -- the y and z
 // passes in both directions, and the x pass in its three forms (forward real-to-half-spectrum,
 // inverse, and the fused inverse-weight-forward form of the operators) -- is timed with CUDA
-// events for each candidate shape: the register-resident four-step kernel where one exists
-// (float, lengths 128 and 256; x pass n0 = 128, 256, 512) and the Stockham engine with 1, 2,
-// 4, ... lines per block up to the shared-memory limit.  The fastest shape goes into the
+// events (median of seven launches) for each candidate shape: the register-resident four-step
+// kernel where one exists (float, lengths 128 and 256; x pass n0 = 128, 256, 512) and the
+// Stockham engine with 1, 2, 4, ... lines per block up to the shared-memory limit.  A shape
+// replaces the built-in choice only when it is at least 3% faster; the winner goes into the
 // process-wide launch table that every later launch consults (and, with VD_TUNE_FILE set, into
 // that file).  Shapes change only the work distribution, never the arithmetic of a line,
 // except that the register kernel and the Stockham engine round differently (both are
@@ -36,22 +37,25 @@ struct Timer {
   }
 };
 
-// median-free best of three launches after one warm-up (ms per launch)
+// median of seven timed launches after two warm-ups (ms per launch)
 template <typename F>
 float time_it(F&& launch, cudaStream_t st, Timer& t) {
   launch();
-  float best = 1e30f;
-  for (int r = 0; r < 3; ++r) {
+  launch();
+  float ms[7];
+  for (int r = 0; r < 7; ++r) {
     cudaEventRecord(t.a, st);
     launch();
     cudaEventRecord(t.b, st);
     cudaEventSynchronize(t.b);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, t.a, t.b);
-    best = std::min(best, ms);
+    cudaEventElapsedTime(&ms[r], t.a, t.b);
   }
-  return best;
+  std::sort(ms, ms + 7);
+  return ms[3];
 }
+
+// keep the built-in shape unless a candidate beats it clearly (timing noise must not flip it)
+constexpr float kSwitchGain = 0.97f;
 
 Xf plain_xf() {
   Xf x{};
@@ -79,7 +83,8 @@ vd_status tune_type(const vd_grid* G, const void* tw, void* a, void* b, cudaStre
     const int n = axis == 2 ? g.pz.n : g.py.n;
     const long long inner = axis == 2 ? (long long)g.n1 * g.h0 : g.h0;
     std::vector<int> cand;
-    if (type == 1 && (n == 128 || n == 256)) cand.push_back(0);
+    const bool reg = type == 1 && (n == 128 || n == 256);
+    if (reg) cand.push_back(0);
     for (int W = 1; W <= 64; W *= 2) {
       if (sizeof(cpx<T>) * (size_t)(n + 2 * W * n) > kSmemCap) break;
       if (W > 1 && W > 2 * inner) break;
@@ -92,8 +97,12 @@ vd_status tune_type(const vd_grid* G, const void* tw, void* a, void* b, cudaStre
       P.in[0] = a;
       P.out[0] = b;
       P.axis = axis;
+      // the built-in shape first: the register kernel, else the heuristic tile width
+      tune_set(0, type, n, axis, dir, -1);
+      float tdef = time_it([&] { launch_axis<T>(P, dir, g, tw, st); }, st, tm);
+      VD_CUDA(cudaGetLastError());
       int best = -1;
-      float tbest = 1e30f;
+      float tbest = tdef * kSwitchGain;
       for (int c : cand) {
         tune_set(0, type, n, axis, dir, c);
         const float ms = time_it([&] { launch_axis<T>(P, dir, g, tw, st); }, st, tm);
@@ -103,7 +112,8 @@ vd_status tune_type(const vd_grid* G, const void* tw, void* a, void* b, cudaStre
           best = c;
         }
       }
-      tune_set(0, type, n, axis, dir, best);
+      (void)reg;
+      tune_set(0, type, n, axis, dir, best >= 0 ? best : default_shape(0, type, n));
     }
   }
   // x pass: forward (mode 1), inverse (mode 2), fused (mode 0 with a weight field)
@@ -124,8 +134,11 @@ vd_status tune_type(const vd_grid* G, const void* tw, void* a, void* b, cudaStre
     X.out[0] = (mode == 2) ? a : b;
     X.wfield = (mode == 0) ? a : nullptr;
     X.scale = (mode == 2) ? 1.0 / (double)g.nreal : 0.5;
+    tune_set(1, type, m, 0, mode, -1);
+    const float tdef = time_it([&] { launch_xpass<T>(X, g, tw, st); }, st, tm);
+    VD_CUDA(cudaGetLastError());
     int best = -1;
-    float tbest = 1e30f;
+    float tbest = tdef * kSwitchGain;
     for (int c : cand) {
       tune_set(1, type, m, 0, mode, c);
       const float ms = time_it([&] { launch_xpass<T>(X, g, tw, st); }, st, tm);
@@ -135,7 +148,7 @@ vd_status tune_type(const vd_grid* G, const void* tw, void* a, void* b, cudaStre
         best = c;
       }
     }
-    tune_set(1, type, m, 0, mode, best);
+    tune_set(1, type, m, 0, mode, best >= 0 ? best : default_shape(1, type, m));
   }
   return VD_OK;
 }
