@@ -635,7 +635,8 @@ vd_status enqueue_solve_graph(const vd_grid* G, vd_op op, vd_solver solver, cons
   const int ncomp = op_ncomp(G, op);
   const long long len = G->g.ncplx * ncomp;
   VD_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned), st));
-  fill_symbol<double>(G, op_symbol(op), opp ? opp->a : 0.0, L.sym, st);
+  // the double symbol serves only double Krylov iterations
+  if (precision == VD_PREC_FP64) fill_symbol<double>(G, op_symbol(op), opp ? opp->a : 0.0, L.sym, st);
   const bool dd = precision == VD_PREC_MIXED_DD && op != VD_OP_VELOCITY;
   if (dd) fwd_transform_dd(G, b, L.bh, L.tmp, st);
   else fwd_all(G, ncomp, b, L.bh, st);
@@ -797,7 +798,8 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
   const int symkind = op_symbol(op);
   // the reduction ticket counter must start at zero (the workspace is uninitialised memory)
   VD_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned), st));
-  fill_symbol<double>(G, symkind, opp ? opp->a : 0.0, L.sym, st);
+  // the double symbol serves only double Krylov iterations (the refinement applies A unpreconditioned)
+  if (prm->precision == VD_PREC_FP64) fill_symbol<double>(G, symkind, opp ? opp->a : 0.0, L.sym, st);
   // spectral right-hand side and initial guess (float-pair transforms in VD_PREC_MIXED_DD
   // pressure solves, double otherwise)
   const bool dd_io = prm->precision == VD_PREC_MIXED_DD && op != VD_OP_VELOCITY;

@@ -631,31 +631,32 @@ void velocity_combine_launch(const vd_grid* G, int sz, const void* u, const void
 
 template <typename T>
 __global__ void k_fill_symbol(GridDesc g, int kind, double a, T* __restrict__ out) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < g.ncplx;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long line = e / g.h0;
-    const int kxi = (int)(e - line * g.h0);
-    const int kyi = (int)(line % g.n1);
-    const int kzi = (int)(line / g.n1);
-    // K_rho symbols use the full wavenumbers (Nyquist kept); the others k~
-    const bool full = (kind == SYM_KLAP_INV || kind == SYM_KLAP);
+  // field offsets fit in 32 bits (ncplx < 2^31 is checked when the grid is created)
+  const int nc = (int)g.ncplx;
+  // K_rho symbols use the full wavenumbers (Nyquist kept); the others k~
+  const bool full = (kind == SYM_KLAP_INV || kind == SYM_KLAP);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nc; e += gridDim.x * blockDim.x) {
+    const int line = e / g.h0;
+    const int kxi = e - line * g.h0;
+    const int kyi = line % g.n1;
+    const int kzi = line / g.n1;
     auto fq = [&](int m, int n) { return full ? freq_full(m, n) : freq_tilde(m, n); };
-    const double kx = g.kfac[0] * fq(kxi, g.n0);
-    double k2 = kx * kx;
+    const T kx = (T)g.kfac[0] * (T)fq(kxi, g.n0);
+    T k2 = kx * kx;
     if (g.ndim >= 2) {
-      const double ky = g.kfac[1] * fq(kyi, g.n1);
+      const T ky = (T)g.kfac[1] * (T)fq(kyi, g.n1);
       k2 += ky * ky;
     }
     if (g.ndim == 3) {
-      const double kz = g.kfac[2] * fq(kzi, g.n2);
+      const T kz = (T)g.kfac[2] * (T)fq(kzi, g.n2);
       k2 += kz * kz;
     }
-    double v = 1.0;
-    if (kind == SYM_PRESSURE || kind == SYM_KLAP_INV) v = (k2 == 0.0) ? 0.0 : -1.0 / k2;
-    else if (kind == SYM_VELOCITY) v = 1.0 / (1.0 + a * k2);
-    else if (kind == SYM_PROJECT) v = (k2 == 0.0) ? 0.0 : 1.0;
+    T v = T(1);
+    if (kind == SYM_PRESSURE || kind == SYM_KLAP_INV) v = (k2 == T(0)) ? T(0) : -recip(k2);
+    else if (kind == SYM_VELOCITY) v = recip(T(1) + (T)a * k2);
+    else if (kind == SYM_PROJECT) v = (k2 == T(0)) ? T(0) : T(1);
     else if (kind == SYM_KLAP) v = -k2;
-    out[e] = (T)v;
+    out[e] = v;
   }
 }
 
