@@ -228,6 +228,18 @@ vd_status vd_flow_set_state(vd_flow* flow, const double* rho, const double* u, v
 vd_status vd_flow_get_state(const vd_flow* flow, double* rho, double* u, double* gradp, double* phi,
                             vd_stream stream);
 vd_status vd_flow_step(vd_flow* flow, double dt, vd_step_info* info, vd_stream stream);
+/*
+ * Checkpoint / resume (not in the paper).  A snapshot is the complete state a step reads:
+ * rho, u, grad p, phi (the pressure solve's initial guess) and the previous step's explicit
+ * terms of the Adams--Bashforth extrapolation with their presence flag, behind a header that
+ * records the grid.  vd_flow_save copies it to a host buffer (synchronises `stream`);
+ * vd_flow_load restores it into a flow on a grid of the same sizes (INVALID_ARG otherwise), and
+ * the steps that follow are bit-identical to those of the flow that was saved (same kernels in
+ * the same order, the same launch shapes).
+ */
+size_t vd_flow_snapshot_bytes(const vd_flow* flow);
+vd_status vd_flow_save(const vd_flow* flow, void* host, size_t bytes, vd_stream stream);
+vd_status vd_flow_load(vd_flow* flow, const void* host, size_t bytes, vd_stream stream);
 
 /*
  * Request server (continuous batching; not in the paper).  Pressure solves of different
@@ -277,6 +289,9 @@ vd_status vd_server_create(const vd_server_params* params, vd_server** out);
 size_t vd_server_request_bytes(const vd_request* request);
 /* enqueue (the request is copied); bytes = vd_server_request_bytes(request) */
 vd_status vd_server_submit(vd_server* server, const vd_request* request, size_t bytes);
+/* withdraw a request that is still queued (not admitted): it produces no completion.
+ * INVALID_ARG if no queued request has this id (unknown, admitted or completed). */
+vd_status vd_server_cancel(vd_server* server, unsigned long long id);
 /* move up to max completions into out; returns how many */
 int vd_server_poll(vd_server* server, vd_completion* out, int max);
 /* server-owned solution of completed request id: copy it to dst (n0 n1 n2 doubles, device,

@@ -25,6 +25,7 @@ VD_OK, VD_ERR_INVALID_ARG, VD_ERR_OOM, VD_ERR_CUDA = 0, 1, 2, 3
 VD_ERR_NOT_CONVERGED, VD_ERR_BREAKDOWN, VD_ERR_DIVERGED, VD_ERR_NONFINITE, VD_ERR_NO_DENSITY = 4, 5, 6, 7, 8
 STATUS_NAMES = {0: "converged", 1: "invalid_arg", 2: "oom", 3: "cuda", 4: "max_iter", 5: "breakdown",
                 6: "diverged", 7: "nonfinite", 8: "no_density"}
+STATUS_CODES = {v: k for k, v in STATUS_NAMES.items()}
 VD_OP_PRESSURE, VD_OP_VELOCITY, VD_OP_KRHO = 0, 1, 2
 VD_SOLVER_CG, VD_SOLVER_GMRES, VD_SOLVER_RMR = 0, 1, 2
 VD_PREC_FP64, VD_PREC_MIXED, VD_PREC_MIXED_DD = 0, 1, 2
@@ -135,9 +136,13 @@ _SIGS = {
     "vd_flow_set_state": (_I, [_P, _P, _P, _P]),
     "vd_flow_get_state": (_I, [_P, _P, _P, _P, _P, _P]),
     "vd_flow_step": (_I, [_P, ctypes.c_double, ctypes.POINTER(vd_step_info), _P]),
+    "vd_flow_snapshot_bytes": (_SZ, [_P]),
+    "vd_flow_save": (_I, [_P, _P, _SZ, _P]),
+    "vd_flow_load": (_I, [_P, _P, _SZ, _P]),
     "vd_server_create": (_I, [ctypes.POINTER(vd_server_params), ctypes.POINTER(_P)]),
     "vd_server_request_bytes": (_SZ, [ctypes.POINTER(vd_request)]),
     "vd_server_submit": (_I, [_P, ctypes.POINTER(vd_request), _SZ]),
+    "vd_server_cancel": (_I, [_P, ctypes.c_ulonglong]),
     "vd_server_poll": (_I, [_P, ctypes.POINTER(vd_completion), _I]),
     "vd_server_fetch": (_I, [_P, ctypes.c_ulonglong, _P, _P]),
     "vd_server_release": (_I, [_P, ctypes.c_ulonglong]),
@@ -303,6 +308,10 @@ def vd_server_request_bytes(req):
 
 def vd_server_submit(h, req, nbytes):
     _check(lib().vd_server_submit(h, ctypes.byref(req), nbytes))
+
+
+def vd_server_cancel(h, rid):
+    _check(lib().vd_server_cancel(h, rid))
 
 
 def vd_server_poll(h, max_n=256):
@@ -560,6 +569,18 @@ class Flow:
         phi = torch.empty_like(rho)
         vd_flow_get_state(self.h, rho, u, gp, phi, stream)
         return rho, u, gp, phi
+
+    def save(self, stream=None):
+        """Snapshot of the complete step state in host memory (bytes)."""
+        nb = int(lib().vd_flow_snapshot_bytes(self.h))
+        buf = (ctypes.c_char * nb)()
+        _check(lib().vd_flow_save(self.h, buf, nb, _stream(stream)))
+        return bytes(buf)
+
+    def load(self, snap, stream=None):
+        """Restore a snapshot taken by save() on a grid of the same sizes."""
+        buf = ctypes.create_string_buffer(snap, len(snap))
+        _check(lib().vd_flow_load(self.h, buf, len(snap), _stream(stream)))
 
     def step(self, dt, stream=None):
         info = vd_step_info()

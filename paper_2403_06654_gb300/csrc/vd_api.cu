@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -868,7 +869,10 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
     const double itol = prm->inner_tol > 0 ? prm->inner_tol : 1e-5;
     const int max_outer = 20;
     for (;;) {
-      const double rel = bnorm > 0 ? rnorm / bnorm : 0.0;
+      // a non-finite norm is reported as such (NaN > 0 is false: it must not read as a zero rhs)
+      const double rel = (!std::isfinite(bnorm) || !std::isfinite(rnorm))
+                             ? std::numeric_limits<double>::quiet_NaN()
+                             : (bnorm > 0 ? rnorm / bnorm : 0.0);
       res.relres = rel;
       if (!std::isfinite(rel)) {
         res.status = VD_ERR_NONFINITE;

@@ -1100,7 +1100,8 @@ __global__ void k_out_check(OState* o, cudaGraphConditionalHandle h_loop, cudaGr
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double rnorm = sqrt(o->rr);
   const double bnorm = sqrt(o->bb);
-  const double rel = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+  // a non-finite norm must not read as a zero right-hand side (NaN > 0 is false)
+  const double rel = (!isfinite(bnorm) || !isfinite(rnorm)) ? (double)NAN : (bnorm > 0.0 ? rnorm / bnorm : 0.0);
   o->rnorm = rnorm;
   o->rel = rel;
   if (o->force) {

@@ -77,7 +77,7 @@ struct vd_server {
   size_t budget = 0;
   int idle = 0;                      // idle workers
   long long inflight = 0;            // admitted + running
-  long long submitted = 0, completed = 0;
+  long long submitted = 0, completed = 0, cancelled = 0;
   bool stop = false;
   std::vector<std::thread> workers;
 
@@ -255,6 +255,21 @@ vd_status vd_server_submit(vd_server* S, const vd_request* r, size_t bytes) {
   return VD_OK;
 }
 
+vd_status vd_server_cancel(vd_server* S, unsigned long long id) {
+  if (!S) return vd::fail(VD_ERR_INVALID_ARG, "null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+    if (it->r.id == id) {
+      S->queue.erase(it);
+      ++S->cancelled;
+      S->admit_locked();
+      S->cv_done.notify_all();
+      return VD_OK;
+    }
+  }
+  return vd::fail(VD_ERR_INVALID_ARG, "no queued request with this id");
+}
+
 int vd_server_poll(vd_server* S, vd_completion* out, int max) {
   if (!S || !out || max <= 0) return 0;
   std::lock_guard<std::mutex> lk(S->mu);
@@ -279,7 +294,7 @@ vd_status vd_server_release(vd_server* S, unsigned long long id) {
 vd_status vd_server_drain(vd_server* S) {
   if (!S) return vd::fail(VD_ERR_INVALID_ARG, "null server");
   std::unique_lock<std::mutex> lk(S->mu);
-  S->cv_done.wait(lk, [&] { return S->completed == S->submitted; });
+  S->cv_done.wait(lk, [&] { return S->completed + S->cancelled == S->submitted; });
   return VD_OK;
 }
 
@@ -299,7 +314,7 @@ vd_status vd_server_destroy(vd_server* S) {
   if (!S) return VD_OK;
   {
     std::unique_lock<std::mutex> lk(S->mu);
-    S->cv_done.wait(lk, [&] { return S->completed == S->submitted; });
+    S->cv_done.wait(lk, [&] { return S->completed + S->cancelled == S->submitted; });
     S->stop = true;
   }
   S->cv_work.notify_all();

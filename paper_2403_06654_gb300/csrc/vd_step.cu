@@ -256,6 +256,72 @@ vd_status vd_flow_get_state(const vd_flow* F, double* rho, double* u, double* gr
   return VD_OK;
 }
 
+// snapshot layout: header, then rho (1), u (d), grad p (d), phi (1), nrho_prev (1), nu_prev (d)
+struct SnapHeader {
+  char magic[8];
+  int version, ndim, n[3], have_prev;
+  long long nreal;
+};
+static const char kSnapMagic[8] = {'v', 'd', 'f', 'l', 'o', 'w', 's', '1'};
+
+static size_t snap_fields(const vd_flow* F) { return (size_t)(3 * F->d + 3); }
+
+size_t vd_flow_snapshot_bytes(const vd_flow* F) {
+  if (!F) return 0;
+  return sizeof(SnapHeader) + snap_fields(F) * F->nr * sizeof(double);
+}
+
+vd_status vd_flow_save(const vd_flow* F, void* host, size_t bytes, vd_stream stream) {
+  if (!F || !host) return fail(VD_ERR_INVALID_ARG, "null argument");
+  if (bytes < vd_flow_snapshot_bytes(F)) return fail(VD_ERR_OOM, "buffer smaller than vd_flow_snapshot_bytes()");
+  cudaStream_t st = (cudaStream_t)stream;
+  SnapHeader h{};
+  std::memcpy(h.magic, kSnapMagic, 8);
+  h.version = 1;
+  h.ndim = F->d;
+  h.n[0] = F->G->g.n0;
+  h.n[1] = F->G->g.n1;
+  h.n[2] = F->G->g.n2;
+  h.have_prev = F->have_prev;
+  h.nreal = (long long)F->nr;
+  char* o = static_cast<char*>(host);
+  std::memcpy(o, &h, sizeof h);
+  o += sizeof h;
+  const size_t fb = F->nr * sizeof(double);
+  const double* src[6] = {F->rho, F->u, F->gradp, F->phi, F->nrho_prev, F->nu_prev};
+  const size_t cnt[6] = {1, (size_t)F->d, (size_t)F->d, 1, 1, (size_t)F->d};
+  for (int k = 0; k < 6; ++k) {
+    VD_CUDA(cudaMemcpyAsync(o, src[k], cnt[k] * fb, cudaMemcpyDeviceToHost, st));
+    o += cnt[k] * fb;
+  }
+  VD_CUDA(cudaStreamSynchronize(st));
+  return VD_OK;
+}
+
+vd_status vd_flow_load(vd_flow* F, const void* host, size_t bytes, vd_stream stream) {
+  if (!F || !host) return fail(VD_ERR_INVALID_ARG, "null argument");
+  if (bytes < sizeof(SnapHeader)) return fail(VD_ERR_INVALID_ARG, "snapshot too short");
+  SnapHeader h;
+  std::memcpy(&h, host, sizeof h);
+  if (std::memcmp(h.magic, kSnapMagic, 8) != 0 || h.version != 1) return fail(VD_ERR_INVALID_ARG, "not a snapshot");
+  if (h.ndim != F->d || h.n[0] != F->G->g.n0 || h.n[1] != F->G->g.n1 || h.n[2] != F->G->g.n2 ||
+      h.nreal != (long long)F->nr)
+    return fail(VD_ERR_INVALID_ARG, "snapshot of another grid");
+  if (bytes < vd_flow_snapshot_bytes(F)) return fail(VD_ERR_INVALID_ARG, "snapshot too short");
+  cudaStream_t st = (cudaStream_t)stream;
+  const char* o = static_cast<const char*>(host) + sizeof h;
+  const size_t fb = F->nr * sizeof(double);
+  double* dst[6] = {F->rho, F->u, F->gradp, F->phi, F->nrho_prev, F->nu_prev};
+  const size_t cnt[6] = {1, (size_t)F->d, (size_t)F->d, 1, 1, (size_t)F->d};
+  for (int k = 0; k < 6; ++k) {
+    VD_CUDA(cudaMemcpyAsync(dst[k], o, cnt[k] * fb, cudaMemcpyHostToDevice, st));
+    o += cnt[k] * fb;
+  }
+  VD_CUDA(cudaStreamSynchronize(st));
+  F->have_prev = h.have_prev;
+  return VD_OK;
+}
+
 vd_status vd_flow_step(vd_flow* F, double dt, vd_step_info* info, vd_stream stream) {
   if (!F || !(dt > 0)) return fail(VD_ERR_INVALID_ARG, "null flow or dt <= 0");
   vd_grid* G = F->G;

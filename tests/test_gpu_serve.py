@@ -163,3 +163,31 @@ def test_server_owned_solutions_fetch_and_release():
         assert e.value.status == vd.VD_ERR_INVALID_ARG
     finally:
         vd.vd_server_destroy(S)
+
+
+def test_server_cancel_queued_requests():
+    """With one slot the later requests queue; cancelled ones produce no completion, the rest
+    complete, and a request that already completed cannot be cancelled."""
+    n, L = (64, 64, 64), (2 * math.pi,) * 3
+    rho = torch.from_numpy(inputs.slab_density(n, L, 20.0, 1, 1.0, math.pi, 3 * L[1] / n[1])).cuda()
+    b = torch.from_numpy(inputs.smooth_random_field(n, L, 12, kmax=5)).cuda()
+    S = vd.vd_server_create(max_inflight=1, hbm_budget=0)
+    try:
+        for i in range(6):
+            q = vd.make_request(i, n, L, rho, b, None, solver="cg", tol=1e-10, precision="fp64")
+            vd.vd_server_submit(S, q, vd.vd_server_request_bytes(q))
+        vd.vd_server_cancel(S, 3)
+        vd.vd_server_cancel(S, 5)
+        vd.vd_server_drain(S)
+        comps = vd.vd_server_poll(S, 64)
+        assert sorted(int(c.id) for c in comps) == [0, 1, 2, 4]
+        assert all(c.status == 0 for c in comps)
+        for c in comps:
+            vd.vd_server_release(S, int(c.id))
+        with pytest.raises(vd.VDError) as e:
+            vd.vd_server_cancel(S, 0)
+        assert e.value.status == vd.VD_ERR_INVALID_ARG
+        st = vd.vd_server_stats(S)
+        assert st["reserved"] == 0 and st["completed"] == 4
+    finally:
+        vd.vd_server_destroy(S)
