@@ -82,7 +82,7 @@ static inline int lines_per_cta(int m, int ept) {
 // ---------------------------------------------------------------------------------------
 
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 : 3)) k_axis(const AxisProg P, const GridDesc g,
+__global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 : (std::is_same<T, dd>::value ? 4 : 3))) k_axis(const AxisProg P, const GridDesc g,
                                                    const cpx<T>* __restrict__ twg, int lw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (P.done && *P.done) return;
