@@ -506,7 +506,7 @@ __device__ __forceinline__ void fourstep(cpx<T> (&u)[M1], cpx<T>* Yl, const cpx<
 }
 
 template <typename T, int M1, int M2>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_xpass_r(const XProg P, const GridDesc g,
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_xpass_r(const XProg P, const GridDesc g,
                                                                           const cpx<T>* __restrict__ twg) {
   using X = XR<T, M1, M2>;
   constexpr int M = X::M, LINES = X::LINES, LS = X::LS;
