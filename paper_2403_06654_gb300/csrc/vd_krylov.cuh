@@ -13,7 +13,7 @@
 namespace vd {
 
 constexpr int kMaxRestart = 64;
-constexpr int kRedBlocks = 1216;  // fixed block count of every reduction (deterministic; 8 per SM on 152 SMs)
+constexpr int kRedBlocks = 608;   // fixed block count of every reduction (deterministic; 4 per SM on 152 SMs)
 constexpr int kRedThreads = 256;
 
 // device-resident scalar state of one solve
