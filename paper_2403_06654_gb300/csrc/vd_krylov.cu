@@ -318,23 +318,28 @@ __device__ __forceinline__ T pweight(int kx, int h0) {
   return (kx == 0 || kx == h0 - 1) ? T(1) : T(2);
 }
 
-// Double-precision accumulator fed by short sub-sums in the vector precision (16 terms):
-// the FP64 pipe of GB300 runs at 1/69 of the float rate, so one double add per 16 elements
-// keeps the reductions at memory speed while every cross-element sum is done in double.
+// Per-thread accumulator of a reduction.  Double vectors add in double.  Float vectors add
+// with a compensated float sum (Knuth's two-sum carries the rounding error of every addition
+// in a second float), about as accurate as a double accumulation of the float terms but
+// without FP64 work per element: the FP64 pipe of GB300 is ~1/64 of the float rate and was
+// the limiter of these memory-bound kernels.  The cross-thread sum of the per-thread totals
+// is done in double (reduce_last).
 template <typename T>
 struct Acc {
   double a = 0.0;
-  T s = T(0);
-  int c = 0;
-  __device__ __forceinline__ void add(T v) {
-    s += v;
-    if (++c == 16) {
-      a += (double)s;
-      s = T(0);
-      c = 0;
-    }
+  __device__ __forceinline__ void add(T v) { a += (double)v; }
+  __device__ __forceinline__ double total() const { return a; }
+};
+template <>
+struct Acc<float> {
+  float s = 0.0f, c = 0.0f;   // value s + c
+  __device__ __forceinline__ void add(float v) {
+    const float t = s + v;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
   }
-  __device__ __forceinline__ double total() const { return a + (double)s; }
+  __device__ __forceinline__ double total() const { return (double)s + (double)c; }
 };
 
 // CG start: p = S r, reduce [bb, rr, rz]

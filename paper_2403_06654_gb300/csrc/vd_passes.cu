@@ -21,9 +21,11 @@ namespace vd {
 
 // Element load / store of a pass.  The float-pair instantiation (T = dd) may read its input
 // from, and write its output to, double fields (the Krylov vectors), converting on the fly.
-template <typename T>
+// CV = false compiles the plain path only (programs without any double field): the
+// conversion code is then absent instead of merely skipped.
+template <typename T, bool CV = true>
 __device__ __forceinline__ cpx<T> ld_el(const void* p, int conv, int go) {
-  if constexpr (std::is_same<T, dd>::value) {
+  if constexpr (std::is_same<T, dd>::value && CV) {
     if (conv) {
       const cpx<double> v = reinterpret_cast<const cpx<double>*>(p)[go];
       return mk<T>(dd_from_double(v.x), dd_from_double(v.y));
@@ -31,9 +33,9 @@ __device__ __forceinline__ cpx<T> ld_el(const void* p, int conv, int go) {
   }
   return reinterpret_cast<const cpx<T>*>(p)[go];
 }
-template <typename T>
+template <typename T, bool CV = true>
 __device__ __forceinline__ void st_el(void* p, int conv, int go, cpx<T> v, bool first) {
-  if constexpr (std::is_same<T, dd>::value) {
+  if constexpr (std::is_same<T, dd>::value && CV) {
     if (conv) {
       cpx<double>* q = reinterpret_cast<cpx<double>*>(p) + go;
       const cpx<double> d = mk<double>(dd_to_double(v.x), dd_to_double(v.y));
@@ -81,7 +83,7 @@ static inline int lines_per_cta(int m, int ept) {
 // strided axis pass
 // ---------------------------------------------------------------------------------------
 
-template <typename T, int S>
+template <typename T, int S, bool CV>
 __global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 : (std::is_same<T, dd>::value ? 4 : 3))) k_axis(const AxisProg P, const GridDesc g,
                                                    const cpx<T>* __restrict__ twg, int lw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -163,9 +165,9 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 
         for (int q = 0; q < nq; ++q) {
           const int i = ib + q * istep;
           const int go = g0 + q * gstep;
-          cpx<T> v = scal(ld_el<T>(src, cin, go), mult(xf.pre, i, go, scale));
+          cpx<T> v = scal(ld_el<T, CV>(src, cin, go), mult(xf.pre, i, go, scale));
           if (xf.pre & MUL_IK) v = mul_i(v);
-          st_el<T>(dst, cout, go, v, xf.first);
+          st_el<T, CV>(dst, cout, go, v, xf.first);
         }
       }
       continue;
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 
       const int i = ib + q * istep;
       const int go = g0 + q * gstep;
       cpx<T> v = mk<T>(T(0), T(0));
-      if (colok) v = ld_el<T>(src, cin, go);
+      if (colok) v = ld_el<T, CV>(src, cin, go);
       if (xf.pre) {
         v = scal(v, mult(xf.pre, i, go, T(1)));
         if (xf.pre & MUL_IK) v = mul_i(v);
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 
         } else {
           v = scal(v, scale);
         }
-        st_el<T>(dst, cout, go, v, xf.first);
+        st_el<T, CV>(dst, cout, go, v, xf.first);
       }
     }
   }
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(kRLines * N2, (sizeof(T) == 4 ? 2 : 1)) k_axis
 // contiguous x pass (real <-> half spectrum through a complex FFT of length n0/2)
 // ---------------------------------------------------------------------------------------
 
-template <typename T>
+template <typename T, bool CV>
 __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 4 : 1)) k_xpass(const XProg P, const GridDesc g,
                                                     const cpx<T>* __restrict__ twg, int llpc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 4 : 1)
       const int cin = (P.conv_in >> c) & 1;
       const int rbase = (int)((line0 + line) * m);
       if (lok)
-        for (int j = t0; j < m; j += TPL) A[lofs + j] = ld_el<T>(P.in[c], cin, rbase + j);
+        for (int j = t0; j < m; j += TPL) A[lofs + j] = ld_el<T, CV>(P.in[c], cin, rbase + j);
       res = fft_lines<T, -1>(A, B, 1, lofs, t0, TPL, g.px, twm);
     } else {
       const int cin = (P.conv_in >> c) & 1;
@@ -393,7 +395,7 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 4 : 1)
       const int pre = P.pre[c];
       if (lok) {
         for (int k = t0; k < h0; k += TPL) {
-          cpx<T> v = ld_el<T>(P.in[c], cin, lbase + k);
+          cpx<T> v = ld_el<T, CV>(P.in[c], cin, lbase + k);
           if (pre) {
             const T kx = kfx * (T)freq_tilde(k, g.n0);
             T cc = T(1);
@@ -420,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 4 : 1)
         const int cout = (P.conv_out >> c) & 1;
         const int rbase = (int)((line0 + line) * m);
         if (lok)
-          for (int j = t0; j < m; j += TPL) st_el<T>(P.out[c], cout, rbase + j, scal(res[lofs + j], scale), true);
+          for (int j = t0; j < m; j += TPL) st_el<T, CV>(P.out[c], cout, rbase + j, scal(res[lofs + j], scale), true);
         continue;
       }
       if (P.wfield && lok) {
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 4 : 1)
         if (post & (MUL_NEGK2 | MUL_IK2)) cc *= -kx * kx;
         X = scal(X, cc);
         if (post & MUL_IK) X = mul_i(X);
-        st_el<T>(P.out[c], cout, obase + k, X, true);
+        st_el<T, CV>(P.out[c], cout, obase + k, X, true);
       }
     }
   }
@@ -736,9 +738,9 @@ size_t xpass_smem_bytes(const GridDesc& g) {
   return sizeof(cpx<T>) * (size_t)(m + (m + 2) + 2 * L * (m + 1));
 }
 
-template <typename T, int S>
+template <typename T, int S, bool CV>
 static void set_axis_attr(size_t smem) {
-  ensure_smem(reinterpret_cast<const void*>(k_axis<T, S>), smem);
+  ensure_smem(reinterpret_cast<const void*>(k_axis<T, S, CV>), smem);
 }
 
 template <typename T, int S, int N1, int N2>
@@ -801,12 +803,19 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
       return;
     }
   }
-  if (dir < 0) {
-    set_axis_attr<T, -1>(smem);
-    k_axis<T, -1><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, ilog2(W));
+  const bool cv = (P.conv_in | P.conv_out) != 0;
+  if (dir < 0 && cv) {
+    set_axis_attr<T, -1, true>(smem);
+    k_axis<T, -1, true><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, ilog2(W));
+  } else if (dir < 0) {
+    set_axis_attr<T, -1, false>(smem);
+    k_axis<T, -1, false><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, ilog2(W));
+  } else if (cv) {
+    set_axis_attr<T, +1, true>(smem);
+    k_axis<T, +1, true><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, ilog2(W));
   } else {
-    set_axis_attr<T, +1>(smem);
-    k_axis<T, +1><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, ilog2(W));
+    set_axis_attr<T, +1, false>(smem);
+    k_axis<T, +1, false><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, ilog2(W));
   }
 }
 
@@ -820,7 +829,9 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
   const long long nlines = (long long)g.n1 * g.n2;
   const long long blocks = (nlines + L - 1) / L;
   const size_t smem = sizeof(cpx<T>) * (size_t)(m + (m + 2) + 2 * L * (m + 1));
-  ensure_smem(reinterpret_cast<const void*>(k_xpass<T>), smem);
+  const bool cv = (P.conv_in | P.conv_out) != 0;
+  ensure_smem(cv ? reinterpret_cast<const void*>(k_xpass<T, true>) : reinterpret_cast<const void*>(k_xpass<T, false>),
+              smem);
   const double fc = (double)g.ncplx * sizeof(cpx<T>), fr = (double)g.nreal * sizeof(T);
   double bytes = 0, flops = 0;
   const double real_fft = (double)g.nreal * 2.5 * std::log2((double)g.n0);   // one real transform of every line
@@ -853,7 +864,8 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
       return;
     }
   }
-  k_xpass<T><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, reinterpret_cast<const cpx<T>*>(tw), ilog2(L));
+  if (cv) k_xpass<T, true><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, reinterpret_cast<const cpx<T>*>(tw), ilog2(L));
+  else k_xpass<T, false><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, reinterpret_cast<const cpx<T>*>(tw), ilog2(L));
 }
 
 template void launch_axis<dd>(const AxisProg&, int, const GridDesc&, const void*, cudaStream_t);
