@@ -74,6 +74,11 @@ def peaks():
 DTYPES = {"mixed_dd": "f32 inner / f64 refinement, residual transforms in float-pair (~2^-48) arithmetic",
           "mixed": "f32 inner / f64 refinement and residual", "fp64": "f64"}
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel class,
+# averaged over the launches of one inner iteration in an ncu capture of this workload
+# (profiles/sections_jet256_mixed_dd.md); reported only for the class it was taken for.
+MEASURED_TRAFFIC = {"axis_f32": 222.7e6}
+
 # FP64 arithmetic peak of the GB300 CUDA cores: 1.25 TFLOP/s nominal (recipe table: FP64 is
 # far below B200); counted with an FMA as two flops.
 FP64_PEAK_TFLOPS = 1.25
@@ -769,7 +774,7 @@ def main():
     if name.endswith("f32"):
         achieved = d["alg_bytes"] / (d["ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "frac": achieved / pk["hbm_gbs"], "traffic": MEASURED_TRAFFIC.get(name),
                 "peak_source": f"{pk_src} hbm_gbs (MEASURED_PEAKS.json)" if pk_src == "measured" else "fallback",
                 "alg_bytes_per_launch": d["alg_bytes"] / max(d["launches"], 1), "ms_per_launch": per_launch_ms}
     else:
