@@ -62,11 +62,48 @@ __device__ __forceinline__ dd& operator+=(dd& a, dd b) {
   return a;
 }
 
-// conversions to and from double (exact split / exact sum of the two parts)
-__device__ __forceinline__ dd dd_from_double(double v) {
-  const float h = __double2float_rn(v);
-  return dd(h, __double2float_rn(v - (double)h));
+// Conversions to and from double, on the integer pipes.  The FP64 pipe of GB300 runs at ~1/64
+// of the float rate, so the conversions are done on the IEEE bit patterns.
+//
+// float -> double, exact for normal floats, zero, inf and nan (subnormal floats flush to zero).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
+  unsigned long long out = s;   // zero and subnormal floats
+  if (e == 0xffu) out = s | (0x7ffull << 52) | m;
+  else if (e != 0u) out = s | ((unsigned long long)(e - 127u + 1023u) << 52) | m;
+  return __longlong_as_double((long long)out);
 }
-__device__ __forceinline__ double dd_to_double(dd a) { return (double)a.hi + (double)a.lo; }
+
+// double -> float pair: hi = the 53-bit significand rounded (half up) to 24 bits, lo = the
+// exact remainder (at most 29 bits) rounded to a float, so v = hi + lo to ~2^-48 |v| and
+// |lo| <= ulp(hi) / 2.  |v| >= 2^128 gives hi = +-inf, |v| < 2^-126 gives zero (subnormal
+// floats are not formed), inf and nan pass to hi; lo is dropped below 2^-149 |scale|.
+__device__ __forceinline__ dd dd_from_double(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const int E = (int)((b >> 52) & 0x7ffu);
+  if (E == 0x7ff) return dd(__uint_as_float(sgn | 0x7f800000u | (unsigned)((b >> 29) & 0x7fffffu)), 0.0f);
+  const unsigned long long sig = (1ull << 52) | (b & 0xfffffffffffffull);
+  const unsigned long long sig_r = ((sig >> 29) + ((sig >> 28) & 1ull)) << 29;
+  const long long diff = (long long)sig - (long long)sig_r;   // |diff| <= 2^28
+  const unsigned long long hr = sig_r >> 29;                 // 2^23 .. 2^24
+  const int carry = (hr >> 24) ? 1 : 0;
+  const int fe = E - 1023 + 127 + carry;
+  if (E == 0 || fe <= 0) return dd(__uint_as_float(sgn), 0.0f);
+  if (fe >= 255) return dd(__uint_as_float(sgn | 0x7f800000u), 0.0f);
+  const float hi = __uint_as_float(sgn | ((unsigned)fe << 23) | (carry ? 0u : (unsigned)(hr & 0x7fffffu)));
+  // lo = diff * 2^(E - 1075): the 2^k factor as float bits when it is a normal float
+  const int ke = E - 1075 + 127;
+  float lo = 0.0f;
+  if (ke >= 1 && ke <= 254) {
+    const float mag = (float)(int)diff * __uint_as_float((unsigned)ke << 23);   // |diff| < 2^31
+    lo = sgn ? -mag : mag;
+  }
+  return dd(hi, lo);
+}
+__device__ __forceinline__ double dd_to_double(dd a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 
 }  // namespace vd
