@@ -883,8 +883,7 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
         break;
       }
       if (total >= prm->max_it || outer >= max_outer) break;
-      spec_copy_scale<double>(len, L.rh, 1.0 / rnorm, L.rh, st);
-      spec_d2f(len, L.rh, L.bh_f, st);
+      spec_d2f_scaled(len, L.rh, 1.0 / rnorm, L.bh_f, st);
       VD_CUDA(cudaMemsetAsync(L.xh_f, 0, sizeof(cpx<float>) * len, st));
       SolveOpts si = so;
       // ask the inner solve for a little more than needed so that the refined residual lands
@@ -903,12 +902,10 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
       total += ri.iters;
       ++outer;
       // x += rnorm * d  (d promoted to double)
-      spec_f2d(len, L.xh_f, L.rh, st);
-      spec_axpy<double>(len, rnorm, L.rh, L.xh, st);
+      spec_axpy_f2d(len, rnorm, L.xh_f, L.xh, st);
       // true residual (double operator, or float-pair transforms in VD_PREC_MIXED_DD)
       resid_apply(L.xh, L.rh);
-      spec_sub<double>(len, L.bh, L.rh, L.rh, st);
-      rnorm = std::sqrt(spec_norm2_host<double>(sys64, L.rh, kw, st));
+      rnorm = std::sqrt(spec_sub_norm2_host(sys64, L.bh, L.rh, L.rh, kw, st));
       if (ri.status == VD_ERR_NONFINITE) {
         res.status = VD_ERR_NONFINITE;
         break;

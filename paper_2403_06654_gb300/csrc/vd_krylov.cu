@@ -463,6 +463,22 @@ __global__ void __launch_bounds__(kRedThreads) k_pdot(Ix ix, const cpx<T>* __res
   if (reduce_last<1>(v, ra.partials, ra.counter, t) && threadIdx.x == 0) epilogue<1>(EPI_NORM, t, ra.ks, ra.hist, ra.tol, 0, 0);
 }
 
+// r = b - q and |r|^2 (weighted) -> ks->rr, accumulated like k_norms
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_sub_norm(Ix ix, const cpx<T>* __restrict__ b,
+                                                          const cpx<T>* __restrict__ q, cpx<T>* __restrict__ r,
+                                                          RedArgs ra) {
+  Acc<T> a1;
+  IX_LOOP(ix) {
+    const cpx<T> rv = b[e] - q[e];
+    r[e] = rv;
+    a1.add(pweight<T>(kx, ix.h0) * (rv.x * rv.x + rv.y * rv.y));
+  }
+  double v[1] = {a1.total()};
+  double t[1];
+  if (reduce_last<1>(v, ra.partials, ra.counter, t) && threadIdx.x == 0) epilogue<1>(EPI_NORM, t, ra.ks, ra.hist, ra.tol, 0, 0);
+}
+
 // RMR: x += alpha S r, r -= alpha w; reduce [rr]
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_rmr_update(Ix ix, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r,
@@ -621,6 +637,26 @@ __global__ void k_d2f(long long len, const cpx<double>* __restrict__ in, cpx<flo
 __global__ void k_f2d(long long len, const cpx<float>* __restrict__ in, cpx<double>* __restrict__ out) {
   GRID_STRIDE(e, len) { out[e] = mk<double>((double)in[e].x, (double)in[e].y); }
 }
+// refinement steps fused over one pass of the double vectors (same arithmetic per element as
+// the separate kernels): out = float(in * s) and y += a * double(xf); s and a come from the
+// host, or from the refinement state (o->scale, o->rnorm) when o is set
+__global__ void k_d2f_scaled(long long len, const cpx<double>* __restrict__ in, double s, const OState* o,
+                             cpx<float>* __restrict__ out) {
+  if (o) s = o->scale;
+  GRID_STRIDE(e, len) {
+    const cpx<double> v = in[e];
+    out[e] = mk<float>((float)(v.x * s), (float)(v.y * s));
+  }
+}
+__global__ void k_axpy_f2d(long long len, double a, const OState* o, const cpx<float>* __restrict__ xf,
+                           cpx<double>* __restrict__ y) {
+  if (o) a = o->rnorm;
+  GRID_STRIDE(e, len) {
+    const cpx<float> v = xf[e];
+    const cpx<double> w = y[e];
+    y[e] = mk<double>(fma(a, (double)v.x, w.x), fma(a, (double)v.y, w.y));
+  }
+}
 template <typename T>
 __global__ void k_project(GridDesc g, int ncomp, cpx<T>* v) {
   const int t = threadIdx.x;   // one thread per corner mode and component
@@ -695,6 +731,26 @@ double spec_dot_host(const SpecSystem& sys, const void* a, const void* b, const 
   cudaMemcpyAsync(&rr, &kw.ks->rr, sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
   return rr;
+}
+
+double spec_sub_norm2_host(const SpecSystem& sys, const void* b, const void* q, void* r, const KWork& kw,
+                           cudaStream_t st) {
+  RedArgs ra{kw.ks, kw.partials, kw.counter, kw.hist, 0.0};
+  const int rb = red_blocks(sys.len);
+  const Ix ix = mkix(sys.len, sys.h0, sys.G->g.ncplx, rb, kRedThreads);
+  { ProfScope ps_(PC_VEC64, st, (double)3 * sys.len * sizeof(cpx<double>), 0.0); k_sub_norm<double><<<rb, kRedThreads, 0, st>>>(ix, (const cpx<double>*)b, (const cpx<double>*)q, (cpx<double>*)r, ra); }
+  double rr = 0.0;
+  cudaMemcpyAsync(&rr, &kw.ks->rr, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  return rr;
+}
+
+void spec_d2f_scaled(long long len, const void* in, double s, void* out, cudaStream_t st) {
+  { ProfScope ps_(PC_VEC64, st, (double)len * (sizeof(cpx<double>) + sizeof(cpx<float>)), 0.0); k_d2f_scaled<<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<double>*)in, s, nullptr, (cpx<float>*)out); }
+}
+
+void spec_axpy_f2d(long long len, double a, const void* xf, void* y, cudaStream_t st) {
+  { ProfScope ps_(PC_VEC64, st, (double)len * (sizeof(cpx<float>) + 2 * sizeof(cpx<double>)), 0.0); k_axpy_f2d<<<ew_blocks(len), 256, 0, st>>>(len, a, nullptr, (const cpx<float>*)xf, (cpx<double>*)y); }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1245,23 +1301,20 @@ vd_status refine_enqueue_graph(const SpecSystem& sys64, const SpecSystem& sys32,
   }
   VD_CUDA(cudaStreamBeginCaptureToGraph(s2, sweep_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   // the sweep: d solves A32 d = r/|r| in float, x += |r| d, r = b - A x, |r|^2
-  k_scale_out<<<eb, 256, 0, s2>>>(len, ost, RH);
+  k_d2f_scaled<<<eb, 256, 0, s2>>>(len, RH, 0.0, ost, (cpx<float>*)bh_f);
   count_launch();
-  spec_d2f(len, RH, bh_f, s2);
   VD_CUDA(cudaMemsetAsync(xh_f, 0, sizeof(cpx<float>) * len, s2));
   SolveOpts si = inner;
   si.x_zero = 1;
   si.dev_outer = ost;
   if ((e = krylov_enqueue_graph<float>(sys32, si, bh_f, xh_f, vecs, kw, s2, s3)) != VD_OK) return e;
   k_out_after_inner<<<1, 1, 0, s2>>>(ost, kw.ks);
-  spec_f2d(len, xh_f, RH, s2);
-  k_axpy_out<<<eb, 256, 0, s2>>>(len, ost, RH, XH);
+  k_axpy_f2d<<<eb, 256, 0, s2>>>(len, 0.0, ost, (const cpx<float>*)xh_f, XH);
   resid(resid_ctx, XH, RH, s2);
-  k_sub<double><<<eb, 256, 0, s2>>>(len, BH, RH, RH, nullptr);
   VD_CUDA(cudaMemsetAsync(kw.counter, 0, sizeof(unsigned), s2));
-  k_norms<double, 1><<<rb, kRedThreads, 0, s2>>>(ixr, nullptr, RH, EPI_NORM, ra, nullptr);
+  k_sub_norm<double><<<rb, kRedThreads, 0, s2>>>(ixr, BH, RH, RH, ra);
   k_out_rr<<<1, 1, 0, s2>>>(ost, kw.ks);
-  for (int i = 0; i < 5; ++i) count_launch();
+  for (int i = 0; i < 4; ++i) count_launch();
   cudaGraph_t tmp = nullptr;
   VD_CUDA(cudaStreamEndCapture(s2, &tmp));
   VD_CUDA(cudaStreamEndCapture(s1, &tmp));
