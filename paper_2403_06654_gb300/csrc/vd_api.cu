@@ -146,6 +146,7 @@ vd_status vd_grid_create(int ndim, const int n[3], const double L[3], vd_grid** 
     g.kfac[j] = 2.0 * 3.14159265358979323846 / G->L[j];
     const long double kl = 2.0L * 3.14159265358979323846264338327950288L / (long double)G->L[j];
     split_ld(kl, &g.kfac_dd[j][0], &g.kfac_dd[j][1]);
+    g.kfac_f[j] = (float)g.kfac[j];
   }
   bool ok = make_plan(nn[0] / 2, &g.px);
   if (ndim >= 2) ok = ok && make_plan(nn[1], &g.py);

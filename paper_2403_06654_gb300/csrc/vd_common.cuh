@@ -84,6 +84,7 @@ struct GridDesc {
   long long ncplx;   // h0 n1 n2
   double kfac[3];    // 2 pi / L_j
   float kfac_dd[3][2];   // float-pair split of kfac (hi, lo)
+  float kfac_f[3];       // kfac rounded to float (float kernels: no double -> float conversion on the device)
   FftPlan px;        // length n0/2
   FftPlan py;        // length n1 (ndim >= 2)
   FftPlan pz;        // length n2 (ndim == 3)

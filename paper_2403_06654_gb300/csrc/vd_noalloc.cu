@@ -130,6 +130,7 @@ extern "C" vd_status vd_apply_pressure_noalloc(int ndim, const int n[3], const d
     g.kfac[j] = 2.0 * 3.14159265358979323846 / G.L[j];
     g.kfac_dd[j][0] = (float)g.kfac[j];
     g.kfac_dd[j][1] = (float)(g.kfac[j] - (double)g.kfac_dd[j][0]);
+    g.kfac_f[j] = (float)g.kfac[j];
   }
   bool ok = na_plan(nn[0] / 2, &g.px);
   int off = 0;

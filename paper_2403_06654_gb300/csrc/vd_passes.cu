@@ -47,16 +47,20 @@ __device__ __forceinline__ void st_el(void* p, int conv, int go, cpx<T> v, bool 
   *q = first ? v : (*q + v);
 }
 
-// kfac[axis] and a scale factor in the arithmetic type (float-pair values come pre-split)
+// kfac[axis] and a scale factor in the arithmetic type.  Float-pair and float values come
+// converted from the host (hi = the double rounded to float), so float kernels issue no
+// double -> float conversions: those run on the FP64 pipe, ~1/64 of the float rate on GB300.
 template <typename T>
 __device__ __forceinline__ T kfac_t(const GridDesc& g, int a) {
   if constexpr (std::is_same<T, dd>::value) return dd(g.kfac_dd[a][0], g.kfac_dd[a][1]);
-  else return (T)g.kfac[a];
+  else if constexpr (std::is_same<T, float>::value) return g.kfac_f[a];
+  else return g.kfac[a];
 }
 template <typename T>
 __device__ __forceinline__ T scale_t(double s, float hi, float lo) {
   if constexpr (std::is_same<T, dd>::value) return dd(hi, lo);
-  else return (T)s;
+  else if constexpr (std::is_same<T, float>::value) return hi;
+  else return s;
 }
 
 constexpr int kThreads = 256;
@@ -220,6 +224,7 @@ constexpr int kRLines = 16;
 template <typename T, int S, int N1, int N2>
 __global__ void __launch_bounds__(kRLines * N2, (sizeof(T) == 4 ? 2 : 1)) k_axis_r(const AxisProg P, const GridDesc g,
                                                         const cpx<T>* __restrict__ twg) {
+  static_assert(std::is_same<T, float>::value, "register four-step pass: float storage only");
   constexpr int N = N1 * N2;
   constexpr int C = N1 / N2;
   constexpr int LS = N + 1;
@@ -327,6 +332,15 @@ __global__ void __launch_bounds__(kRLines * N2, (sizeof(T) == 4 ? 2 : 1)) k_axis
       for (int n2 = 0; n2 < N2; ++n2) v[n2] = Yl[n2 * N1 + k1];
       dftR<T, S, N2>(v);
       if (colok) {
+        // a transform that accumulates reads all of its partial sums before its first store,
+        // so their latencies overlap (the compiler cannot move a load of dst above a store to
+        // dst); the partials were written by this thread, so the order is unchanged
+        cpx<T>* q = reinterpret_cast<cpx<T>*>(dst);
+        cpx<T> prev[N2];
+        if (!xf.first) {
+#pragma unroll
+          for (int k2 = 0; k2 < N2; ++k2) prev[k2] = q[gbase + (k1 + N1 * k2) * line_stride];
+        }
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
           const int i = k1 + N1 * k2;
@@ -338,7 +352,7 @@ __global__ void __launch_bounds__(kRLines * N2, (sizeof(T) == 4 ? 2 : 1)) k_axis
           } else {
             vv = scal(vv, scale);
           }
-          st_el<T>(dst, cout, go, vv, xf.first);
+          q[go] = xf.first ? vv : (prev[k2] + vv);
         }
       }
     }
@@ -763,6 +777,7 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
   for (int t = 0; t < P.nxf; ++t) split_scale(P.xf[t].scale, &P.xf[t].scale_hi, &P.xf[t].scale_lo);
   const int n = (P.axis == 2) ? g.pz.n : g.py.n;
   const int choice = tune_get(0, type_code<T>(), n, P.axis, dir);
+  const bool reg_ok = std::is_same<T, float>::value && (n == 256 || n == 128);
   const int W = choice > 0 ? choice : tile_width(n, kEPT<T>);
   long long inner_n, outer_n;
   if (P.axis == 2) {
@@ -792,7 +807,7 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
                flops);
   if constexpr (std::is_same<T, float>::value) {
     // register-resident four-step kernel for the common lengths (unless tuned otherwise)
-    if ((n == 256 || n == 128) && choice <= 0) {
+    if (reg_ok && choice <= 0) {
       if (n == 256) {
         if (dir < 0) launch_axis_r<T, -1, 16, 16>(P, g, twp, inner_n, outer_n, st);
         else launch_axis_r<T, +1, 16, 16>(P, g, twp, inner_n, outer_n, st);
