@@ -14,6 +14,8 @@
 
 #include <cuda_runtime.h>
 
+#include "vd_common.cuh"
+
 namespace vd {
 
 struct dd {
@@ -60,6 +62,47 @@ __device__ __forceinline__ dd& operator*=(dd& a, dd b) {
 __device__ __forceinline__ dd& operator+=(dd& a, dd b) {
   a = a + b;
   return a;
+}
+
+// a b + c d with one renormalisation: both products are formed as (p, e) with p = fl(hi hi)
+// and e its FMA error plus the cross terms, the high parts are summed exactly (two_sum) and
+// the error terms in float.  19 float operations against 25 for two products and a sum;
+// absolute error ~2^-47 (|a b| + |c d|), the normwise bound a transform needs.
+__device__ __forceinline__ dd dd_sum_prod(dd a, dd b, dd c, dd d) {
+  const float p = a.hi * b.hi;
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float q = c.hi * d.hi;
+  float f = __fmaf_rn(c.hi, d.hi, -q);
+  f = __fmaf_rn(c.hi, d.lo, f);
+  f = __fmaf_rn(c.lo, d.hi, f);
+  const dd s = dd_two_sum(p, q);
+  return dd_fast_two_sum(s.hi, s.lo + (e + f));
+}
+
+// complex products on float pairs (preferred over the generic templates by overload
+// resolution): a w and a conj(w)
+__device__ __forceinline__ cpx<dd> cmul(cpx<dd> a, cpx<dd> w) {
+  return mk<dd>(dd_sum_prod(a.x, w.x, -a.y, w.y), dd_sum_prod(a.x, w.y, a.y, w.x));
+}
+__device__ __forceinline__ cpx<dd> cmulc(cpx<dd> a, cpx<dd> w) {
+  return mk<dd>(dd_sum_prod(a.x, w.x, a.y, w.y), dd_sum_prod(a.y, w.x, -a.x, w.y));
+}
+
+// a + b without the final renormalisation: exact sum of the high parts, low parts added in
+// float, so |lo| may reach a few ulp(hi).  Only for values that go straight into normalising
+// additions (the first layer of a radix-4 butterfly); the pair still carries ~2^-47 relative
+// accuracy.
+__device__ __forceinline__ dd dd_add_lazy(dd a, dd b) {
+  const dd s = dd_two_sum(a.hi, b.hi);
+  return dd(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ cpx<dd> cadd_lazy(cpx<dd> a, cpx<dd> b) {
+  return mk<dd>(dd_add_lazy(a.x, b.x), dd_add_lazy(a.y, b.y));
+}
+__device__ __forceinline__ cpx<dd> csub_lazy(cpx<dd> a, cpx<dd> b) {
+  return mk<dd>(dd_add_lazy(a.x, -b.x), dd_add_lazy(a.y, -b.y));
 }
 
 // Conversions to and from double, on the integer pipes.  The FP64 pipe of GB300 runs at ~1/64

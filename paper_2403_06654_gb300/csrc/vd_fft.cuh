@@ -16,6 +16,9 @@
 #pragma once
 
 #include "vd_common.cuh"
+#include "vd_dd.cuh"
+
+#include <type_traits>
 
 namespace vd {
 
@@ -38,8 +41,19 @@ __device__ __forceinline__ void dft2(cpx<T>& a, cpx<T>& b) {
 
 template <typename T, int S>
 __device__ __forceinline__ void dft4(cpx<T>* u) {
-  cpx<T> a = u[0] + u[2], b = u[0] - u[2];
-  cpx<T> c = u[1] + u[3], d = mul_si<T, S>(u[1] - u[3]);
+  cpx<T> a, b, c, d;
+  if constexpr (std::is_same<T, dd>::value) {
+    // first layer unnormalised: its sums only feed the normalising sums below
+    a = cadd_lazy(u[0], u[2]);
+    b = csub_lazy(u[0], u[2]);
+    c = cadd_lazy(u[1], u[3]);
+    d = mul_si<T, S>(csub_lazy(u[1], u[3]));
+  } else {
+    a = u[0] + u[2];
+    b = u[0] - u[2];
+    c = u[1] + u[3];
+    d = mul_si<T, S>(u[1] - u[3]);
+  }
   u[0] = a + c;
   u[2] = a - c;
   u[1] = b + d;
