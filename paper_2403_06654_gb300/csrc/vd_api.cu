@@ -838,6 +838,7 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
   // the device history buffer holds max_it + 2 entries
   const int hcap = hh ? std::min(info->hist_cap, prm->max_it + 2) : 0;
   SpecSystem sys64 = make_system<double>(G, op, opp, L.sym, L.tmp);
+  bool x_phys_current = false;   // x already holds the inverse transform of the final L.xh
   int outer = 0;
   double relres_true = 0.0;
   if (prm->precision == VD_PREC_FP64) {
@@ -849,15 +850,26 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
     SpecSystem sys32 = make_system<float>(G, op, opp, L.sym_f, L.tmp_f);
     // residual operator of the refinement: double, or float-pair transforms (pressure)
     const bool use_dd = prm->precision == VD_PREC_MIXED_DD && op != VD_OP_VELOCITY;
-    auto resid_apply = [&](const cpx<double>* xin, cpx<double>* yout) {
-      if (use_dd && op == VD_OP_KRHO) apply_krho_spec_dd(G, xin, yout, L.tmp, nullptr, st);
-      else if (use_dd) apply_pressure_spec_dd(G, xin, yout, L.tmp, nullptr, st);
-      else sys64.apply(sys64, xin, yout, false, nullptr, st);
+    // With want_phys the float-pair pressure residual also writes the physical-space iterate
+    // into x (its fused x pass carries the inverse transform of the iterate); when the loop
+    // ends right after such a residual the final inverse transform is skipped.  It is asked
+    // for on a sweep expected to be the last: the outer residual it aims at (rel times the
+    // inner tolerance) within a factor 10 of tol.  A wrong guess either way costs time only.
+    auto resid_apply = [&](const cpx<double>* xin, cpx<double>* yout, bool want_phys) {
+      if (use_dd && op == VD_OP_KRHO) {
+        apply_krho_spec_dd(G, xin, yout, L.tmp, nullptr, st);
+        x_phys_current = false;
+      } else if (use_dd) {
+        apply_pressure_spec_dd(G, xin, yout, L.tmp, nullptr, st, want_phys ? x : nullptr);
+        x_phys_current = want_phys;
+      } else {
+        sys64.apply(sys64, xin, yout, false, nullptr, st);
+      }
     };
     const double bb = spec_norm2_host<double>(sys64, L.bh, kw, st);
     const double bnorm = std::sqrt(bb);
     if (prm->use_x0) {
-      resid_apply(L.xh, L.rh);
+      resid_apply(L.xh, L.rh, false);
       spec_sub<double>(len, L.bh, L.rh, L.rh, st);
     } else {
       VD_CUDA(cudaMemcpyAsync(L.rh, L.bh, sizeof(cpx<double>) * len, cudaMemcpyDeviceToDevice, st));
@@ -905,7 +917,7 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
       // x += rnorm * d  (d promoted to double)
       spec_axpy_f2d(len, rnorm, L.xh_f, L.xh, st);
       // true residual (double operator, or float-pair transforms in VD_PREC_MIXED_DD)
-      resid_apply(L.xh, L.rh);
+      resid_apply(L.xh, L.rh, rel * si.tol <= 10.0 * prm->tol);
       rnorm = std::sqrt(spec_sub_norm2_host(sys64, L.bh, L.rh, L.rh, kw, st));
       if (ri.status == VD_ERR_NONFINITE) {
         res.status = VD_ERR_NONFINITE;
@@ -918,8 +930,8 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
     if (info) info->hist_len = hlen;
   }
   // back to physical space
-  if (dd_io) inv_transform_dd(G, L.xh, x, L.tmp, st);
-  else inv_all(G, ncomp, L.xh, x, L.tmp, st);
+  if (dd_io && !x_phys_current) inv_transform_dd(G, L.xh, x, L.tmp, st);
+  else if (!dd_io) inv_all(G, ncomp, L.xh, x, L.tmp, st);
   if (prm->precision == VD_PREC_FP64) {
     // true residual of the returned iterate
     const double bb = spec_norm2_host<double>(sys64, L.bh, kw, st);

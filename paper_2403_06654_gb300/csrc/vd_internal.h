@@ -90,8 +90,10 @@ void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const 
 
 // Pressure operator with float-pair transforms: double spectral fields in and out (no
 // preconditioner), float-pair intermediates in tmp (3 spectral fields of 16 bytes per element).
+// phys_out (may be null): also the inverse transform of `in` (real, n2 x n1 x n0 doubles),
+// written by the fused x pass and equal bit for bit to inv_transform_dd of `in`
 void apply_pressure_spec_dd(const vd_grid* G, const cpx<double>* in, cpx<double>* out, void* tmp, const int* done,
-                            cudaStream_t st);
+                            cudaStream_t st, double* phys_out = nullptr);
 
 // Plain forward / inverse transforms with float-pair arithmetic (double fields in and out;
 // tmp: one spectral field of 16-byte elements).

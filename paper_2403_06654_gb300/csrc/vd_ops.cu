@@ -195,11 +195,14 @@ void inv_transform_dd(const vd_grid* G, const cpx<double>* in, double* out, void
 // ---------------------------------------------------------------------------------------
 
 // conv: the float-pair instantiation reads `in` and writes `out` as double fields
+// phys_out (may be null): the fused x pass also writes the inverse transform of `in` there,
+// equal bit for bit to the separate inverse transform when the apply is unpreconditioned
 template <typename T>
 static void pressure_impl(const vd_grid* G, const void* in, void* out, const T* symarr, const void* rinv_s,
-                          cpx<T>* tmp, const int* done, cudaStream_t st, int conv) {
+                          cpx<T>* tmp, const int* done, cudaStream_t st, int conv, void* phys_out = nullptr) {
   const GridDesc& g = G->g;
   const int S = symarr ? MUL_SYM : 0;
+  if (symarr) phys_out = nullptr;   // the by-product is the inverse of `in` itself: unpreconditioned applies only
   const size_t nc = (size_t)g.ncplx;
   const void* tw = twtab<T>(G);
   if (g.ndim == 1) {
@@ -211,6 +214,9 @@ static void pressure_impl(const vd_grid* G, const void* in, void* out, const T* 
     X.pre[0] = S | MUL_IK;
     X.post[0] = MUL_IK;
     X.wfield = rinv_s;
+    X.aux_out = phys_out;
+    X.aux_scale = 1.0 / (double)g.nreal;
+    X.aux_conv = conv;
     X.scale = 0.5;
     X.symarr = symarr;
     X.done = done;
@@ -246,6 +252,9 @@ static void pressure_impl(const vd_grid* G, const void* in, void* out, const T* 
     X.in[1] = T1;
     X.out[1] = T1;
     X.wfield = rinv_s;
+    X.aux_out = phys_out;
+    X.aux_scale = 1.0 / (double)g.nreal;
+    X.aux_conv = conv;
     X.scale = 0.5;
     X.done = done;
     launch_xpass<T>(X, g, tw, st);
@@ -309,6 +318,9 @@ static void pressure_impl(const vd_grid* G, const void* in, void* out, const T* 
     X.in[2] = T1;
     X.out[2] = T1;
     X.wfield = rinv_s;
+    X.aux_out = phys_out;
+    X.aux_scale = 1.0 / (double)g.nreal;
+    X.aux_conv = conv;
     X.scale = 0.5;
     X.done = done;
     launch_xpass<T>(X, g, tw, st);
@@ -352,8 +364,8 @@ void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const 
 }
 
 void apply_pressure_spec_dd(const vd_grid* G, const cpx<double>* in, cpx<double>* out, void* tmp, const int* done,
-                            cudaStream_t st) {
-  pressure_impl<dd>(G, in, out, nullptr, G->rinv_s_dd, reinterpret_cast<cpx<dd>*>(tmp), done, st, 1);
+                            cudaStream_t st, double* phys_out) {
+  pressure_impl<dd>(G, in, out, nullptr, G->rinv_s_dd, reinterpret_cast<cpx<dd>*>(tmp), done, st, 1, phys_out);
 }
 
 // ---------------------------------------------------------------------------------------

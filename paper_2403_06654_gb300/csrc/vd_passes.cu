@@ -394,22 +394,26 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 4 : 1)
   const T scale = scale_t<T>(P.scale, P.scale_hi, P.scale_lo);
   const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr) + (line0 + line) * h0;
 
-  for (int c = 0; c < P.ncomp; ++c) {
+  // c = -1: the inverse-only transform of component 0 into aux_out (mode 0 programs only)
+  for (int c = P.aux_out ? -1 : 0; c < P.ncomp; ++c) {
+    const bool aux = c < 0;
+    const int ci = aux ? 0 : c;
+    const int mode = aux ? 2 : P.mode;
     cpx<T>* res;
     __syncthreads();
-    if (P.mode == 1) {
+    if (mode == 1) {
       const int cin = (P.conv_in >> c) & 1;
       const int rbase = (int)((line0 + line) * m);
       if (lok)
         for (int j = t0; j < m; j += TPL) A[lofs + j] = ld_el<T, CV>(P.in[c], cin, rbase + j);
       res = fft_lines<T, -1>(A, B, 1, lofs, t0, TPL, g.px, twm);
     } else {
-      const int cin = (P.conv_in >> c) & 1;
+      const int cin = (P.conv_in >> ci) & 1;
       const int lbase = (int)((line0 + line) * h0);
-      const int pre = P.pre[c];
+      const int pre = aux ? 0 : P.pre[ci];
       if (lok) {
         for (int k = t0; k < h0; k += TPL) {
-          cpx<T> v = ld_el<T, CV>(P.in[c], cin, lbase + k);
+          cpx<T> v = ld_el<T, CV>(P.in[ci], cin, lbase + k);
           if (pre) {
             const T kx = kfx * (T)freq_tilde(k, g.n0);
             T cc = T(1);
@@ -432,11 +436,13 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 4 : 1)
         }
       }
       res = fft_lines<T, +1>(A, B, 1, lofs, t0, TPL, g.px, twm);
-      if (P.mode == 2) {
-        const int cout = (P.conv_out >> c) & 1;
+      if (mode == 2) {
+        void* o = aux ? P.aux_out : P.out[c];
+        const int cout = aux ? P.aux_conv : ((P.conv_out >> c) & 1);
+        const T sc = aux ? scale_t<T>(P.aux_scale, P.aux_scale_hi, P.aux_scale_lo) : scale;
         const int rbase = (int)((line0 + line) * m);
         if (lok)
-          for (int j = t0; j < m; j += TPL) st_el<T, CV>(P.out[c], cout, rbase + j, scal(res[lofs + j], scale), true);
+          for (int j = t0; j < m; j += TPL) st_el<T, CV>(o, cout, rbase + j, scal(res[lofs + j], sc), true);
         continue;
       }
       if (P.wfield && lok) {
@@ -836,15 +842,34 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
 
 template <typename T>
 void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream_t st) {
+  if (P0.aux_out && (P0.mode != 0 || !std::is_same<T, dd>::value)) {
+    // the extra inverse output is fused into the float-pair engine only: elsewhere it is a
+    // separate mode-2 pass over in[0], run before the program (which may work in place)
+    XProg A{};
+    A.ncomp = 1;
+    A.mode = 2;
+    A.in[0] = P0.in[0];
+    A.conv_in = P0.conv_in & 1;
+    A.out[0] = P0.aux_out;
+    A.conv_out = P0.aux_conv;
+    A.scale = P0.aux_scale;
+    A.done = P0.done;
+    launch_xpass<T>(A, g, tw, st);
+    XProg B = P0;
+    B.aux_out = nullptr;
+    launch_xpass<T>(B, g, tw, st);
+    return;
+  }
   XProg P = P0;
   split_scale(P.scale, &P.scale_hi, &P.scale_lo);
+  split_scale(P.aux_scale, &P.aux_scale_hi, &P.aux_scale_lo);
   const int m = g.n0 / 2;
   const int choice = tune_get(1, type_code<T>(), m, 0, P.mode);
   const int L = choice > 0 ? choice : lines_per_cta(m, kEPT<T>);
   const long long nlines = (long long)g.n1 * g.n2;
   const long long blocks = (nlines + L - 1) / L;
   const size_t smem = sizeof(cpx<T>) * (size_t)(m + (m + 2) + 2 * L * (m + 1));
-  const bool cv = (P.conv_in | P.conv_out) != 0;
+  const bool cv = (P.conv_in | P.conv_out | (P.aux_out ? P.aux_conv : 0)) != 0;
   ensure_smem(cv ? reinterpret_cast<const void*>(k_xpass<T, true>) : reinterpret_cast<const void*>(k_xpass<T, false>),
               smem);
   const double fc = (double)g.ncplx * sizeof(cpx<T>), fr = (double)g.nreal * sizeof(T);
@@ -856,6 +881,10 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
   } else {
     bytes = P.ncomp * (fc + fr);
     flops = P.ncomp * real_fft;
+  }
+  if (P.aux_out) {   // the inverse-only transform of in[0] and its real output
+    bytes += fr;
+    flops += real_fft;
   }
   bool sym = false;
   for (int c = 0; c < P.ncomp; ++c) sym = sym || ((P.pre[c] | P.post[c]) & MUL_SYM);

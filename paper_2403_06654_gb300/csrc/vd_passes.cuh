@@ -70,6 +70,13 @@ struct XProg {
   const int* done;
   int conv_in;          // float-pair kernels: bit c set -> in[c] holds doubles
   int conv_out;         // float-pair kernels: bit c set -> out[c] holds doubles
+  // mode 0 only: if aux_out is set, component 0 is also transformed inverse-only (no pre
+  // multiplier, as mode 2) into the real field aux_out, scaled by aux_scale (doubles when
+  // aux_conv is set); that output equals a separate mode-2 pass over in[0] bit for bit
+  void* aux_out;
+  double aux_scale;
+  float aux_scale_hi, aux_scale_lo;
+  int aux_conv;
 };
 
 template <typename T>

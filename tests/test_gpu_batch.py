@@ -66,9 +66,11 @@ def test_batch_matches_single_solves(vel_solver, pres_solver, precision):
             assert iv["iters"] == sv_["iters"] and ip["iters"] == sp_["iters"], (i, iv, sv_, ip, sp_)
             assert iv["outer_iters"] == sv_["outer_iters"] and ip["outer_iters"] == sp_["outer_iters"]
             assert iv["relres_true"] <= 1e-10 * 1.01 and ip["relres_true"] <= 1e-10 * 1.01
-            for got, ref in ((items[i]["x_vel"], xv), (items[i]["x_pres"], xp)):
-                err = float((got - ref).abs().max() / ref.abs().max())
-                assert err <= 1e-13, (i, err)
+            err = float((items[i]["x_vel"] - xv).abs().max() / xv.abs().max())
+            assert err <= 1e-13, (i, err)
+            # pressure: the same kernels in the same order, bit for bit (vd_solve's float-pair
+            # residual also carries the final inverse transform; the graph runs it separately)
+            assert torch.equal(items[i]["x_pres"], xp), (i, float((items[i]["x_pres"] - xp).abs().max()))
     finally:
         B.close()
 
