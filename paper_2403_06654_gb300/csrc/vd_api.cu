@@ -868,13 +868,14 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
     };
     const double bb = spec_norm2_host<double>(sys64, L.bh, kw, st);
     const double bnorm = std::sqrt(bb);
+    // r = b - A x0; with x0 = 0 the first sweep reads b itself and |r| = |b|
+    const cpx<double>* r_cur = L.bh;
+    double rnorm = bnorm;
     if (prm->use_x0) {
       resid_apply(L.xh, L.rh, false);
-      spec_sub<double>(len, L.bh, L.rh, L.rh, st);
-    } else {
-      VD_CUDA(cudaMemcpyAsync(L.rh, L.bh, sizeof(cpx<double>) * len, cudaMemcpyDeviceToDevice, st));
+      rnorm = std::sqrt(spec_sub_norm2_host(sys64, L.bh, L.rh, L.rh, kw, st));
+      r_cur = L.rh;
     }
-    double rnorm = std::sqrt(spec_norm2_host<double>(sys64, L.rh, kw, st));
     int total = 0;
     int hlen = 0;
     if (hh && hcap > 0) hh[hlen++] = bnorm > 0 ? rnorm / bnorm : 0.0;
@@ -896,7 +897,7 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
         break;
       }
       if (total >= prm->max_it || outer >= max_outer) break;
-      spec_d2f_scaled(len, L.rh, 1.0 / rnorm, L.bh_f, st);
+      spec_d2f_scaled(len, r_cur, 1.0 / rnorm, L.bh_f, st);
       VD_CUDA(cudaMemsetAsync(L.xh_f, 0, sizeof(cpx<float>) * len, st));
       SolveOpts si = so;
       // ask the inner solve for a little more than needed so that the refined residual lands
@@ -919,6 +920,7 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
       // true residual (double operator, or float-pair transforms in VD_PREC_MIXED_DD)
       resid_apply(L.xh, L.rh, rel * si.tol <= 10.0 * prm->tol);
       rnorm = std::sqrt(spec_sub_norm2_host(sys64, L.bh, L.rh, L.rh, kw, st));
+      r_cur = L.rh;
       if (ri.status == VD_ERR_NONFINITE) {
         res.status = VD_ERR_NONFINITE;
         break;
