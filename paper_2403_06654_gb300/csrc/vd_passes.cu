@@ -404,14 +404,17 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 4 : 1)
     if (mode == 1) {
       const int cin = (P.conv_in >> c) & 1;
       const int rbase = (int)((line0 + line) * m);
-      if (lok)
+      if (lok) {
+#pragma unroll 4
         for (int j = t0; j < m; j += TPL) A[lofs + j] = ld_el<T, CV>(P.in[c], cin, rbase + j);
+      }
       res = fft_lines<T, -1>(A, B, 1, lofs, t0, TPL, g.px, twm);
     } else {
       const int cin = (P.conv_in >> ci) & 1;
       const int lbase = (int)((line0 + line) * h0);
       const int pre = aux ? 0 : P.pre[ci];
       if (lok) {
+#pragma unroll 4
         for (int k = t0; k < h0; k += TPL) {
           cpx<T> v = ld_el<T, CV>(P.in[ci], cin, lbase + k);
           if (pre) {
@@ -447,6 +450,7 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 4 : 1)
       }
       if (P.wfield && lok) {
         const cpx<T>* __restrict__ wf = reinterpret_cast<const cpx<T>*>(P.wfield) + (line0 + line) * m;
+#pragma unroll 4
         for (int j = t0; j < m; j += TPL) {
           const cpx<T> z = res[lofs + j];
           const cpx<T> wv = wf[j];
@@ -572,9 +576,18 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_xpass_r(const
 #pragma unroll
       for (int q = 0; q < M1; ++q) u[q] = lok ? ld_el<T>(P.in[c], cin, rb + M2 * q + t) : mk<T>(T(0), T(0));
     } else {
-      // stage the half spectrum, then pack it into the length-m complex spectrum
-      if (lok)
-        for (int k = t; k < h0; k += M2) Yl[k] = premul(P.pre[c], k, ld_el<T>(P.in[c], cin, lb + k));
+      // stage the half spectrum (h0 = M + 1 entries: k = t + M2 q, and k = M for thread 0),
+      // all loads of the thread issued before the first store, then pack it into the
+      // length-m complex spectrum
+      if (lok) {
+        cpx<T> hv[M1];
+#pragma unroll
+        for (int q = 0; q < M1; ++q) hv[q] = ld_el<T>(P.in[c], cin, lb + t + M2 * q);
+        const cpx<T> hn = (t == 0) ? ld_el<T>(P.in[c], cin, lb + M) : mk<T>(T(0), T(0));
+#pragma unroll
+        for (int q = 0; q < M1; ++q) Yl[t + M2 * q] = premul(P.pre[c], t + M2 * q, hv[q]);
+        if (t == 0) Yl[M] = premul(P.pre[c], M, hn);
+      }
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < M1; ++q) {
@@ -608,7 +621,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_xpass_r(const
     __syncthreads();
     if (lok) {
       const int post = P.post[c];
-      for (int k = t; k < h0; k += M2) {
+      // entries k = t + M2 q (q < M1) and, for thread 0, k = M: a fixed count, unrolled
+      auto unpack = [&](int k) {
         const cpx<T> Z = Yl[k == M ? 0 : k];
         const cpx<T> Zc = conjg(Yl[k == 0 ? 0 : M - k]);
         cpx<T> Xv = (Z + Zc) - mul_i(cmul(Z - Zc, pk[k]));
@@ -622,7 +636,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_xpass_r(const
         Xv = scal(Xv, cc);
         if (post & MUL_IK) Xv = mul_i(Xv);
         st_el<T>(P.out[c], cout, lb + k, Xv, true);
-      }
+      };
+#pragma unroll
+      for (int q = 0; q < M1; ++q) unpack(t + M2 * q);
+      if (t == 0) unpack(M);
     }
   }
 }
