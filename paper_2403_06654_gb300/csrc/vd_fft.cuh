@@ -39,7 +39,9 @@ __device__ __forceinline__ void dft2(cpx<T>& a, cpx<T>& b) {
   b = t;
 }
 
-template <typename T, int S>
+// LAZY_OUT (float pairs only): the outputs are left unnormalised too, for a caller whose next
+// operations on them normalise (the final layer of dft8)
+template <typename T, int S, bool LAZY_OUT = false>
 __device__ __forceinline__ void dft4(cpx<T>* u) {
   cpx<T> a, b, c, d;
   if constexpr (std::is_same<T, dd>::value) {
@@ -48,6 +50,13 @@ __device__ __forceinline__ void dft4(cpx<T>* u) {
     b = csub_lazy(u[0], u[2]);
     c = cadd_lazy(u[1], u[3]);
     d = mul_si<T, S>(csub_lazy(u[1], u[3]));
+    if constexpr (LAZY_OUT) {
+      u[0] = cadd_lazy(a, c);
+      u[2] = csub_lazy(a, c);
+      u[1] = cadd_lazy(b, d);
+      u[3] = csub_lazy(b, d);
+      return;
+    }
   } else {
     a = u[0] + u[2];
     b = u[0] - u[2];
@@ -96,14 +105,22 @@ __device__ __forceinline__ void dft8(cpx<T>* u) {
   const T r2 = T(0.70710678118654752440084436210485);  // 1/sqrt(2)
   cpx<T> e[4] = {u[0], u[2], u[4], u[6]};
   cpx<T> o[4] = {u[1], u[3], u[5], u[7]};
-  dft4<T, S>(e);
-  dft4<T, S>(o);
+  // float pairs: the half-size transforms and the twiddle sums stay unnormalised (two lazy
+  // layers, |lo| of a few ulp(hi)); the final layer and the products normalise
+  constexpr bool lazy = std::is_same<T, dd>::value;
+  dft4<T, S, lazy>(e);
+  dft4<T, S, lazy>(o);
   // o_k *= W8^k, W8 = exp(S 2 pi i / 8)
   cpx<T> o1 = o[1], o3 = o[3];
   // W8^1 = (1 + S i)/sqrt 2 ; W8^2 = S i ; W8^3 = (-1 + S i)/sqrt 2
-  o[1] = scal(o1 + mul_si<T, S>(o1), r2);
+  if constexpr (lazy) {
+    o[1] = scal(cadd_lazy(o1, mul_si<T, S>(o1)), r2);
+    o[3] = scal(csub_lazy(mul_si<T, S>(o3), o3), r2);
+  } else {
+    o[1] = scal(o1 + mul_si<T, S>(o1), r2);
+    o[3] = scal(mul_si<T, S>(o3) - o3, r2);
+  }
   o[2] = mul_si<T, S>(o[2]);
-  o[3] = scal(mul_si<T, S>(o3) - o3, r2);
   u[0] = e[0] + o[0];
   u[4] = e[0] - o[0];
   u[1] = e[1] + o[1];

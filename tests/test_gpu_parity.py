@@ -272,3 +272,32 @@ def test_mixed_dd_residual_matches_fp64(solver, n, L):
     A, M = op.pressure_system(rho, g)
     ref = sv.solve(solver, A, M, fb, tol=1e-12, maxit=500)
     assert rel2(N(x), ref.x) < 2.5 * tol
+
+
+@pytest.mark.parametrize("n,L", [((48, 40, 32), (2 * math.pi,) * 3), ((256,), (2 * math.pi,)), ((512,), (2 * math.pi,)),
+                                 ((64, 48), (2 * math.pi, 1.0)), ((256, 16, 16), (2 * math.pi,) * 3),
+                                 ((30, 20, 50), (2 * math.pi, 1.0, 3.0)), ((256, 256), (2 * math.pi,) * 2)])
+def test_float_pair_residual_accuracy(n, L):
+    """The float-pair residual b - A x alone: a warm-started mixed_dd solve with max_it = 0
+    evaluates it once at x0 (a converged FP64 solution: the residual is 1e-13..1e-11 |b|, so
+    the cancellation is maximal) and reports its norm; the same residual through the double
+    operator must agree to the normwise float-pair bound 2^-47 |A| |x0| / |b| with
+    |A| = |k|_max^2 max(1/rho).  Measured discrepancies are 0.02-0.3 of that bound; it is
+    largest on long 1D lines across a sharp interface (5e-11 of |b| at n = 256, 2.6e-10 at
+    512), which is the accuracy floor of the float-pair refinement residual there."""
+    g = sp.Grid(n, L)
+    rho = inputs.slab_density(g.n, g.L, 5.0, g.ndim - 1, 0.5 * g.L[-1], 0.5 * g.L[-1], 4 * g.L[-1] / g.n[-1])
+    f = inputs.smooth_random_field(g.n, g.L, 23, kmax=6)
+    G = vd.Grid(n, L)
+    G.set_density(T(rho))
+    x0, info0 = G.solve("pressure", "cg", T(f), tol=1e-13, max_it=1500)
+    assert info0["status"] == "converged"
+    _, info = G.solve("pressure", "cg", T(f), x0=x0, tol=0.0, max_it=0, precision="mixed_dd")
+    assert info["iters"] == 0
+    fb = sp.project_range(f, g)
+    r64 = fb - N(G.apply("pressure", x0))
+    rel64 = np.linalg.norm(r64) / np.linalg.norm(fb)
+    assert rel64 < 1e-10
+    kmax2 = sum((math.pi * g.n[j] / g.L[j]) ** 2 for j in range(g.ndim))
+    bound = 2.0 ** -47 * kmax2 * float(np.max(1.0 / rho)) * np.linalg.norm(N(x0)) / np.linalg.norm(fb)
+    assert abs(info["relres_true"] - rel64) <= bound, (info["relres_true"], rel64, bound)
