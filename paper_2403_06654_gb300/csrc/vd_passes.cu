@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 
 constexpr int kRLines = 16;
 
 template <typename T, int S, int N1, int N2>
-__global__ void __launch_bounds__(kRLines * N2, (sizeof(T) == 4 ? 2 : 1)) k_axis_r(const AxisProg P, const GridDesc g,
+__global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(const AxisProg P, const GridDesc g,
                                                         const cpx<T>* __restrict__ twg) {
   static_assert(std::is_same<T, float>::value, "register four-step pass: float storage only");
   constexpr int N = N1 * N2;
@@ -336,23 +336,27 @@ __global__ void __launch_bounds__(kRLines * N2, (sizeof(T) == 4 ? 2 : 1)) k_axis
         // so their latencies overlap (the compiler cannot move a load of dst above a store to
         // dst); the partials were written by this thread, so the order is unchanged
         cpx<T>* q = reinterpret_cast<cpx<T>*>(dst);
-        cpx<T> prev[N2];
-        if (!xf.first) {
+        constexpr int PB = N2 < 8 ? N2 : 8;   // partial sums read in batches of PB
 #pragma unroll
-          for (int k2 = 0; k2 < N2; ++k2) prev[k2] = q[gbase + (k1 + N1 * k2) * line_stride];
-        }
+        for (int k0 = 0; k0 < N2; k0 += PB) {
+          cpx<T> prev[PB];
+          if (!xf.first) {
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) {
-          const int i = k1 + N1 * k2;
-          const int go = gbase + i * line_stride;
-          cpx<T> vv = v[k2];
-          if (xf.post) {
-            vv = scal(vv, mult(xf.post, i, go, scale));
-            if (xf.post & MUL_IK) vv = mul_i(vv);
-          } else {
-            vv = scal(vv, scale);
+            for (int b = 0; b < PB; ++b) prev[b] = q[gbase + (k1 + N1 * (k0 + b)) * line_stride];
           }
-          q[go] = xf.first ? vv : (prev[k2] + vv);
+#pragma unroll
+          for (int b = 0; b < PB; ++b) {
+            const int i = k1 + N1 * (k0 + b);
+            const int go = gbase + i * line_stride;
+            cpx<T> vv = v[k0 + b];
+            if (xf.post) {
+              vv = scal(vv, mult(xf.post, i, go, scale));
+              if (xf.post & MUL_IK) vv = mul_i(vv);
+            } else {
+              vv = scal(vv, scale);
+            }
+            q[go] = xf.first ? vv : (prev[b] + vv);
+          }
         }
       }
     }
