@@ -4,8 +4,10 @@
 // blocks writes per-block partials, and the last block to finish (atomic ticket) adds them
 // in a fixed order and runs the scalar epilogue of the algorithm (step lengths, Givens
 // rotations, convergence tests) in one thread.  The scalars never leave the device; the
-// host only reads the `done` flag every `check_every` iterations.  Kernels of an iteration
-// return at once when the flag is set, so the host may enqueue iterations ahead.
+// host only reads the `done` flag every `check_every` iterations, and (CG, RMR) one batch
+// behind: it waits for the flag of batch k-1 with batch k already queued.  Kernels of an
+// iteration return at once when the flag is set, so iterations enqueued ahead cost a launch
+// each and change nothing.
 #include "vd_krylov.cuh"
 #include "vd_prof.h"
 
@@ -778,6 +780,45 @@ static vd_status read_head(const KWork& kw, KHead* h, cudaStream_t st) {
   return VD_OK;
 }
 
+// Convergence polling one batch behind: after enqueuing batch k the host waits for the head
+// snapshot taken after batch k-1, so the device always has the next batch queued instead of
+// idling while the host wakes up and launches.  Batches enqueued past convergence return at
+// once (every kernel of an iteration checks the device `done` flag).  Two pinned snapshot
+// slots and events per host thread (server slots solve from several threads).
+struct HeadPipe {
+  KHead* slot = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int taken = 0;
+  bool ok = false;
+  HeadPipe() {
+    ok = cudaHostAlloc(reinterpret_cast<void**>(&slot), 2 * sizeof(KHead), cudaHostAllocDefault) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) == cudaSuccess;
+  }
+  // snapshot of the head after the work enqueued so far
+  vd_status snapshot(const KWork& kw, cudaStream_t st) {
+    const int k = taken & 1;
+    VD_CUDA(cudaMemcpyAsync(slot + k, kw.ks, sizeof(KHead), cudaMemcpyDeviceToHost, st));
+    VD_CUDA(cudaEventRecord(ev[k], st));
+    ++taken;
+    return VD_OK;
+  }
+  // wait for the latest snapshot (taken before the batch just enqueued) and copy it out
+  vd_status latest(KHead* h) {
+    const int k = (taken - 1) & 1;
+    VD_CUDA(cudaEventSynchronize(ev[k]));
+    *h = slot[k];
+    return VD_OK;
+  }
+};
+
+static HeadPipe* head_pipe() {
+  static thread_local HeadPipe* hp = nullptr;
+  if (!hp) hp = new HeadPipe();   // kept for the thread's lifetime
+  hp->taken = 0;
+  return hp->ok ? hp : nullptr;
+}
+
 template <typename T>
 vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b, void* x, void* vecs,
                        const KWork& kw, double* host_hist, int host_hist_cap, SolveOut* out, cudaStream_t st) {
@@ -822,16 +863,33 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
     }
     { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)3 * len * sizeof(cpx<T>) + (double)nc * sizeof(T), 0.0); k_cg_init<T><<<rb, kRedThreads, 0, st>>>(ixr, B, r, p, sym, ra); }
     int it = 0;
+    HeadPipe* hp = head_pipe();
     for (;;) {
+      const long long mark = prof_mark();
       for (int c = 0; c < check && it < o.maxit; ++c, ++it) {
         sys.apply(sys, p, q, false, done, st);
         { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)2 * len * sizeof(cpx<T>), 0.0); k_dot<T, 1><<<rb, kRedThreads, 0, st>>>(ixr, p, q, EPI_CG_ALPHA, ra, done); }
         { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)6 * len * sizeof(cpx<T>) + (double)nc * sizeof(T), 0.0); k_cg_update<T><<<rb, kRedThreads, 0, st>>>(ixr, X, p, r, q, sym, ra); }
         { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)3 * len * sizeof(cpx<T>) + (double)nc * sizeof(T), 0.0); k_cg_p<T><<<eb, 256, 0, st>>>(ixe, p, r, sym, kw.ks); }
       }
-      vd_status e = read_head(kw, &hd, st);
+      vd_status e = VD_OK;
+      if (!hp) {
+        e = read_head(kw, &hd, st);
+        if (e != VD_OK) return e;
+        if (hd.done || it >= o.maxit) break;
+        continue;
+      }
+      if (hp->taken > 0) {
+        e = hp->latest(&hd);   // the batch before the one just enqueued
+        if (e != VD_OK) return e;
+        if (hd.done) {
+          prof_discard(mark, st);   // the batch just enqueued returns at once
+          break;
+        }
+      }
+      if (it >= o.maxit) break;
+      e = hp->snapshot(kw, st);
       if (e != VD_OK) return e;
-      if (hd.done || it >= o.maxit) break;
     }
   } else if (o.solver == VD_SOLVER_RMR) {
     cpx<T>* r = vb;
@@ -844,15 +902,32 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
     }
     { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)2 * len * sizeof(cpx<T>), 0.0); k_norms<T, 2><<<rb, kRedThreads, 0, st>>>(ixr, B, r, EPI_INIT_RMR, ra, nullptr); }
     int it = 0;
+    HeadPipe* hp = head_pipe();
     for (;;) {
+      const long long mark = prof_mark();
       for (int c = 0; c < check && it < o.maxit; ++c, ++it) {
         sys.apply(sys, r, w, true, done, st);
         { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)2 * len * sizeof(cpx<T>), 0.0); k_dot<T, 2><<<rb, kRedThreads, 0, st>>>(ixr, r, w, EPI_RMR_ALPHA, ra, done); }
         { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)5 * len * sizeof(cpx<T>) + (double)nc * sizeof(T), 0.0); k_rmr_update<T><<<rb, kRedThreads, 0, st>>>(ixr, X, r, w, sym, ra); }
       }
-      vd_status e = read_head(kw, &hd, st);
+      vd_status e = VD_OK;
+      if (!hp) {
+        e = read_head(kw, &hd, st);
+        if (e != VD_OK) return e;
+        if (hd.done || it >= o.maxit) break;
+        continue;
+      }
+      if (hp->taken > 0) {
+        e = hp->latest(&hd);
+        if (e != VD_OK) return e;
+        if (hd.done) {
+          prof_discard(mark, st);
+          break;
+        }
+      }
+      if (it >= o.maxit) break;
+      e = hp->snapshot(kw, st);
       if (e != VD_OK) return e;
-      if (hd.done || it >= o.maxit) break;
     }
   } else {
     cpx<T>* V = vb;

@@ -17,6 +17,9 @@ struct Pending {
   int cls;
   cudaEvent_t a, b;
   double bytes, flops;
+  cudaStream_t st;
+  long long seq;
+  bool dropped;
 };
 struct ClassTotals {
   long long launches = 0;
@@ -27,6 +30,7 @@ static std::mutex g_mu;
 static std::vector<Pending> g_pending;
 static std::vector<cudaEvent_t> g_free;
 static ClassTotals g_tot[PC_N];
+static long long g_seq = 0;   // sequence number of the next record
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -51,6 +55,9 @@ ProfScope::ProfScope(int c, cudaStream_t s, double by, double fl) : cls(c), st(s
   p.b = get_event();
   p.bytes = by;
   p.flops = fl;
+  p.st = s;
+  p.seq = g_seq++;
+  p.dropped = false;
   cudaEventRecord(p.a, s);
   g_pending.push_back(p);
   slot = (int)g_pending.size() - 1;
@@ -67,15 +74,28 @@ static void collect_locked() {
     cudaEventSynchronize(p.b);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p.a, p.b);
-    ClassTotals& t = g_tot[p.cls];
-    t.launches += 1;
-    t.ms += ms;
-    t.bytes += p.bytes;
-    t.flops += p.flops;
+    if (!p.dropped) {
+      ClassTotals& t = g_tot[p.cls];
+      t.launches += 1;
+      t.ms += ms;
+      t.bytes += p.bytes;
+      t.flops += p.flops;
+    }
     g_free.push_back(p.a);
     g_free.push_back(p.b);
   }
   g_pending.clear();
+}
+
+long long prof_mark() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_seq;
+}
+
+void prof_discard(long long mark, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& p : g_pending)
+    if (p.seq >= mark && p.st == st) p.dropped = true;
 }
 
 }  // namespace vd

@@ -26,6 +26,12 @@ enum ProfClass : int {
 void count_launch();
 bool vd_profile_is_on();   // event timing enabled (events cannot be recorded into a graph)
 
+// Launches enqueued past convergence (they return at once) must not add their algorithmic
+// bytes: prof_mark() before enqueuing such a batch, prof_discard(mark, st) once it is known
+// to have been speculative drops the records of that stream from the mark on.
+long long prof_mark();
+void prof_discard(long long mark, cudaStream_t st);
+
 // RAII bracket of one launch; records events only when profiling is on
 struct ProfScope {
   ProfScope(int cls, cudaStream_t st, double bytes, double flops);
