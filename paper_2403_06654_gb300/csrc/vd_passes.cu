@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(con
         // so their latencies overlap (the compiler cannot move a load of dst above a store to
         // dst); the partials were written by this thread, so the order is unchanged
         cpx<T>* q = reinterpret_cast<cpx<T>*>(dst);
-        constexpr int PB = N2 < 8 ? N2 : 8;   // partial sums read in batches of PB
+        constexpr int PB = N2 < 4 ? N2 : 4;   // partial sums read in batches of PB (fewer spills than 8)
 #pragma unroll
         for (int k0 = 0; k0 < N2; k0 += PB) {
           cpx<T> prev[PB];
