@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(con
 // ---------------------------------------------------------------------------------------
 
 template <typename T, bool CV>
-__global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 4 : 1)) k_xpass(const XProg P, const GridDesc g,
+__global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)) k_xpass(const XProg P, const GridDesc g,
                                                     const cpx<T>* __restrict__ twg, int llpc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (P.done && *P.done) return;
