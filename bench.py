@@ -80,7 +80,7 @@ DTYPES = {"mixed_dd": "f32 inner / f64 refinement, residual transforms in float-
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel class,
 # averaged over the launches of one inner iteration in an ncu capture of this workload
 # (profiles/sections_jet256_mixed_dd.md); reported only for the class it was taken for.
-MEASURED_TRAFFIC = {"axis_f32": 222.4e6}
+MEASURED_TRAFFIC = {"axis_f32": 230.5e6}
 
 # FP64 arithmetic peak of the GB300 CUDA cores: 1.25 TFLOP/s nominal (recipe table: FP64 is
 # far below B200); counted with an FMA as two flops.
