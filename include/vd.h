@@ -94,7 +94,9 @@ typedef struct {
   int use_x0;        /* 1: x holds the initial guess (warm start, Sec. 3.1); 0: start from 0 */
   int precision;     /* vd_precision */
   double inner_tol;  /* VD_PREC_MIXED: relative tolerance of each inner solve (default 1e-5) */
-  int check_every;   /* iterations enqueued between host convergence checks (default 1) */
+  int check_every;   /* iterations enqueued between host convergence checks (default 1); CG
+                        and RMR check one batch behind, so one batch may be launched after
+                        convergence: its kernels see the device flag and return at once */
 } vd_solve_params;
 
 typedef struct {
