@@ -11,8 +11,8 @@ true double-precision residual that the library returns.
 The headline value is the mixed-precision solve rate (float transforms inside double
 iterative refinement); the plain double-precision rate is measured beside it.  The headline
 steps run without instrumentation; the same number of solves then runs again with CUDA
-events around every kernel, and the roofline, per-iteration and kernel-class figures come
-from that second pass.
+events around every kernel (the roofline and kernel-class figures), and a third time with
+events around each inner float solve only (the per-iteration figure).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 """
@@ -704,6 +704,15 @@ def main():
     vd.vd_profile_enable(False)
     t_prof = evp[0].elapsed_time(evp[1]) / 1e3
     prof = {c: vd.vd_profile_read(c) for c in vd.PROFILE_CLASSES}
+
+    # ---------------- and once more in span mode: each inner float solve timed as a whole ----------------
+    # (two events per inner solve instead of two per kernel: the per-iteration figure below)
+    vd.vd_profile_reset()
+    vd.vd_profile_enable(2)
+    infos_span = [solve(head) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    vd.vd_profile_enable(0)
+    span = vd.vd_profile_read(vd.PROFILE_SPAN_INNER_F32)
     if pg is not None:
         tt = torch.tensor([t_mixed], device=dev)
         pg.all_reduce(tt, op=pg.ReduceOp.MAX)
@@ -771,15 +780,25 @@ def main():
 
     # ---------------- roofline of the dominant kernel class ----------------
     pk, pk_src = peaks()
-    # per inner (float) Krylov iteration: float passes + float vector kernels
+    # per inner (float) Krylov iteration: float passes + float vector kernels.  Primary: the
+    # span pass (each inner solve between two events: host gaps included, no per-kernel events);
+    # beside it the sum of the per-kernel event durations of the instrumented pass.
     n_inner = sum(i["iters"] for i in infos_prof)
     f32c = [c for c in prof if vd.PROFILE_CLASSES[c] in ("axis_f32", "xpass_f32", "vec_f32")]
-    it_ms = sum(prof[c]["ms"] for c in f32c) / max(n_inner, 1)
-    it_bytes = sum(prof[c]["alg_bytes"] for c in f32c) / max(n_inner, 1)
+    k_ms = sum(prof[c]["ms"] for c in f32c) / max(n_inner, 1)
+    k_bytes = sum(prof[c]["alg_bytes"] for c in f32c) / max(n_inner, 1)
+    n_span = sum(i["iters"] for i in infos_span)
+    it_ms = span["ms"] / max(n_span, 1)
+    it_bytes = span["alg_bytes"] / max(n_span, 1)
     per_iter = {"ms": it_ms, "alg_bytes": it_bytes, "achieved_gbs": it_bytes / (it_ms / 1e3) / 1e9,
                 "frac_of_hbm": it_bytes / (it_ms / 1e3) / 1e9 / pk["hbm_gbs"],
-                "iterations": n_inner,
-                "includes": "float transform passes + float Krylov vector kernels of the inner CG, per iteration"}
+                "iterations": n_span, "inner_solves": span["launches"],
+                "includes": "whole inner float CG solves (transform passes, vector kernels, host gaps) "
+                            "between two CUDA events each, divided by their iterations",
+                "from_kernel_events": {"ms": k_ms, "alg_bytes": k_bytes,
+                                       "frac_of_hbm": k_bytes / (k_ms / 1e3) / 1e9 / pk["hbm_gbs"],
+                                       "note": "sum of per-kernel event durations (each inflated by the "
+                                               "events around it)"}}
     dom = max((c for c in prof if c != 4), key=lambda c: prof[c]["ms"])
     d = prof[dom]
     name = vd.PROFILE_CLASSES[dom]
@@ -857,8 +876,9 @@ def main():
         "per_iteration": per_iter,
         "kernel_classes": classes,
         "profiled_pass": {"steps": args.steps, "ms_per_step": t_prof / args.steps * 1e3,
-                          "note": "roofline, per_iteration and kernel_classes come from this second pass of the "
-                                  "same solves with CUDA events around every kernel"},
+                          "note": "roofline and kernel_classes come from this second pass of the same solves "
+                                  "with CUDA events around every kernel; per_iteration from a third pass with "
+                                  "events around each inner solve only"},
         "clocks": clocks,
         "cpu_baseline": cpu,
         "workloads": extras,

@@ -406,6 +406,10 @@ vd_status vd_apply_pressure_noalloc(int ndim, const int n[3], const double L[3],
  * 0 strided pass double, 1 strided pass float, 2 x pass double, 3 x pass float,
  * 5 strided pass float-pair, 6 x pass float-pair, 7 Krylov vector kernels on float vectors,
  * 8 Krylov vector kernels on double vectors (4: unused).
+ * vd_profile_enable(2): span mode: only each inner float Krylov solve of a mixed-precision
+ * refinement sweep is bracketed (two events), with the algorithmic bytes and flops of every
+ * launch inside it, into class 9; individual launches are not timed.
+ * vd_profile_enable(0) turns profiling off; other values are INVALID_ARG.
  * vd_profile_read synchronises on the recorded events; vd_profile_reset clears the totals.
  */
 long long vd_launch_count(void);

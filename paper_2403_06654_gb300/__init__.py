@@ -374,7 +374,8 @@ def vd_launch_count():
 
 
 def vd_profile_enable(on):
-    _check(lib().vd_profile_enable(int(bool(on))))
+    """0 off, 1 (or True) every launch bracketed by events, 2 span mode (whole inner solves)."""
+    _check(lib().vd_profile_enable(int(on)))
 
 
 def vd_profile_reset():
@@ -383,6 +384,7 @@ def vd_profile_reset():
 
 PROFILE_CLASSES = {0: "axis_f64", 1: "axis_f32", 2: "xpass_f64", 3: "xpass_f32", 5: "axis_dd", 6: "xpass_dd",
                    7: "vec_f32", 8: "vec_f64"}
+PROFILE_SPAN_INNER_F32 = 9   # span mode: whole inner float solves
 
 
 def vd_profile_read(cls):

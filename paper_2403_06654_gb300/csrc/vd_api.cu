@@ -909,7 +909,10 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
       std::vector<double> ih;
       const int icap = hh ? std::min(std::max(0, hcap - hlen) + 1, prm->max_it + 2) : 0;
       if (icap > 0) ih.resize(icap);
-      e = krylov_solve<float>(sys32, si, L.bh_f, L.xh_f, L.vecs, kw, icap > 0 ? ih.data() : nullptr, icap, &ri, st);
+      {
+        ProfSpan span(PC_INNER32, st);   // the whole inner solve, for the profiler's span mode
+        e = krylov_solve<float>(sys32, si, L.bh_f, L.xh_f, L.vecs, kw, icap > 0 ? ih.data() : nullptr, icap, &ri, st);
+      }
       if (e != VD_OK) return e;
       // history: inner residuals rescaled to the outer right-hand side
       for (int i = 1; i <= ri.iters && hlen < hcap && i < (int)ih.size(); ++i) hh[hlen++] = ih[i] * rel;

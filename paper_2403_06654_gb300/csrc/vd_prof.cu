@@ -47,20 +47,54 @@ static cudaEvent_t get_event() {
 
 ProfScope::ProfScope(int c, cudaStream_t s, double by, double fl) : cls(c), st(s), bytes(by), flops(fl), slot(-1) {
   count_launch();
-  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  const int mode = g_prof_on.load(std::memory_order_relaxed);
+  if (!mode) return;
   std::lock_guard<std::mutex> lk(g_mu);
   Pending p;
   p.cls = c;
-  p.a = get_event();
-  p.b = get_event();
+  p.a = nullptr;
+  p.b = nullptr;
   p.bytes = by;
   p.flops = fl;
   p.st = s;
   p.seq = g_seq++;
   p.dropped = false;
-  cudaEventRecord(p.a, s);
+  if (mode == 1) {
+    p.a = get_event();
+    p.b = get_event();
+    cudaEventRecord(p.a, s);
+  }
   g_pending.push_back(p);
-  slot = (int)g_pending.size() - 1;
+  if (mode == 1) slot = (int)g_pending.size() - 1;
+}
+
+ProfSpan::ProfSpan(int c, cudaStream_t s) : cls(c), st(s), seq0(-1), a(nullptr) {
+  if (g_prof_on.load(std::memory_order_relaxed) != 2) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  seq0 = g_seq;
+  a = get_event();
+  cudaEventRecord(a, s);
+}
+
+ProfSpan::~ProfSpan() {
+  if (!a) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Pending p;
+  p.cls = cls;
+  p.a = a;
+  p.b = get_event();
+  p.bytes = 0.0;
+  p.flops = 0.0;
+  for (const auto& q : g_pending)
+    if (!q.a && q.seq >= seq0 && q.st == st && !q.dropped) {
+      p.bytes += q.bytes;
+      p.flops += q.flops;
+    }
+  p.st = st;
+  p.seq = g_seq++;
+  p.dropped = false;
+  cudaEventRecord(p.b, st);
+  g_pending.push_back(p);
 }
 
 ProfScope::~ProfScope() {
@@ -71,6 +105,7 @@ ProfScope::~ProfScope() {
 
 static void collect_locked() {
   for (auto& p : g_pending) {
+    if (!p.a) continue;   // span mode: a launch counted only inside its span
     cudaEventSynchronize(p.b);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p.a, p.b);
@@ -107,9 +142,10 @@ extern "C" {
 long long vd_launch_count(void) { return g_launches.load(); }
 
 vd_status vd_profile_enable(int on) {
+  if (on < 0 || on > 2) return fail(VD_ERR_INVALID_ARG, "profile mode: 0 off, 1 every launch, 2 spans");
   std::lock_guard<std::mutex> lk(g_mu);
   if (!on) collect_locked();
-  g_prof_on.store(on ? 1 : 0);
+  g_prof_on.store(on);
   return VD_OK;
 }
 

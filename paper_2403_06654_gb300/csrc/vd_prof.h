@@ -20,7 +20,8 @@ enum ProfClass : int {
   PC_XPASSDD = 6,  // contiguous x pass, float-pair
   PC_VEC32 = 7,    // Krylov vector kernels on float vectors
   PC_VEC64 = 8,    // Krylov vector kernels on double vectors
-  PC_N = 9
+  PC_INNER32 = 9,  // a whole inner float Krylov solve (span mode only)
+  PC_N = 10
 };
 
 void count_launch();
@@ -32,7 +33,19 @@ bool vd_profile_is_on();   // event timing enabled (events cannot be recorded in
 long long prof_mark();
 void prof_discard(long long mark, cudaStream_t st);
 
-// RAII bracket of one launch; records events only when profiling is on
+// RAII bracket of a stretch of work (span mode, vd_profile_enable(2)): two events around it
+// on its stream and the algorithmic bytes and flops of the launches issued inside it on that
+// stream; the launches themselves are not bracketed in this mode
+struct ProfSpan {
+  ProfSpan(int cls, cudaStream_t st);
+  ~ProfSpan();
+  int cls;
+  cudaStream_t st;
+  long long seq0;
+  cudaEvent_t a;
+};
+
+// RAII bracket of one launch; records events only when profiling is on (mode 1)
 struct ProfScope {
   ProfScope(int cls, cudaStream_t st, double bytes, double flops);
   ~ProfScope();
