@@ -216,7 +216,9 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 
 // Thread n2 of a line holds x[N2 n1 + n2] (the rows it loads), transforms over n1 in
 // registers, multiplies by W_n^{n2 k1}, and one shared-memory transpose hands column k1 to
 // thread k1 mod N2, which transforms over n2 and stores rows k1 + N1 k2.  16 lines (columns)
-// per block, line stride n + 1 in shared memory (conflict-free transposes).
+// per block, line stride n + 1 in shared memory (conflict-free transposes).  Length 256 runs
+// three blocks per SM (80 registers, a few hundred bytes of spills held in L1): measured
+// faster than two (128 registers) and four (64 registers, spills reaching L2).
 // ---------------------------------------------------------------------------------------
 
 constexpr int kRLines = 16;
@@ -367,6 +369,8 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(con
 // contiguous x pass (real <-> half spectrum through a complex FFT of length n0/2)
 // ---------------------------------------------------------------------------------------
 
+// float pairs: three blocks per SM (80 registers, no spills); the tuned 16 lines per block
+// take 70 KB of shared memory each, so a fourth block would not fit anyway
 template <typename T, bool CV>
 __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)) k_xpass(const XProg P, const GridDesc g,
                                                     const cpx<T>* __restrict__ twg, int llpc) {
