@@ -38,7 +38,7 @@ WORKLOAD = ("3D periodic 256^3 swirling-jet-like density (s=0.5, R=0.5, d=0.05, 
             "rhs = div of axial+swirl(q=1) velocity + 1e-3 noise (seed 3); pressure solve to 1e-10, x0 = 0")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--serve-count", type=int, default=None, help="requests of the serving trace")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrival rate (req/s)")
     ap.add_argument("--serve-inflight", type=int, default=8, help="server execution slots")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def peaks():
@@ -150,6 +150,26 @@ def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(t, pg, device):
+    """The job's duration is its slowest rank's: max of t over the ranks (t itself at N = 1)."""
+    if pg is None:
+        return float(t)
+    import torch
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def sum_over_ranks(v, pg, device):
+    """Whole-job total of a per-rank quantity (v itself at N = 1)."""
+    if pg is None:
+        return float(v)
+    import torch
+    tt = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    pg.all_reduce(tt, op=pg.ReduceOp.SUM)
+    return float(tt.item())
 
 
 # ------------------------------------------------------------------------------------------
@@ -565,7 +585,6 @@ SERVE_WORKLOAD = ("Poisson arrivals (seed 5) of pressure solves: 95% batched-ins
 
 def serve_line(args, vd, dev, rank, world, pg):
     """The serving line: the full trace at the configured rate, a rate sweep, and one-at-a-time runs."""
-    import torch
     count = args.serve_count or 20000
     sampler = ClockSampler(dev.index)
     sampler.start()
@@ -574,11 +593,7 @@ def serve_line(args, vd, dev, rank, world, pg):
                     sweep=(100.0, 150.0, 200.0, 250.0, 500.0, 1000.0, 2000.0), baseline_count=200)
     launches = vd.vd_launch_count() - l0
     clocks = sampler.stop()
-    value = s["solves_per_s"]
-    if pg is not None:
-        t = torch.tensor([value], device=dev)
-        pg.all_reduce(t)
-        value = float(t.item())
+    value = sum_over_ranks(s["solves_per_s"], pg, dev)
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": s["requests"],
            "warmup": args.serve_inflight, "ms_per_step": 1e3 / max(value, 1e-9), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES["mixed_dd"], "data": "synthetic",
@@ -713,10 +728,7 @@ def main():
     torch.cuda.synchronize()
     vd.vd_profile_enable(0)
     span = vd.vd_profile_read(vd.PROFILE_SPAN_INNER_F32)
-    if pg is not None:
-        tt = torch.tensor([t_mixed], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_mixed = float(tt.item())
+    t_mixed = max_over_ranks(t_mixed, pg, dev)
 
     # double-precision check of the last headline solution (outside the timed region)
     fb = f.clone()
@@ -734,7 +746,7 @@ def main():
     ev3[1].record(stream)
     torch.cuda.synchronize()
     barrier()
-    t_side = ev3[0].elapsed_time(ev3[1]) / 1e3
+    t_side = max_over_ranks(ev3[0].elapsed_time(ev3[1]) / 1e3, pg, dev)
 
     # ---------------- timed: plain FP64 ----------------
     ev2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -745,10 +757,7 @@ def main():
     torch.cuda.synchronize()
     barrier()
     t64 = ev2[0].elapsed_time(ev2[1]) / 1e3
-    if pg is not None:
-        tt = torch.tensor([t64], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t64 = float(tt.item())
+    t64 = max_over_ranks(t64, pg, dev)
 
     # ---------------- end to end through host buffers ----------------
     rho_h = rho_d.cpu().pin_memory()
@@ -773,10 +782,7 @@ def main():
     torch.cuda.synchronize()
     t_e2e = e0.elapsed_time(e1) / 1e3
     wall_e2e = time.perf_counter() - t0
-    if pg is not None:
-        tt = torch.tensor([t_e2e], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = max_over_ranks(t_e2e, pg, dev)
 
     # ---------------- roofline of the dominant kernel class ----------------
     pk, pk_src = peaks()
