@@ -15,6 +15,8 @@
 #include <cmath>
 #include <cstddef>
 #include <cstring>
+#include <vector>
+#include <mutex>
 
 namespace vd {
 
@@ -784,7 +786,9 @@ static vd_status read_head(const KWork& kw, KHead* h, cudaStream_t st) {
 // snapshot taken after batch k-1, so the device always has the next batch queued instead of
 // idling while the host wakes up and launches.  Batches enqueued past convergence return at
 // once (every kernel of an iteration checks the device `done` flag).  Two pinned snapshot
-// slots and events per host thread (server slots solve from several threads).
+// slots and events per solve in flight, leased from a process-wide pool (server slots solve
+// from several threads; the pool never shrinks, so it holds the peak number of concurrent
+// solves).
 struct HeadPipe {
   KHead* slot = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -812,12 +816,44 @@ struct HeadPipe {
   }
 };
 
-static HeadPipe* head_pipe() {
-  static thread_local HeadPipe* hp = nullptr;
-  if (!hp) hp = new HeadPipe();   // kept for the thread's lifetime
-  hp->taken = 0;
-  return hp->ok ? hp : nullptr;
-}
+class HeadPipeLease {
+ public:
+  HeadPipeLease() {
+    {
+      std::lock_guard<std::mutex> lk(mu());
+      if (!pool().empty()) {
+        hp_ = pool().back();
+        pool().pop_back();
+      }
+    }
+    if (!hp_) hp_ = new HeadPipe();
+    hp_->taken = 0;
+  }
+  ~HeadPipeLease() {
+    // no snapshot copy may still be landing in the slots when the next solve takes them
+    if (hp_->ok && hp_->taken > 0) {
+      cudaEventSynchronize(hp_->ev[0]);
+      if (hp_->taken > 1) cudaEventSynchronize(hp_->ev[1]);
+    }
+    std::lock_guard<std::mutex> lk(mu());
+    pool().push_back(hp_);
+  }
+  HeadPipeLease(const HeadPipeLease&) = delete;
+  HeadPipeLease& operator=(const HeadPipeLease&) = delete;
+  // null when the pinned buffer or the events could not be created: poll synchronously
+  HeadPipe* get() const { return hp_->ok ? hp_ : nullptr; }
+
+ private:
+  static std::mutex& mu() {
+    static std::mutex m;
+    return m;
+  }
+  static std::vector<HeadPipe*>& pool() {
+    static std::vector<HeadPipe*> p;
+    return p;
+  }
+  HeadPipe* hp_ = nullptr;
+};
 
 template <typename T>
 vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b, void* x, void* vecs,
@@ -863,7 +899,8 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
     }
     { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)3 * len * sizeof(cpx<T>) + (double)nc * sizeof(T), 0.0); k_cg_init<T><<<rb, kRedThreads, 0, st>>>(ixr, B, r, p, sym, ra); }
     int it = 0;
-    HeadPipe* hp = head_pipe();
+    HeadPipeLease lease;
+    HeadPipe* hp = lease.get();
     for (;;) {
       const long long mark = prof_mark();
       for (int c = 0; c < check && it < o.maxit; ++c, ++it) {
@@ -902,7 +939,8 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
     }
     { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)2 * len * sizeof(cpx<T>), 0.0); k_norms<T, 2><<<rb, kRedThreads, 0, st>>>(ixr, B, r, EPI_INIT_RMR, ra, nullptr); }
     int it = 0;
-    HeadPipe* hp = head_pipe();
+    HeadPipeLease lease;
+    HeadPipe* hp = lease.get();
     for (;;) {
       const long long mark = prof_mark();
       for (int c = 0; c < check && it < o.maxit; ++c, ++it) {
