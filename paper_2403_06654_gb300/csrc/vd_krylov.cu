@@ -635,12 +635,6 @@ __global__ void k_sub(long long len, const cpx<T>* __restrict__ b, const cpx<T>*
   if (done && *done) return;
   GRID_STRIDE(e, len) { r[e] = b[e] - q[e]; }
 }
-__global__ void k_d2f(long long len, const cpx<double>* __restrict__ in, cpx<float>* __restrict__ out) {
-  GRID_STRIDE(e, len) { out[e] = mk<float>((float)in[e].x, (float)in[e].y); }
-}
-__global__ void k_f2d(long long len, const cpx<float>* __restrict__ in, cpx<double>* __restrict__ out) {
-  GRID_STRIDE(e, len) { out[e] = mk<double>((double)in[e].x, (double)in[e].y); }
-}
 // refinement steps fused over one pass of the double vectors (same arithmetic per element as
 // the separate kernels): out = float(in * s) and y += a * double(xf); s and a come from the
 // host, or from the refinement state (o->scale, o->rnorm) when o is set
@@ -701,12 +695,6 @@ void spec_axpy(long long len, double a, const void* x, void* y, cudaStream_t st)
 template <typename T>
 void spec_sub(long long len, const void* b, const void* q, void* r, cudaStream_t st) {
   { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)3 * len * sizeof(cpx<T>), 0.0); k_sub<T><<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<T>*)b, (const cpx<T>*)q, (cpx<T>*)r, nullptr); }
-}
-void spec_d2f(long long len, const void* in, void* out, cudaStream_t st) {
-  { k_d2f<<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<double>*)in, (cpx<float>*)out); count_launch(); }
-}
-void spec_f2d(long long len, const void* in, void* out, cudaStream_t st) {
-  { k_f2d<<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<float>*)in, (cpx<double>*)out); count_launch(); }
 }
 template <typename T>
 void spec_project(const vd_grid* G, int ncomp, void* v, cudaStream_t st) {
@@ -1322,16 +1310,6 @@ __global__ void k_out_info(const OState* o, double* info) {
 }
 
 // v *= 1/|r| and x += |r| d with the scalars read from the refinement state
-__global__ void k_scale_out(long long n, const OState* o, cpx<double>* v) {
-  const double s = o->scale;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    v[e] = scal(v[e], s);
-}
-__global__ void k_axpy_out(long long n, const OState* o, const cpx<double>* x, cpx<double>* y) {
-  const double a = o->rnorm;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    y[e] = y[e] + scal(x[e], a);
-}
 
 static vd_status open_cond(cudaStream_t st, cudaGraphConditionalNodeType type, cudaGraphConditionalHandle hnd,
                            cudaGraph_t* body) {

@@ -133,14 +133,12 @@ double spec_dot_host(const SpecSystem& sys, const void* a, const void* b, const 
 // zero the 2^d null-space coefficients of each component
 template <typename T>
 void spec_project(const vd_grid* G, int ncomp, void* v, cudaStream_t st);
-// precision conversions of spectral vectors
-void spec_d2f(long long len, const void* in, void* out, cudaStream_t st);
-// fused refinement steps on double vectors: out = float(in * s); y += a * double(xf);
-// r = b - q returning |r|^2 (weighted) to the host
+// refinement steps on double vectors, each one pass: out = float(in * s) (narrowed right-hand
+// side of the inner solve); y += a * double(xf) (correction); r = b - q returning |r|^2
+// (weighted) to the host
 void spec_d2f_scaled(long long len, const void* in, double s, void* out, cudaStream_t st);
 void spec_axpy_f2d(long long len, double a, const void* xf, void* y, cudaStream_t st);
 double spec_sub_norm2_host(const SpecSystem& sys, const void* b, const void* q, void* r, const KWork& kw,
                            cudaStream_t st);
-void spec_f2d(long long len, const void* in, void* out, cudaStream_t st);
 
 }  // namespace vd
