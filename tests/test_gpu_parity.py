@@ -303,21 +303,23 @@ def test_float_pair_residual_accuracy(n, L):
     assert abs(info["relres_true"] - rel64) <= bound, (info["relres_true"], rel64, bound)
 
 
-@pytest.mark.parametrize("max_it", [2, 5, 9])
+@pytest.mark.parametrize("max_it", [2, 5, 9, 12, 15, 20])
 @pytest.mark.parametrize("precision", ["mixed_dd", "mixed"])
 def test_capped_mixed_solve_returns_the_reported_iterate(max_it, precision):
-    """With the iteration cap hit before convergence, the returned field is the iterate whose
-    true residual is reported (mixed_dd may take it from the last refinement residual's fused
-    inverse transform instead of a separate one): the reported relres_true equals the residual
-    recomputed from the returned field with the double operator."""
+    """With an iteration cap (hit in the first or in a later refinement sweep, or not at all),
+    the returned field is the iterate whose true residual is reported -- mixed_dd takes it
+    from the last refinement residual's fused inverse transform when that sweep was expected
+    to be the last, else from a separate inverse transform: the reported relres_true equals
+    the residual recomputed from the returned field with the double operator."""
     n, L = (40, 32, 24), (2 * math.pi, 1.0, 2.0)
     g = sp.Grid(n, L)
     rho = inputs.slab_density(g.n, g.L, 10.0, 1, 0.5 * g.L[1], 0.5 * g.L[1], 3 * g.L[1] / g.n[1])
     f = inputs.smooth_random_field(g.n, g.L, 31, kmax=5)
     G = vd.Grid(n, L)
     G.set_density(T(rho))
-    x, info = G.solve("pressure", "cg", T(f), tol=1e-12, max_it=max_it, precision=precision)
-    assert info["status"] == "max_iter" and info["iters"] == max_it
+    x, info = G.solve("pressure", "cg", T(f), tol=1e-10, max_it=max_it, precision=precision)
+    assert info["iters"] <= max_it
+    assert info["status"] == ("converged" if info["relres_true"] <= 1e-10 else "max_iter")
     fb = sp.project_range(f, g)
     rel = np.linalg.norm(fb - N(G.apply("pressure", x))) / np.linalg.norm(fb)
     assert abs(info["relres_true"] - rel) <= 1e-9 * rel + 1e-13, (info["relres_true"], rel)
