@@ -53,6 +53,22 @@ def test_host_side_argument_checks_without_gpu():
     assert L.vd_version().startswith(b"vdspectral")
 
 
+def test_profiler_modes_checked_on_the_host():
+    """Profile mode 0 off, 1 every launch, 2 spans; anything else is refused before any
+    device call, and reading an unknown class is refused too."""
+    L = _lib_or_skip()
+    for bad in (-1, 3, 7):
+        assert L.vd_profile_enable(bad) == vd.VD_ERR_INVALID_ARG
+    assert b"profile mode" in L.vd_last_error()
+    assert L.vd_profile_enable(0) == vd.VD_OK
+    n = ctypes.c_longlong()
+    ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    for bad in (-1, 10):
+        assert L.vd_profile_read(bad, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by),
+                                 ctypes.byref(fl)) == vd.VD_ERR_INVALID_ARG
+    assert vd.PROFILE_SPAN_INNER_F32 == 9 and 9 not in vd.PROFILE_CLASSES
+
+
 def test_pointer_marshalling_rejects_noncontiguous():
     """Every pointer of the C interface addresses a dense row-major array: strided tensors are refused."""
     import torch
