@@ -11,8 +11,19 @@ VDINSE.Lrho.num, VDINSE.num.gradp.update) on a fully periodic grid:
    (dt/2) zeta(rho, w) = w - V~_rho w;
 4. pressure: L~_{rho^{n+1/2}} phi = div u* / dt;
 5. projection: u^{n+1} = u* - dt grad(phi) / rho^{n+1/2};
-6. gradient-form pressure update:
-   grad p^{n+1/2} = grad p^{n-1/2} + grad phi - rho^{n+1/2} (dt/2) zeta(rho^{n+1/2}, grad phi / rho^{n+1/2}).
+6. pressure update in the paper's scalar form (Eq. VDINSE.num.p.update), stored as its gradient:
+   p^{n+1/2} = p^{n-1/2} + phi - Lap^+ div(rho^{n+1/2} (dt/2) zeta(rho^{n+1/2}, grad phi / rho^{n+1/2})),
+   i.e. grad p += grad phi - grad Lap^+ div(c) with c the correction field.  The gradient form
+   (Eq. VDINSE.num.gradp.update: grad p += grad phi - c) equals it only up to the solenoidal
+   part of c, which the gradient form keeps: with variable density that part is not zero, it
+   accumulates O(dt^2) per step into grad p and enters the next predictor, which costs the
+   scheme its second order in time when viscosity and density variation are both strong
+   (Sec. 4.1 workload: Re = 1, s = 10).  The paper's time study marches the scalar form;
+   FlowParams.p_update = "gradient" selects the other one.
+
+Optional source terms (Sec. 4.1 adds a mass source and a body force so that a manufactured
+field solves the modified equations): mass_source S and force F, both given at t^{n+1/2},
+enter as -dt [u.grad rho - S]^{n+1/2} in step 1 and +dt F in the predictor of step 3.
 
 Readings (the paper is silent on these):
 * [.]^{n+1/2} by Adams--Bashforth 2 = 1.5 N^n - 0.5 N^{n-1}; the first step uses N^n
@@ -28,7 +39,7 @@ from __future__ import annotations
 from dataclasses import dataclass, field
 import numpy as np
 
-from .spectral import Grid, deriv, div, fwd, inv, ksq
+from .spectral import Grid, deriv, div, fwd, inv, ksq, precond_pressure
 from .operators import RhoDerivs, apply_velocity, pressure_system, velocity_system
 from .solvers import solve
 
@@ -44,6 +55,7 @@ class FlowParams:
     tol: float = 1e-10
     maxit: int = 200
     restart: int = 30
+    p_update: str = "scalar"        # "scalar" (Eq. VDINSE.num.p.update) or "gradient"
 
 
 @dataclass
@@ -73,12 +85,14 @@ def body_force(rho_h, grid, p: FlowParams):
     return f
 
 
-def step(st: FlowState, grid: Grid, dt: float, p: FlowParams) -> FlowState:
+def step(st: FlowState, grid: Grid, dt: float, p: FlowParams, mass_source=None, force=None) -> FlowState:
     d = grid.ndim
     rho, u = st.rho, st.u
     # 1. mass equation
     n_rho = advect_scalar(u, rho, grid)
     ab_rho = n_rho if st.n_rho_prev is None else 1.5 * n_rho - 0.5 * st.n_rho_prev
+    if mass_source is not None:
+        ab_rho = ab_rho - mass_source
     c = dt / (2.0 * p.Re * p.Sc)
     k2 = ksq(grid)
     rho_new = np.real(inv(((1.0 - c * k2) * fwd(rho) - dt * fwd(ab_rho)) / (1.0 + c * k2)))
@@ -91,7 +105,10 @@ def step(st: FlowState, grid: Grid, dt: float, p: FlowParams) -> FlowState:
     ab_u = n_u if st.n_u_prev is None else 1.5 * n_u - 0.5 * st.n_u_prev
     rd = RhoDerivs(rho_h, grid)
     half_zeta_u = u - apply_velocity(rho_h, u, grid, a, inv_sc, rd)
-    rhs = u + dt * (-ab_u - st.gradp / rho_h + body_force(rho_h, grid, p)) + half_zeta_u
+    f_body = body_force(rho_h, grid, p)
+    if force is not None:
+        f_body = f_body + force
+    rhs = u + dt * (-ab_u - st.gradp / rho_h + f_body) + half_zeta_u
     Av, Mv = velocity_system(rho_h, grid, a, inv_sc)
     rv = solve(p.vel_solver, Av, Mv, rhs, x0=u, tol=p.tol, maxit=p.maxit, restart=p.restart)
     u_star = rv.x
@@ -103,10 +120,16 @@ def step(st: FlowState, grid: Grid, dt: float, p: FlowParams) -> FlowState:
     # 5. projection
     gphi = np.stack([deriv(phi, grid, j) for j in range(d)])
     u_new = u_star - dt * gphi / rho_h
-    # 6. pressure update (gradient form)
+    # 6. pressure update: correction c = rho_h (dt/2) zeta(rho_h, grad phi / rho_h)
     w = gphi / rho_h
     half_zeta_w = w - apply_velocity(rho_h, w, grid, a, inv_sc, rd)
-    gradp_new = st.gradp + gphi - rho_h * half_zeta_w
+    corr = rho_h * half_zeta_w
+    if p.p_update == "scalar":
+        q = precond_pressure(div(list(corr), grid), grid)          # Lap^+ div c
+        corr = np.stack([deriv(q, grid, j) for j in range(d)])     # its gradient
+    elif p.p_update != "gradient":
+        raise ValueError(p.p_update)
+    gradp_new = st.gradp + gphi - corr
     log = {"vel_iters": rv.iters, "vel_status": rv.status, "vel_relres": rv.relres_true,
            "pres_iters": rp.iters, "pres_status": rp.status, "pres_relres": rp.relres_true}
     return FlowState(rho=rho_new, u=u_new, gradp=gradp_new, phi=phi, n_rho_prev=n_rho,
