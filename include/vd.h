@@ -196,8 +196,10 @@ vd_status vd_gradient(const vd_grid* grid, const double* phi, double* out, void*
  * Lrho.num, num.proj, num.gradp.update) on the grid: Crank--Nicolson + Adams--Bashforth 2
  * mass update (diagonal in Fourier), rho_h = (rho^{n+1} + rho^n)/2, velocity predictor solved
  * with V~_{rho_h} (a = dt/(2 Re); warm start u^n), pressure increment L~_{rho_h} phi = div(u*) / dt
- * (warm start: previous phi), projection u = u* - dt grad(phi) / rho_h and the gradient-form
- * pressure update.  Readings: Euler for the first step's advection terms; gravity along
+ * (warm start: previous phi), projection u = u* - dt grad(phi) / rho_h and the pressure update
+ * in the scalar form of Eq. VDINSE.num.p.update (the form the paper's time study marches),
+ * kept as its gradient: grad p += grad phi - grad Lap^+ div(rho_h (dt/2) zeta(rho_h,
+ * grad phi / rho_h)).  Readings: Euler for the first step's advection terms; gravity along
  * gravity_axis as the periodic body force -Fr^-1 (1 - <rho_h>/rho_h) (the paper's -Fr^-1 e_z
  * with its mean weight removed); -1 for no gravity.
  * Memory: vd_flow_bytes() device bytes (caller-owned) hold the state (rho, u, grad p, phi,
@@ -226,6 +228,12 @@ vd_status vd_flow_create(vd_grid* grid, const vd_flow_params* params, void* mem,
 vd_status vd_flow_destroy(vd_flow* flow);
 /* initial state: rho (n points) and u (ndim fields); grad p and phi start at 0 */
 vd_status vd_flow_set_state(vd_flow* flow, const double* rho, const double* u, vd_stream stream);
+/* optional source terms for the following steps (Sec. 4.1 adds a mass source and a body
+ * force so that a manufactured field solves the equations): mass_source (n points) and force
+ * (ndim fields), device buffers the flow copies; each step uses them as values at its mid-time
+ * t^{n+1/2}: -dt [u.grad rho - S] in the mass update, +dt F in the predictor.  Set them before
+ * every step whose sources change; a null pointer removes that term.  Not part of snapshots. */
+vd_status vd_flow_set_sources(vd_flow* flow, const double* mass_source, const double* force, vd_stream stream);
 /* copy out any of rho, u, grad p, phi (null pointers are skipped) */
 vd_status vd_flow_get_state(const vd_flow* flow, double* rho, double* u, double* gradp, double* phi,
                             vd_stream stream);

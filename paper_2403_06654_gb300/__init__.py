@@ -135,6 +135,7 @@ _SIGS = {
     "vd_flow_destroy": (_I, [_P]),
     "vd_flow_set_state": (_I, [_P, _P, _P, _P]),
     "vd_flow_get_state": (_I, [_P, _P, _P, _P, _P, _P]),
+    "vd_flow_set_sources": (_I, [_P, _P, _P, _P]),
     "vd_flow_step": (_I, [_P, ctypes.c_double, ctypes.POINTER(vd_step_info), _P]),
     "vd_flow_snapshot_bytes": (_SZ, [_P]),
     "vd_flow_save": (_I, [_P, _P, _SZ, _P]),
@@ -286,6 +287,11 @@ def vd_flow_set_state(f, rho, u, stream=None):
 def vd_flow_get_state(f, rho=None, u=None, gradp=None, phi=None, stream=None):
     p = lambda t: _ptr(t) if t is not None else None  # noqa: E731
     _check(lib().vd_flow_get_state(f, p(rho), p(u), p(gradp), p(phi), _stream(stream)))
+
+
+def vd_flow_set_sources(f, mass_source=None, force=None, stream=None):
+    p = lambda t: _ptr(t) if t is not None else None  # noqa: E731
+    _check(lib().vd_flow_set_sources(f, p(mass_source), p(force), _stream(stream)))
 
 
 def vd_flow_step(f, dt, info, stream=None):
@@ -561,6 +567,15 @@ class Flow:
     def set_state(self, rho, u, stream=None):
         g = self.grid
         vd_flow_set_state(self.h, g._field(rho, 0, "rho"), g._field(u, g.ndim, "u"), stream)
+
+    def set_sources(self, mass_source=None, force=None, stream=None):
+        """Mass source (scalar field) and body force (ndim fields) at the next step's mid-time;
+        None removes a term."""
+        g = self.grid
+        ms = g._field(mass_source, 0, "mass_source") if mass_source is not None else None
+        fo = g._field(force, g.ndim, "force") if force is not None else None
+        vd_flow_set_sources(self.h, ms, fo, stream)
+        self._sources = (ms, fo)   # keep the tensors alive until the copies have run
 
     def state(self, stream=None):
         import torch

@@ -7,8 +7,14 @@
 //     + (dt/2) zeta(rho_h, u), with (dt/2) zeta(rho, w) = w - V~_rho w and a = dt/(2 Re);
 //  4. pressure (Eq. VDINSE.Lrho.num): L~_{rho_h} phi = div u* / dt;
 //  5. projection (Eq. VDINSE.num.proj): u^{n+1} = u* - dt grad phi / rho_h;
-//  6. gradient-form update (Eq. VDINSE.num.gradp.update):
-//     grad p += grad phi - rho_h (dt/2) zeta(rho_h, grad phi / rho_h).
+//  6. pressure update in the scalar form (Eq. VDINSE.num.p.update), stored as its gradient:
+//     grad p += grad phi - grad Lap^+ div(c),  c = rho_h (dt/2) zeta(rho_h, grad phi / rho_h).
+//     The gradient form (Eq. VDINSE.num.gradp.update, grad p += grad phi - c) would keep the
+//     solenoidal part of c, which with variable density accumulates into grad p and costs the
+//     scheme its second order in time at strong viscosity (Sec. 4.1: Re = 1, s = 10).
+// Optional sources (vd_flow_set_sources; Sec. 4.1 adds them so that a manufactured field is an
+// exact solution): a mass source S and a body force F, both at t^{n+1/2}, enter as
+// -dt [u.grad rho - S] in step 1 and +dt F in step 3.
 // Readings: Adams--Bashforth 2 (1.5 N^n - 0.5 N^{n-1}), Euler on the first step; periodic
 // gravity f = -Fr^-1 (1 - <rho_h>/rho_h) e_g.  Both solves are warm-started from the
 // previous solution (u^n for u*, the previous phi for phi).
@@ -27,6 +33,9 @@ struct vd_flow {
   // state
   double *rho, *u, *gradp, *phi, *nrho_prev, *nu_prev;
   int have_prev;
+  // optional sources at t^{n+1/2}
+  double *msrc, *force;
+  int has_msrc, has_force;
   // temporaries
   double *rho_new, *rho_h, *grad, *nrho, *nu, *rhs, *hz, *ustar, *fphi, *w, *sum;
   void* spec;          // 3 spectral fields
@@ -78,17 +87,27 @@ __global__ void k_mass(GridDesc g, double c, double dt, const cpx<double>* __res
     out[e] = mk<double>((a * rh[e].x - dt * ab[e].x) * b, (a * rh[e].y - dt * ab[e].y) * b);
   }
 }
-// predictor right-hand side
+// predictor right-hand side (fext: optional body force, d fields)
 __global__ void k_rhs(long long n, int d, const double* __restrict__ u, const double* __restrict__ ab,
                       const double* __restrict__ gradp, const double* __restrict__ rho_h, const double* __restrict__ hz,
-                      double dt, int gaxis, double inv_fr, double mean_rho, double* __restrict__ out) {
+                      double dt, int gaxis, double inv_fr, double mean_rho, const double* __restrict__ fext,
+                      double* __restrict__ out) {
   EW_LOOP(e, n) {
     const double r = rho_h[e];
     for (int i = 0; i < d; ++i) {
       const long long k = i * n + e;
-      const double f = (i == gaxis) ? -inv_fr * (1.0 - mean_rho / r) : 0.0;
+      double f = (i == gaxis) ? -inv_fr * (1.0 - mean_rho / r) : 0.0;
+      if (fext) f += fext[k];
       out[k] = u[k] + dt * (-ab[k] - gradp[k] / r + f) + hz[k];
     }
+  }
+}
+// out_i = rho a_i
+__global__ void k_mul_by(long long n, int d, const double* __restrict__ a, const double* __restrict__ rho,
+                         double* __restrict__ out) {
+  EW_LOOP(e, n) {
+    const double r = rho[e];
+    for (int i = 0; i < d; ++i) out[i * n + e] = r * a[i * n + e];
   }
 }
 // out_i = a_i / rho
@@ -107,12 +126,11 @@ __global__ void k_project(long long n, int d, const double* __restrict__ us, con
     for (int i = 0; i < d; ++i) out[i * n + e] = us[i * n + e] - dt * gphi[i * n + e] / r;
   }
 }
-// gradp += gphi - rho_h * hz
-__global__ void k_gradp(long long n, int d, const double* __restrict__ gphi, const double* __restrict__ rho_h,
-                        const double* __restrict__ hz, double* __restrict__ gradp) {
+// gradp += gphi - gq  (gq: gradient of the scalar-form correction)
+__global__ void k_gradp(long long n, int d, const double* __restrict__ gphi, const double* __restrict__ gq,
+                        double* __restrict__ gradp) {
   EW_LOOP(e, n) {
-    const double r = rho_h[e];
-    for (int i = 0; i < d; ++i) gradp[i * n + e] += gphi[i * n + e] - r * hz[i * n + e];
+    for (int i = 0; i < d; ++i) gradp[i * n + e] += gphi[i * n + e] - gq[i * n + e];
   }
 }
 // per-block sums (fixed grid: deterministic order)
@@ -163,6 +181,8 @@ static size_t flow_layout(vd_grid* G, const vd_flow_params* p, vd_flow* F, char*
   F->phi = (double*)take(fb);
   F->nrho_prev = (double*)take(fb);
   F->nu_prev = (double*)take(d * fb);
+  F->msrc = (double*)take(fb);
+  F->force = (double*)take(d * fb);
   F->rho_new = (double*)take(fb);
   F->rho_h = (double*)take(fb);
   F->grad = (double*)take(d * fb);
@@ -224,6 +244,8 @@ vd_status vd_flow_create(vd_grid* G, const vd_flow_params* p, void* mem, size_t 
     return fail(VD_ERR_OOM, "flow memory smaller than vd_flow_bytes()");
   }
   F->have_prev = 0;
+  F->has_msrc = 0;
+  F->has_force = 0;
   *out = F;
   return VD_OK;
 }
@@ -242,6 +264,17 @@ vd_status vd_flow_set_state(vd_flow* F, const double* rho, const double* u, vd_s
   VD_CUDA(cudaMemsetAsync(F->gradp, 0, F->d * fb, st));
   VD_CUDA(cudaMemsetAsync(F->phi, 0, fb, st));
   F->have_prev = 0;
+  return VD_OK;
+}
+
+vd_status vd_flow_set_sources(vd_flow* F, const double* mass_source, const double* force, vd_stream stream) {
+  if (!F) return fail(VD_ERR_INVALID_ARG, "null flow");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t fb = F->nr * sizeof(double);
+  if (mass_source) VD_CUDA(cudaMemcpyAsync(F->msrc, mass_source, fb, cudaMemcpyDeviceToDevice, st));
+  if (force) VD_CUDA(cudaMemcpyAsync(F->force, force, F->d * fb, cudaMemcpyDeviceToDevice, st));
+  F->has_msrc = mass_source ? 1 : 0;
+  F->has_force = force ? 1 : 0;
   return VD_OK;
 }
 
@@ -344,6 +377,10 @@ vd_status vd_flow_step(vd_flow* F, double dt, vd_step_info* info, vd_stream stre
     { k_lin<<<b, 256, 0, st>>>(n, 1.5, F->nrho, -0.5, F->nrho_prev, F->rhs); count_launch(); }
     ab = F->rhs;
   }
+  if (F->has_msrc) {   // [u.grad rho]^{n+1/2} - S^{n+1/2}
+    { k_lin<<<b, 256, 0, st>>>(n, 1.0, ab, -1.0, F->msrc, F->fphi); count_launch(); }
+    ab = F->fphi;
+  }
   fwd_transform<double>(G, F->rho, s0, st);
   fwd_transform<double>(G, ab, s1, st);
   const double c = dt / (2.0 * p.Re * p.Sc);
@@ -384,7 +421,7 @@ vd_status vd_flow_step(vd_flow* F, double dt, vd_step_info* info, vd_stream stre
     mean_rho = s / (double)n;
   }
   { k_rhs<<<b, 256, 0, st>>>(n, d, F->u, abu, F->gradp, F->rho_h, F->hz, dt, p.gravity_axis, 1.0 / p.Fr, mean_rho,
-                             F->rhs); count_launch(); }
+                             F->has_force ? F->force : nullptr, F->rhs); count_launch(); }
   VD_CUDA(cudaMemcpyAsync(F->ustar, F->u, d * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   vd_solve_params sp{};
   sp.tol = p.tol;
@@ -409,12 +446,20 @@ vd_status vd_flow_step(vd_flow* F, double dt, vd_step_info* info, vd_stream stre
   // 5. projection
   e = vd_gradient(G, F->phi, F->grad, F->spec, F->spec_bytes, stream);
   if (e != VD_OK) return e;
-  // 6. gradient-form pressure update: w = gphi/rho_h, hz = w - V w
+  // 6. pressure update, scalar form: w = gphi/rho_h, hz = w - V w, c = rho_h hz,
+  //    q = Lap^+ div c (the pressure preconditioner is Lap^+), grad p += gphi - grad q
   { k_div_by<<<b, 256, 0, st>>>(n, d, F->grad, F->rho_h, F->w); count_launch(); }
   e = vd_apply_op(G, VD_OP_VELOCITY, &opp, F->w, F->hz, F->ws, F->ws_bytes, stream);
   if (e != VD_OK) return e;
   { k_lin<<<ewb(n * d), 256, 0, st>>>(n * d, 1.0, F->w, -1.0, F->hz, F->hz); count_launch(); }
-  { k_gradp<<<b, 256, 0, st>>>(n, d, F->grad, F->rho_h, F->hz, F->gradp); count_launch(); }
+  { k_mul_by<<<b, 256, 0, st>>>(n, d, F->hz, F->rho_h, F->hz); count_launch(); }
+  e = vd_divergence(G, F->hz, F->fphi, F->spec, F->spec_bytes, stream);
+  if (e != VD_OK) return e;
+  e = vd_apply_precond(G, VD_OP_PRESSURE, nullptr, F->fphi, F->rhs, F->ws, F->ws_bytes, stream);
+  if (e != VD_OK) return e;
+  e = vd_gradient(G, F->rhs, F->w, F->spec, F->spec_bytes, stream);
+  if (e != VD_OK) return e;
+  { k_gradp<<<b, 256, 0, st>>>(n, d, F->grad, F->w, F->gradp); count_launch(); }
   { k_project<<<b, 256, 0, st>>>(n, d, F->ustar, F->grad, F->rho_h, dt, F->u); count_launch(); }
   // history and new density
   VD_CUDA(cudaMemcpyAsync(F->nrho_prev, F->nrho, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
