@@ -126,6 +126,28 @@ __global__ void k_project(long long n, int d, const double* __restrict__ us, con
     for (int i = 0; i < d; ++i) out[i * n + e] = us[i * n + e] - dt * gphi[i * n + e] / r;
   }
 }
+// gradient part of d vector fields, in Fourier: c_j <- k~_j (k~ . c) / |k~|^2 (0 where |k~| = 0),
+// i.e. grad Lap^+ div c with the discrete D_j = F^-1 diag(i k~_j) F
+__global__ void k_grad_part(GridDesc g, int d, cpx<double>* __restrict__ c) {
+  EW_LOOP(e, g.ncplx) {
+    const long long line = e / g.h0;
+    const int kxi = (int)(e - line * g.h0);
+    const int kyi = (int)(line % g.n1);
+    const int kzi = (int)(line / g.n1);
+    double k[3] = {g.kfac[0] * freq_tilde(kxi, g.n0), 0.0, 0.0};
+    if (g.ndim >= 2) k[1] = g.kfac[1] * freq_tilde(kyi, g.n1);
+    if (g.ndim == 3) k[2] = g.kfac[2] * freq_tilde(kzi, g.n2);
+    double k2 = 0.0, dx = 0.0, dy = 0.0;
+    for (int j = 0; j < d; ++j) {
+      const cpx<double> v = c[(long long)j * g.ncplx + e];
+      k2 += k[j] * k[j];
+      dx += k[j] * v.x;
+      dy += k[j] * v.y;
+    }
+    const double s = (k2 == 0.0) ? 0.0 : 1.0 / k2;
+    for (int j = 0; j < d; ++j) c[(long long)j * g.ncplx + e] = mk<double>(k[j] * s * dx, k[j] * s * dy);
+  }
+}
 // gradp += gphi - gq  (gq: gradient of the scalar-form correction)
 __global__ void k_gradp(long long n, int d, const double* __restrict__ gphi, const double* __restrict__ gq,
                         double* __restrict__ gradp) {
@@ -446,19 +468,21 @@ vd_status vd_flow_step(vd_flow* F, double dt, vd_step_info* info, vd_stream stre
   // 5. projection
   e = vd_gradient(G, F->phi, F->grad, F->spec, F->spec_bytes, stream);
   if (e != VD_OK) return e;
-  // 6. pressure update, scalar form: w = gphi/rho_h, hz = w - V w, c = rho_h hz,
-  //    q = Lap^+ div c (the pressure preconditioner is Lap^+), grad p += gphi - grad q
+  // 6. pressure update, scalar form: w = gphi/rho_h, hz = w - V w, c = rho_h hz, and
+  //    grad p += gphi - grad Lap^+ div c, the gradient part of c taken in Fourier
+  //    (d forward and d inverse transforms; the solve workspace is free here: scratch)
   { k_div_by<<<b, 256, 0, st>>>(n, d, F->grad, F->rho_h, F->w); count_launch(); }
   e = vd_apply_op(G, VD_OP_VELOCITY, &opp, F->w, F->hz, F->ws, F->ws_bytes, stream);
   if (e != VD_OK) return e;
   { k_lin<<<ewb(n * d), 256, 0, st>>>(n * d, 1.0, F->w, -1.0, F->hz, F->hz); count_launch(); }
   { k_mul_by<<<b, 256, 0, st>>>(n, d, F->hz, F->rho_h, F->hz); count_launch(); }
-  e = vd_divergence(G, F->hz, F->fphi, F->spec, F->spec_bytes, stream);
-  if (e != VD_OK) return e;
-  e = vd_apply_precond(G, VD_OP_PRESSURE, nullptr, F->fphi, F->rhs, F->ws, F->ws_bytes, stream);
-  if (e != VD_OK) return e;
-  e = vd_gradient(G, F->rhs, F->w, F->spec, F->spec_bytes, stream);
-  if (e != VD_OK) return e;
+  for (int j = 0; j < d; ++j) fwd_transform<double>(G, F->hz + (size_t)j * n, s0 + (size_t)j * g.ncplx, st);
+  { k_grad_part<<<ewb(g.ncplx), 256, 0, st>>>(g, d, s0); count_launch(); }
+  for (int j = 0; j < d; ++j) {
+    Mult m;
+    inv_transform<double>(G, s0 + (size_t)j * g.ncplx, m, F->w + (size_t)j * n, reinterpret_cast<cpx<double>*>(F->ws),
+                          st);
+  }
   { k_gradp<<<b, 256, 0, st>>>(n, d, F->grad, F->w, F->gradp); count_launch(); }
   { k_project<<<b, 256, 0, st>>>(n, d, F->ustar, F->grad, F->rho_h, dt, F->u); count_launch(); }
   // history and new density
