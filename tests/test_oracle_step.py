@@ -111,3 +111,82 @@ def test_gradient_form_update_loses_second_order():
     assert np.log2(e16[2] / e32[2]) < 1.5
     s32 = _tg_errors(32, "scalar")
     assert e32[2] > 3 * s32[2]
+
+
+# --------------------------------------------------------------------------------------
+# Body force (gravity).  The RTI case of Sec. 4.2 adds -Fr^-1 e_z; on a periodic box the
+# oracle removes its mean weight (the force becomes -Fr^-1 (1 - <rho>/rho) e_z) so that a
+# periodic hydrostatic pressure exists.  Two consequences that do not depend on how the force
+# is written pin it:
+#  (i)  a density that varies only along gravity is in hydrostatic balance: from rest, the
+#       velocity stays zero (to the solve tolerance) step after step.  With the full weight
+#       -Fr^-1 e_z no periodic pressure balances the force and the whole box accelerates by
+#       dt/Fr per step;
+#  (ii) the heavy fluid sinks along gravity (Sec. 4.2: the RTI mushroom grows downward, the
+#       heavier fluid penetrating the lighter one): after one step from rest the density-
+#       weighted vertical velocity sum_x (rho - <rho>) u_z is negative.  A force of the wrong
+#       sign makes the heavy fluid rise.
+# --------------------------------------------------------------------------------------
+
+def _stratified(nx=16, nz=32):
+    """Horizontally uniform density rho(z) = 1.5 + 0.5 cos(pi z) (ratio 2) on a 1 x 2 box,
+    gravity along z.  Smooth on purpose: the Nyquist row of the force (k~ = 0 there, reading
+    c1) is not a gradient and is not balanced; here it is below 1e-12 of the force."""
+    g = sp.Grid((nx, nz), (1.0, 2.0))
+    z = (np.arange(nz) * 2.0 / nz)[:, None]
+    rho = 1.5 + 0.5 * np.cos(np.pi * z)
+    return g, np.array(np.broadcast_to(rho, (nz, nx)), copy=True)
+
+
+def _hydrostatic_speed(steps=3, dt=1e-3, Fr=1.0):
+    g, rho = _stratified()
+    p = st.FlowParams(Re=1000.0, Sc=1.0, Fr=Fr, gravity_axis=1, vel_solver="gmres", pres_solver="cg", tol=1e-12,
+                      maxit=300)
+    s = st.FlowState(rho=rho, u=np.zeros((2,) + g.shape), gradp=np.zeros((2,) + g.shape), phi=np.zeros(g.shape))
+    top = 0.0
+    for _ in range(steps):
+        s = st.step(s, g, dt, p)
+        top = max(top, float(np.max(np.abs(s.u))))
+    return top / (dt / Fr)
+
+
+def _buoyancy_flux_one_step(dt=1e-3):
+    # the RT-like layer with a large interface perturbation (eta amplitude 0.5), so that a good
+    # part of the force is not balanced by pressure and drives motion at once
+    case = inputs.rt_2d(nx=32, nz=64, delta=0.08, s=3.0, eta_amp=0.5)
+    g = sp.Grid(case.n, case.L)
+    p = st.FlowParams(Re=case.Re, Sc=case.Sc, Fr=case.Fr, gravity_axis=case.gravity_axis, vel_solver="gmres",
+                      pres_solver="cg", tol=1e-12, maxit=300)
+    s = st.FlowState(rho=case.rho.copy(), u=np.zeros_like(case.u), gradp=np.zeros_like(case.u),
+                     phi=np.zeros(g.shape))
+    s1 = st.step(s, g, dt, p)
+    w = s1.u[case.gravity_axis]
+    flux = float(np.sum((case.rho - case.rho.mean()) * w))
+    return flux / float(np.sum(np.abs(case.rho - case.rho.mean()) * np.abs(w)))
+
+
+def test_body_force_hydrostatic_rest():
+    assert _hydrostatic_speed() < 1e-8
+
+
+def test_body_force_heavy_fluid_sinks():
+    # normalised flux: -1 if every heavy parcel moves along gravity and every light one against
+    assert _buoyancy_flux_one_step() < -0.1
+
+
+def test_body_force_pins_catch_planted_mistakes(monkeypatch):
+    """Planted in the oracle: the full weight (mean not removed) fails pin (i); the wrong
+    sign fails pin (ii)."""
+    real = st.body_force
+
+    def full_weight(rho_h, grid, p):
+        f = np.zeros((grid.ndim,) + grid.shape)
+        if p.gravity_axis >= 0:
+            f[p.gravity_axis] = -(1.0 / p.Fr)
+        return f
+
+    monkeypatch.setattr(st, "body_force", full_weight)
+    assert _hydrostatic_speed() > 0.5
+    monkeypatch.setattr(st, "body_force", lambda rho_h, grid, p: -real(rho_h, grid, p))
+    assert _hydrostatic_speed() < 1e-8
+    assert _buoyancy_flux_one_step() > 0.1
