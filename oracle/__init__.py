@@ -23,8 +23,9 @@ incompressible variable-density flows", arXiv 2403.06654):
   null space), as in the condition-number study of Sec. 3.1 / 3.2.
 * ``direct1d``  -- an exact, non-iterative solve of the 1D periodic pressure equation.
 
-Everything is float64 numpy.  Transforms use ``numpy.fft`` as a library primitive; the
-module also carries its own O(n^2) DFT written from the definition, used to pin it.
+Everything is float64 numpy.  Transforms use ``scipy.fft`` (complex, all axes) as a library
+primitive, single-threaded unless ``spectral.FFT_WORKERS`` is raised for timing on many
+cores; the module also carries its own O(n^2) DFT written from the definition, used to pin it.
 
 Parity pins: every function here is pinned by ``tests/test_oracle_*.py`` against closed
 forms, exact solves, brute force or invariants (see the test module docstrings).
