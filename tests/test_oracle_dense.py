@@ -114,3 +114,26 @@ def test_constant_density_preconditioned_is_scaled_identity():
     B = dense.assemble(lambda v: sp.precond_pressure(op.apply_pressure(rho, v, g), g), g.shape)
     P = dense.assemble(lambda v: sp.project_range(v, g), g.shape)
     assert np.max(np.abs(B - P / rho0)) < 1e-13
+
+
+def test_golden_tophat1d_is_current():
+    """tests/golden/tophat1d.json (read by the benchmark beside the GPU's 1D top-hat solves) is
+    what its script computes from the oracle now; its eigenvalue ratio meets the rho_max/rho_min
+    bound and its preconditioned SVD condition number is O(1)-O(10) (Sec. 3.2) while the
+    unpreconditioned one is O(10^4)."""
+    import importlib.util
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_tophat1d", os.path.join(here, "make_tophat1d.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    fresh = mod.compute()
+    with open(os.path.join(here, "tophat1d.json")) as fh:
+        stored = json.load(fh)
+    for k in ("kappa_L", "kappa_left_MA", "kappa_right_AM", "eig_ratio_MA"):
+        assert abs(stored[k] - fresh[k]) <= 1e-6 * abs(fresh[k]), k
+    for s in ("cg", "gmres", "rmr"):
+        assert stored["solvers"][s]["iters"] == fresh["solvers"][s]["iters"]
+    assert stored["eig_ratio_MA"] <= stored["eig_bound_rho_ratio"] * (1 + 1e-10)
+    assert stored["kappa_left_MA"] < 100 and stored["kappa_L"] > 1e4
