@@ -78,17 +78,9 @@ DTYPES = {"mixed_dd": "f32 inner / f64 refinement, residual transforms in float-
           "mixed": "f32 inner / f64 refinement and residual", "fp64": "f64"}
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel class,
-# averaged over the launches of one inner iteration in an ncu capture of this workload
-# (profiles/sections_jet256_mixed_dd.md); reported only for the class it was taken for.
-MEASURED_TRAFFIC = {"axis_f32": 230.5e6}
-
-# FP64 arithmetic peak of the GB300 CUDA cores: 1.25 TFLOP/s nominal (recipe table: FP64 is
-# far below B200); counted with an FMA as two flops.
-FP64_PEAK_TFLOPS = 1.25
-# Float-pair arithmetic: 152 SMs x 128 FP32 lanes x 2.07 GHz x 2 = 80.5 TFLOP/s of FP32 FMA; one
-# float-pair add costs 11 FP32 instructions and a multiply 7 (9 on average, an FFT being
-# mostly adds and twiddle products), so one float-pair flop ~ 9 FP32 issue slots.
-DD_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 9 / 1e12
+# averaged over its launches in one ncu capture of this workload, with the capture it came
+# from; reported only for that class, and only while the kernel is unchanged since.
+MEASURED_TRAFFIC = {"axis_f32": (230.5e6, "profiles/sections_jet256_mixed_dd.md (kernel of commit 1b377d5)")}
 
 
 class ClockSampler:
@@ -176,6 +168,47 @@ def sum_over_ranks(v, pg, device):
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ------------------------------------------------------------------------------------------
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+class OracleSolve:
+    """The oracle's own CG solve of the full-size workload (its code unmodified; its library FFT
+    on `workers` threads).  Set-up (inputs, rhs = div u*, operator closures) is not timed; a
+    timed solve covers the range projection of the rhs and the CG iterations.  The operator is
+    wrapped to stamp the time of each application: one per iteration after the initial one."""
+
+    def __init__(self, n, workers):
+        from oracle import operators as op
+        from oracle import spectral as sp
+        from paper_2403_06654_gb300 import inputs
+        sp.FFT_WORKERS = int(workers)
+        self.workers = int(workers)
+        case = inputs.jet_3d(n=n)
+        self.g = sp.Grid(case.n, case.L)
+        self.f = sp.div(list(case.u), self.g)
+        self.A, self.M = op.pressure_system(case.rho, self.g)
+        self.stamps = []
+
+    def solve(self, tol=1e-10, maxit=500):
+        from oracle import solvers as sv
+        from oracle import spectral as sp
+        self.stamps = []
+
+        def A(p):
+            self.stamps.append(time.perf_counter())
+            return self.A(p)
+
+        t0 = time.perf_counter()
+        r = sv.cg(A, self.M, sp.project_range(self.f, self.g), tol=tol, maxit=maxit)
+        t1 = time.perf_counter()
+        # the last operator application is _finish's true residual, not an iteration
+        return {"seconds": t1 - t0, "iters": r.iters, "status": r.status, "relres_true": r.relres_true}
+
+
 def oracle_iteration_seconds(n, reps=1):
     """Time one oracle CG iteration of the full-size workload: operator apply, preconditioner
     apply and the vector updates of PCG (the oracle's own code, unmodified)."""
@@ -204,26 +237,39 @@ def oracle_iteration_seconds(n, reps=1):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the host cores.  A step is one CG iteration of the
+    oracle's 256^3 solve; complete solves run back to back until at least `steps` iterations
+    are timed, after `warmup` iterations of a discarded solve.  value = complete solves per
+    second over the timed solves; ms_per_step = their time per iteration."""
     if rank != 0:
         return 0
-    import numpy as np  # noqa: F401
-
-    iters = 13   # iterations of the oracle's own PCG on this workload to 1e-10 (true relres 2.87e-11)
-    for _ in range(args.warmup):
-        oracle_iteration_seconds(args.n)
-    t = []
-    for _ in range(args.steps):
-        t.append(oracle_iteration_seconds(args.n))
-    per_iter = statistics.median(t)
-    value = 1.0 / (per_iter * iters)
+    from oracle import spectral as sp
+    cores = host_cores()
+    orc = OracleSolve(args.n, cores)
+    if args.warmup > 0:
+        orc.solve(maxit=args.warmup)
+    solves, iters = [], 0
+    t0 = time.perf_counter()
+    while iters < max(args.steps, 1):
+        r = orc.solve()
+        if r["status"] != "converged":
+            raise SystemExit(f"oracle solve failed: {r}")
+        solves.append(r)
+        iters += r["iters"]
+    t = time.perf_counter() - t0
+    value = len(solves) / t
+    sample = (f"each step: one CG iteration of the oracle's {args.n}^3 solve (complete solves back to back: "
+              f"{len(solves)} solves of {solves[0]['iters']} iterations, {t:.1f} s); oracle FFT on {cores} threads "
+              f"(scipy.fft workers), numpy elementwise work on 1")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * iters * 1e3,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / iters * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": WORKLOAD, "solver": "cg", "precision": "fp64"},
-           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                            "sample": f"each step: one oracle CG iteration at {args.n}^3 (operator, preconditioner, "
-                                      f"updates), scaled to {iters} iterations per solve"},
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                            "sample": sample, "seconds_per_solve": t / len(solves),
+                            "relres_true": solves[0]["relres_true"]},
            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    sp.FFT_WORKERS = 1
     print(json.dumps(out), flush=True)
     return 0
 
@@ -257,8 +303,19 @@ def extra_tophat1d(dev):
             ts.append(e0.elapsed_time(e1) * 1e3)
         out[solver] = {"iters": info["iters"], "status": info["status"], "relres": info["relres"],
                        "relres_true": info["relres_true"], "us_per_solve_median": float(np.median(ts))}
-    return {"workload": "1D periodic N=256 top-hat r=3 d=0.05, 16-mode rhs (seed 1), tol 1e-12, x0 = 0",
-            "dtype": "f64", "solvers": out}
+    res = {"workload": "1D periodic N=256 top-hat r=3 d=0.05, 16-mode rhs (seed 1), tol 1e-12, x0 = 0",
+           "dtype": "f64", "solvers": out}
+    # condition numbers of this operator from dense assembly and the oracle's own iteration
+    # counts, stored by tests/golden/make_tophat1d.py
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "tophat1d.json")) as fh:
+            gold = json.load(fh)
+        res["dense_assembly"] = {k: gold[k] for k in ("kappa_L", "kappa_left_MA", "kappa_right_AM", "eig_ratio_MA",
+                                                      "eig_bound_rho_ratio")}
+        res["oracle_iters"] = {k: v["iters"] for k, v in gold["solvers"].items()}
+    except (OSError, KeyError, ValueError):
+        pass
+    return res
 
 
 def extra_krho(dev, G, rho_d, f, x_l, reps=5):
@@ -351,7 +408,7 @@ class _ServeInputs:
 
     def __init__(self, dev):
         self.dev = dev
-        self.rhs, self.dens, self.count = {}, {}, {}
+        self.rhs, self.dens = {}, {}
 
     def add(self, trace):
         import torch
@@ -363,15 +420,14 @@ class _ServeInputs:
                 self.rhs[key] = torch.from_numpy(inputs.smooth_random_field(inst.n, inst.L, 900 + sum(inst.n),
                                                                             kmax=5)).to(dev)
                 self.dens[key] = []
-                self.count[key] = 0
             if len(self.dens[key]) < SERVE_VARIANTS:
                 self.dens[key].append(torch.from_numpy(inst.density()).to(dev))
 
-    def take(self, inst):
+    def take(self, i, inst):
+        """Inputs of trace entry i: a function of the entry alone (its size and index), so that the
+        served request and the same request solved alone get the same density and rhs."""
         key = tuple(inst.n)
-        v = self.count[key] % len(self.dens[key])
-        self.count[key] += 1
-        return self.dens[key][v], self.rhs[key]
+        return self.dens[key][i % len(self.dens[key])], self.rhs[key]
 
 
 def run_trace(vd, trace, src, max_inflight, precision, solver="cg"):
@@ -410,7 +466,7 @@ def run_trace(vd, trace, src, max_inflight, precision, solver="cg"):
                 collect()
                 if dt > 2e-4:
                     time.sleep(min(dt - 1e-4, 1e-3))
-            rho, b = src.take(inst)
+            rho, b = src.take(i, inst)
             q = vd.make_request(i, inst.n, inst.L, rho, b, None, solver=solver, tol=inst.tol, max_it=500,
                                 precision=precision)
             pending[i] = (tuple(inst.n), t_sched, inst.tol)
@@ -433,7 +489,9 @@ def serve_summary(recs, t0, rate):
     big = np.array([r["n"] == (256, 256, 256) for r in recs])
     bad = [r for r in recs if not (r["status"] == 0 and r["relres_true"] <= r["tol"])]
     ok = not bad
-    return {"offered_rate": rate, "requests": len(recs), "solves_per_s": len(recs) / makespan,
+    # only requests that reached their tolerance count as served solves
+    return {"offered_rate": rate, "requests": len(recs), "solves_per_s": (len(recs) - len(bad)) / makespan,
+            "n_failures": len(bad),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max()), "mean": float(lat.mean())},
             "latency_ms_256cubed": ({"p50": float(np.percentile(lat[big], 50)),
@@ -443,8 +501,7 @@ def serve_summary(recs, t0, rate):
             "submit_lag_ms_p99": float(np.percentile(lag, 99)),
             "arrival_span_s": span, "makespan_s": makespan,
             "keeps_up": bool(makespan <= 1.1 * span + 1.0), "all_converged": ok,
-            "failures": [{k: r[k] for k in ("id", "n", "tol", "status", "iters", "relres_true")} for r in bad[:8]],
-            "n_failures": len(bad)}
+            "failures": [{k: r[k] for k in ("id", "n", "tol", "status", "iters", "relres_true")} for r in bad[:8]]}
 
 
 def one_at_a_time(vd, trace, src, precision, dev):
@@ -453,12 +510,12 @@ def one_at_a_time(vd, trace, src, precision, dev):
     grids = {}
     torch.cuda.synchronize()
     t = time.perf_counter()
-    for _, inst in trace:
+    for i, (_, inst) in enumerate(trace):
         key = tuple(inst.n)
         if key not in grids:
             grids[key] = vd.Grid(inst.n, inst.L, device=dev)
         G = grids[key]
-        rho, b = src.take(inst)
+        rho, b = src.take(i, inst)
         G.set_density(rho)
         _, info = G.solve("pressure", "cg", b, tol=inst.tol, max_it=500, precision=precision)
         if info["status"] != "converged":
@@ -610,6 +667,50 @@ def serve_line(args, vd, dev, rank, world, pg):
     return 0
 
 
+def cufft_compare(vd, G, dev, reps=20):
+    """Plain 3D real transforms of the headline grid: the library's passes (vd_fft_r2c /
+    vd_fft_c2r) next to cuFFT (torch.fft.rfftn / irfftn, a comparison baseline outside the
+    product path), double and float, CUDA events over `reps` back-to-back launches each."""
+    import torch
+    shape = G.shape
+    out = {}
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+    x64 = torch.randn(shape, dtype=torch.float64, device=dev, generator=g)
+    for prec, x in (("fp64", x64), ("mixed", x64.float())):
+        xh = G.fft_r2c(x, prec)
+        back = G.fft_c2r(xh, prec)
+        ref = torch.fft.rfftn(x)
+        bref = torch.fft.irfftn(ref, s=shape)
+        rel = float(torch.linalg.vector_norm(xh - ref) / torch.linalg.vector_norm(ref))
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        t = {"ours_r2c_ms": timed(lambda: G.fft_r2c(x, prec, out=xh)),
+             "ours_c2r_ms": timed(lambda: G.fft_c2r(xh, prec, out=back)),
+             "cufft_r2c_ms": timed(lambda: torch.fft.rfftn(x)),
+             "cufft_c2r_ms": timed(lambda: torch.fft.irfftn(ref, s=shape))}
+        t["r2c_ours_over_cufft"] = t["ours_r2c_ms"] / t["cufft_r2c_ms"]
+        t["c2r_ours_over_cufft"] = t["ours_c2r_ms"] / t["cufft_c2r_ms"]
+        t["rel_diff_vs_cufft"] = rel
+        t["dtype"] = "f64" if prec == "fp64" else "f32"
+        out[t["dtype"]] = t
+        del xh, back, ref, bref
+    out["grid"] = list(reversed(shape))
+    out["note"] = ("cuFFT via torch.fft (comparison only, never on the solve path); ours = the x, y and z "
+                   "passes of the library, three HBM round trips per 3D transform")
+    return out
+
+
 # ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
@@ -663,11 +764,14 @@ def main():
     x = torch.zeros_like(f)
     kw = dict(tol=args.tol, max_it=500, restart=30)
 
-    def solve(prec):
-        _, info = G.solve("pressure", args.solver, f, out=x, precision=prec, **kw)
+    def solve(prec, dst=None):
+        _, info = G.solve("pressure", args.solver, f, out=x if dst is None else dst, precision=prec, **kw)
         if info["status"] != "converged" or not (info["relres_true"] <= args.tol):
             raise SystemExit(f"solve failed: {info}")
         return info
+
+    # every timed headline solve writes a buffer of its own, checked after the timed region
+    xs = [torch.empty_like(f) for _ in range(args.steps)]
 
     head = args.precision
     side = "mixed" if head == "mixed_dd" else "mixed_dd"
@@ -695,7 +799,7 @@ def main():
         nvtx.range_push("timed")   # lets a profiler select exactly the timed solves
     ev[0].record(stream)
     for k in range(args.steps):
-        infos.append(solve(head))
+        infos.append(solve(head, xs[k]))
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
     if nvtx is not None:
@@ -730,13 +834,18 @@ def main():
     span = vd.vd_profile_read(vd.PROFILE_SPAN_INNER_F32)
     t_mixed = max_over_ranks(t_mixed, pg, dev)
 
-    # double-precision check of the last headline solution (outside the timed region)
-    fb = f.clone()
-    r64 = fb - G.apply("pressure", x)
-    # the pressure right-hand side is projected onto the range: remove its null-space part
-    r64 = r64 - r64.mean()
-    fmean = fb - fb.mean()
-    verified = float(torch.linalg.vector_norm(r64) / torch.linalg.vector_norm(fmean))
+    # double-precision check of every timed headline solution (outside the timed region): the
+    # residual through the library's FP64 operator; the rhs of this workload is the divergence
+    # of a velocity, whose only null-space content is the mean
+    fmean = f - f.mean()
+    fnorm = float(torch.linalg.vector_norm(fmean))
+    verified_all = []
+    for xk in xs:
+        r64 = f - G.apply("pressure", xk)
+        r64 = r64 - r64.mean()
+        verified_all.append(float(torch.linalg.vector_norm(r64)) / fnorm)
+    verified = max(verified_all)
+    del xs
 
     # ---------------- timed: the other mixed mode ----------------
     ev3 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -786,6 +895,10 @@ def main():
 
     # ---------------- roofline of the dominant kernel class ----------------
     pk, pk_src = peaks()
+    alu = {"fp64_tflops": vd.vd_alu_rate(0) / 1e12, "fp32_tflops": vd.vd_alu_rate(1) / 1e12,
+           "float_pair_tflops": vd.vd_alu_rate(2) / 1e12,
+           "how": "vd_alu_rate: independent FMA (float-pair: multiply + add) chains, 8 blocks x 256 threads per "
+                  "SM, best of three launches; an FMA or a float-pair multiply-add counts 2 flops"}
     # per inner (float) Krylov iteration: float passes + float vector kernels.  Primary: the
     # span pass (each inner solve between two events: host gaps included, no per-kernel events);
     # beside it the sum of the per-kernel event durations of the instrumented pass.
@@ -811,17 +924,19 @@ def main():
     per_launch_ms = d["ms"] / max(d["launches"], 1)
     if name.endswith("f32"):
         achieved = d["alg_bytes"] / (d["ms"] / 1e3) / 1e9
+        tr = MEASURED_TRAFFIC.get(name)
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": MEASURED_TRAFFIC.get(name),
+                "frac": achieved / pk["hbm_gbs"], "traffic": tr[0] if tr else None,
+                "traffic_source": tr[1] if tr else None,
                 "peak_source": f"{pk_src} hbm_gbs (MEASURED_PEAKS.json)" if pk_src == "measured" else "fallback",
                 "alg_bytes_per_launch": d["alg_bytes"] / max(d["launches"], 1), "ms_per_launch": per_launch_ms}
     else:
         achieved = d["alg_flops"] / (d["ms"] / 1e3) / 1e12
-        pk_alu = FP64_PEAK_TFLOPS if name.endswith("f64") else DD_PEAK_TFLOPS
+        pk_alu = alu["fp64_tflops"] if name.endswith("f64") else alu["float_pair_tflops"]
         roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": pk_alu, "unit": "TFLOP/s",
                 "frac": achieved / pk_alu, "traffic": None,
-                "peak_source": ("nominal GB300 FP64 (recipe table), FMA = 2 flops" if name.endswith("f64") else
-                                "float-pair peak derived from the FP32 unit count and clock (see DESIGN.md)"),
+                "peak_source": "measured in this run by vd_alu_rate (" +
+                               ("FP64 FMA" if name.endswith("f64") else "float-pair multiply-add") + ")",
                 "alg_flops_per_launch": d["alg_flops"] / max(d["launches"], 1), "ms_per_launch": per_launch_ms,
                 "hbm_gbs_achieved": d["alg_bytes"] / (d["ms"] / 1e3) / 1e9}
     classes = {vd.PROFILE_CLASSES[c]: {"launches": prof[c]["launches"], "ms": prof[c]["ms"],
@@ -832,7 +947,7 @@ def main():
     extras = None
     if not args.no_extras:
         extras = {"tophat1d": extra_tophat1d(dev), "rt2d": extra_rt2d(dev, args.rt_steps),
-                  "krho256": extra_krho(dev, G, rho_d, f, x)}
+                  "krho256": extra_krho(dev, G, rho_d, f, x), "cufft": cufft_compare(vd, G, dev)}
 
     batch = None
     if not args.no_batch:
@@ -845,11 +960,22 @@ def main():
     # ---------------- CPU oracle baseline (rank 0, N = 1) ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        iters64 = infos64[0]["iters"]
-        t_it = oracle_iteration_seconds(n)
-        cpu = {"value": 1.0 / (t_it * iters64), "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": f"one oracle CG iteration of the {n}^3 solve ({t_it:.1f} s: operator, preconditioner, "
-                         f"updates; numpy single-threaded), scaled to the {iters64} CG iterations of the FP64 solve"}
+        cores = host_cores()
+        orc = OracleSolve(n, cores)
+        r = orc.solve(tol=args.tol)
+        t_it1 = None
+        try:
+            from oracle import spectral as osp
+            osp.FFT_WORKERS = 1
+            t_it1 = oracle_iteration_seconds(n)
+        finally:
+            osp.FFT_WORKERS = 1
+        cpu = {"value": 1.0 / r["seconds"], "unit": "solves/s", "cores": cores, "kind": "oracle",
+               "sample": (f"one complete oracle CG solve of this {n}^3 workload to {args.tol:g} ({r['iters']} "
+                          f"iterations, {r['seconds']:.1f} s, true relres {r['relres_true']:.2e}); library FFT on "
+                          f"{cores} threads, numpy elementwise work on 1"),
+               "seconds_per_solve": r["seconds"], "iters": r["iters"],
+               "one_thread_seconds_per_iteration": t_it1}
 
     total_solves = args.steps * world
     value = total_solves / t_mixed
@@ -866,6 +992,8 @@ def main():
         "iters": infos[-1]["iters"], "outer_iters": infos[-1]["outer_iters"],
         "relres_true_max": max(i["relres_true"] for i in infos),
         "relres_fp64_check": verified,
+        "relres_fp64_check_note": "max over every timed solve of the residual through the FP64 operator",
+        "alu_rates": alu,
         side: {"value": args.side_steps * world / t_side, "unit": "solves/s",
                "ms_per_step": t_side / args.side_steps * 1e3, "iters": infos_side[-1]["iters"],
                "relres_true_max": max(i["relres_true"] for i in infos_side), "dtype": DTYPES[side]},

@@ -52,7 +52,11 @@ typedef enum {
   VD_ERR_BREAKDOWN = 5,      /* Krylov breakdown (zero curvature / zero search direction) */
   VD_ERR_DIVERGED = 6,       /* RMR: monitored residual grew above 1e3 x the best value */
   VD_ERR_NONFINITE = 7,      /* NaN or Inf met in a reduction */
-  VD_ERR_NO_DENSITY = 8      /* an operator was used before vd_density_set */
+  VD_ERR_NO_DENSITY = 8,     /* an operator was used before vd_density_set */
+  VD_ERR_RHS_NOT_IN_RANGE = 9, /* the part of b outside the operator's range exceeds
+                                 vd_solve_params.range_tol ||b|| (only when range_tol > 0) */
+  VD_ERR_TIMEOUT = 10        /* a kernel gave up a bounded wait on its own staged transfers
+                                (vd_solve reports it; the result is not valid) */
 } vd_status;
 
 /*
@@ -73,7 +77,7 @@ typedef enum {
   VD_PREC_FP64 = 0,  /* every transform, product and reduction in IEEE double */
   VD_PREC_MIXED = 1, /* inner Krylov solve with float transforms and preconditioner, double
                         dot products, inside a double iterative-refinement loop whose true
-                        residual uses the double operator (spec precision form) */
+                        residual uses the double operator */
   VD_PREC_MIXED_DD = 2 /* as VD_PREC_MIXED, but the refinement residual b - A x of the pressure
                         operator is formed with float-pair transforms (two floats per value,
                         ~2^-48 relative rounding, on the FP32 pipes; storage stays double).
@@ -93,10 +97,22 @@ typedef struct {
   int restart;       /* GMRES restart length m (1..64), default 30 when <= 0 */
   int use_x0;        /* 1: x holds the initial guess (warm start, Sec. 3.1); 0: start from 0 */
   int precision;     /* vd_precision */
-  double inner_tol;  /* VD_PREC_MIXED: relative tolerance of each inner solve (default 1e-5) */
+  double inner_tol;  /* mixed modes: relative tolerance of each inner float solve (<= 0: 1e-5).
+                        A float CG cannot go much below kappa times the float rounding: an inner CG
+                        solve below 1e-3 whose residual has not halved in 8 iterations, or has
+                        grown 100-fold from its best, ends its sweep and the refinement goes on */
   int check_every;   /* iterations enqueued between host convergence checks (default 1); CG
                         and RMR check one batch behind, so one batch may be launched after
                         convergence: its kernels see the device flag and return at once */
+  int coef_pair;     /* VD_PREC_MIXED(_DD), pressure and K_rho operators: arithmetic of the
+                        variable-coefficient multiply (1/rho, or c of K_rho) inside the inner float
+                        operator.  0 (default): float pairs (hi + lo, ~2^-48, the multiply rounded
+                        once to float) when rho_max / rho_min > 10, plain float otherwise;
+                        1: always float pairs; -1: always plain float */
+  double range_tol;  /* pressure and K_rho right-hand sides lose their part outside the range
+                        (its norm is reported in vd_solve_info.rhs_removed).  0 (default): project
+                        silently; > 0: refuse with VD_ERR_RHS_NOT_IN_RANGE when that part
+                        exceeds range_tol ||b|| (checked before iterating; synchronises stream) */
 } vd_solve_params;
 
 typedef struct {
@@ -108,6 +124,11 @@ typedef struct {
   double* hist;        /* optional host array: monitored relres per iteration (hist[0] = initial) */
   int hist_cap;        /* capacity of hist */
   int hist_len;        /* entries written */
+  double rhs_removed;  /* ||Pi b - b|| / ||b||: the relative part of the right-hand side outside
+                          the operator's range, removed before solving (pressure: the 2^ndim
+                          null-space modes; K_rho: the component along w = rho^-1/2; velocity: 0).
+                          relres and relres_true are relative to ||Pi b|| */
+  int coef_pair;       /* 1 if the inner float operator multiplied by 1/rho (or c) in float pairs */
 } vd_solve_info;
 
 /* Last error message of the calling thread (static storage, never null). */
@@ -182,6 +203,24 @@ vd_status vd_apply_precond(const vd_grid* grid, vd_op op, const vd_op_params* pa
 vd_status vd_solve(const vd_grid* grid, vd_op op, vd_solver solver, const vd_op_params* op_params,
                    const vd_solve_params* params, const double* b, double* x, vd_solve_info* info, void* ws,
                    size_t ws_bytes, vd_stream stream);
+
+/*
+ * Plain transforms of the F-F-F discretisation (Sec. 3: constant-coefficient problems are
+ * diagonal in Fourier space; the transforms are the unit of cost of every apply).
+ * vd_fft_r2c: unnormalised forward DFT over every axis of a physical field (n0 n1 n2 reals)
+ * into its half spectrum ((n0/2+1) n1 n2 complex values, interleaved re/im, layout
+ * [n2][n1][n0/2+1]): out(k) = sum_x in(x) exp(-i k.x).  vd_fft_c2r: the inverse, divided by
+ * N = n0 n1 n2 (the imaginary parts of the self-conjugate modes are ignored).
+ * prec: VD_PREC_FP64 (double fields, double arithmetic), VD_PREC_MIXED (float fields, float
+ * arithmetic), VD_PREC_MIXED_DD (double fields, float-pair arithmetic).  ws: device scratch
+ * of vd_transform_ws_bytes(grid, prec) bytes (unused by the double and float r2c and by 1D
+ * c2r).  in and out (device, caller-owned) may not alias.  Stream-ordered, no synchronisation.
+ */
+size_t vd_transform_ws_bytes(const vd_grid* grid, int prec);
+vd_status vd_fft_r2c(const vd_grid* grid, int prec, const void* in, void* out, void* ws, size_t ws_bytes,
+                     vd_stream stream);
+vd_status vd_fft_c2r(const vd_grid* grid, int prec, const void* in, void* out, void* ws, size_t ws_bytes,
+                     vd_stream stream);
 
 /* out = sum_j D_j u_j (spectral divergence of an ndim-component physical field). */
 vd_status vd_divergence(const vd_grid* grid, const double* u, double* out, void* ws, size_t ws_bytes,
@@ -398,9 +437,12 @@ vd_status vd_autotune_set(int kind, int type, int n, int axis, int dir, int choi
  * the process exits; grids needing more (3D beyond about 64^3, 2D beyond 512 x 1024) are
  * rejected with VD_ERR_INVALID_ARG and a message giving the size.  The first call on a
  * device looks up the array's device address (once per device, with that device current):
- * make that first call before any stream capture.  All calls share the array and it keeps
- * the last call's contents, so calls whose kernels overlap on the GPU race: serialise them.
- * rho must be positive and finite (VD_ERR_INVALID_ARG otherwise; this synchronises stream).
+ * make that first call before any stream capture.  The address is kept for the life of the
+ * process, so the call must not be used across a cudaDeviceReset of that device.  All calls
+ * share the array and it keeps the last call's contents, so calls whose kernels overlap on the
+ * GPU race: serialise them.  rho must be positive and finite (VD_ERR_INVALID_ARG otherwise):
+ * every call reads that check back to the host, so every call synchronises `stream` and
+ * blocks the calling thread until the density has been checked.
  */
 vd_status vd_apply_pressure_noalloc(int ndim, const int n[3], const double L[3], const double* rho, const double* in,
                                     double* out, vd_stream stream);
@@ -421,6 +463,12 @@ vd_status vd_apply_pressure_noalloc(int ndim, const int n[3], const double L[3],
  * vd_profile_read synchronises on the recorded events; vd_profile_reset clears the totals.
  */
 long long vd_launch_count(void);
+/* Measured arithmetic rate of the current GPU (flop/s, an FMA or a float-pair multiply-add
+ * counted as 2 flops): kind 0 FP64 FMA, 1 FP32 FMA, 2 float-pair multiply + add.  Eight
+ * independent dependency chains per thread, 8 blocks of 256 threads per SM, best of three
+ * launches timed with CUDA events on `stream` (synchronised).  The denominators of the
+ * ALU-bound rooflines (double and float-pair transform passes). */
+vd_status vd_alu_rate(int kind, double* flops_per_s, vd_stream stream);
 vd_status vd_profile_enable(int on);
 vd_status vd_profile_reset(void);
 vd_status vd_profile_read(int cls, long long* launches, double* ms, double* alg_bytes, double* alg_flops);

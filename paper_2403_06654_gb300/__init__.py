@@ -23,8 +23,9 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "vd.h")
 
 VD_OK, VD_ERR_INVALID_ARG, VD_ERR_OOM, VD_ERR_CUDA = 0, 1, 2, 3
 VD_ERR_NOT_CONVERGED, VD_ERR_BREAKDOWN, VD_ERR_DIVERGED, VD_ERR_NONFINITE, VD_ERR_NO_DENSITY = 4, 5, 6, 7, 8
+VD_ERR_RHS_NOT_IN_RANGE, VD_ERR_TIMEOUT = 9, 10
 STATUS_NAMES = {0: "converged", 1: "invalid_arg", 2: "oom", 3: "cuda", 4: "max_iter", 5: "breakdown",
-                6: "diverged", 7: "nonfinite", 8: "no_density"}
+                6: "diverged", 7: "nonfinite", 8: "no_density", 9: "rhs_not_in_range", 10: "timeout"}
 STATUS_CODES = {v: k for k, v in STATUS_NAMES.items()}
 VD_OP_PRESSURE, VD_OP_VELOCITY, VD_OP_KRHO = 0, 1, 2
 VD_SOLVER_CG, VD_SOLVER_GMRES, VD_SOLVER_RMR = 0, 1, 2
@@ -47,7 +48,7 @@ class vd_op_params(ctypes.Structure):
 class vd_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_it", ctypes.c_int), ("restart", ctypes.c_int),
                 ("use_x0", ctypes.c_int), ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("check_every", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("coef_pair", ctypes.c_int), ("range_tol", ctypes.c_double)]
 
 
 class vd_flow_params(ctypes.Structure):
@@ -94,7 +95,8 @@ class vd_batch_params(ctypes.Structure):
 class vd_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("status", ctypes.c_int),
                 ("relres", ctypes.c_double), ("relres_true", ctypes.c_double),
-                ("hist", ctypes.POINTER(ctypes.c_double)), ("hist_cap", ctypes.c_int), ("hist_len", ctypes.c_int)]
+                ("hist", ctypes.POINTER(ctypes.c_double)), ("hist_cap", ctypes.c_int), ("hist_len", ctypes.c_int),
+                ("rhs_removed", ctypes.c_double), ("coef_pair", ctypes.c_int)]
 
 
 _lib = None
@@ -116,6 +118,9 @@ _SIGS = {
     "vd_apply_precond": (_I, [_P, _I, ctypes.POINTER(vd_op_params), _P, _P, _P, _SZ, _P]),
     "vd_solve": (_I, [_P, _I, _I, ctypes.POINTER(vd_op_params), ctypes.POINTER(vd_solve_params), _P, _P,
                       ctypes.POINTER(vd_solve_info), _P, _SZ, _P]),
+    "vd_transform_ws_bytes": (_SZ, [_P, _I]),
+    "vd_fft_r2c": (_I, [_P, _I, _P, _P, _P, _SZ, _P]),
+    "vd_fft_c2r": (_I, [_P, _I, _P, _P, _P, _SZ, _P]),
     "vd_divergence": (_I, [_P, _P, _P, _P, _SZ, _P]),
     "vd_gradient": (_I, [_P, _P, _P, _P, _SZ, _P]),
     "vd_autotune_bytes": (_SZ, [_P]),
@@ -152,6 +157,7 @@ _SIGS = {
                              ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
     "vd_server_destroy": (_I, [_P]),
     "vd_launch_count": (ctypes.c_longlong, []),
+    "vd_alu_rate": (_I, [_I, ctypes.POINTER(ctypes.c_double), _P]),
     "vd_profile_enable": (_I, [_I]),
     "vd_profile_reset": (_I, []),
     "vd_profile_read": (_I, [_I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
@@ -243,9 +249,30 @@ def vd_solve(h, op, solver, op_params, params, b, x, info, ws, stream=None):
     st = lib().vd_solve(h, op, solver, ctypes.byref(op_params) if op_params is not None else None,
                         ctypes.byref(params), _ptr(b), _ptr(x), ctypes.byref(info), _ptr(ws), ws.numel(),
                         _stream(stream))
-    if st in (VD_ERR_INVALID_ARG, VD_ERR_OOM, VD_ERR_CUDA, VD_ERR_NO_DENSITY):
+    if st in (VD_ERR_INVALID_ARG, VD_ERR_OOM, VD_ERR_CUDA, VD_ERR_NO_DENSITY, VD_ERR_RHS_NOT_IN_RANGE, VD_ERR_TIMEOUT):
         _check(st)
     return st
+
+
+def vd_transform_ws_bytes(h, prec):
+    return int(lib().vd_transform_ws_bytes(h, prec))
+
+
+def vd_fft_r2c(h, prec, x, out, ws, stream=None):
+    _check(lib().vd_fft_r2c(h, prec, _ptr(x), _ptr(out), _ptr(ws), ws.numel() * ws.element_size(),
+                            _stream(stream)))
+
+
+def vd_fft_c2r(h, prec, x, out, ws, stream=None):
+    _check(lib().vd_fft_c2r(h, prec, _ptr(x), _ptr(out), _ptr(ws), ws.numel() * ws.element_size(),
+                            _stream(stream)))
+
+
+def vd_alu_rate(kind, stream=None):
+    """Measured flop/s of the GPU: kind 0 FP64 FMA, 1 FP32 FMA, 2 float-pair multiply-add."""
+    v = ctypes.c_double()
+    _check(lib().vd_alu_rate(kind, ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def vd_divergence(h, u, out, ws, stream=None):
@@ -486,10 +513,11 @@ class Grid:
         vd_apply_precond(self.h, opc, vd_op_params(a, 1.0) if opc == VD_OP_VELOCITY else None, x, out, ws, stream)
         return out
 
-    def solve_params(self, tol=1e-10, max_it=500, restart=30, use_x0=False, precision="fp64", inner_tol=1e-5,
-                     check_every=1):
+    def solve_params(self, tol=1e-10, max_it=500, restart=30, use_x0=False, precision="fp64", inner_tol=0.0,
+                     check_every=1, coef_pair=0, range_tol=0.0):
         return vd_solve_params(tol=tol, max_it=max_it, restart=restart, use_x0=int(bool(use_x0)),
-                               precision=PRECISIONS[precision], inner_tol=inner_tol, check_every=check_every)
+                               precision=PRECISIONS[precision], inner_tol=inner_tol, check_every=check_every,
+                               coef_pair=int(coef_pair), range_tol=float(range_tol))
 
     def workspace_bytes(self, op, solver, **kw):
         return vd_workspace_bytes(self.h, OPS[op], SOLVERS[solver], self.solve_params(**kw))
@@ -515,10 +543,40 @@ class Grid:
         st = vd_solve(self.h, opc, sc, vd_op_params(a, inv_sc) if opc == VD_OP_VELOCITY else None, p, b, out, info,
                       ws, stream)
         res = {"status": STATUS_NAMES.get(st, st), "iters": info.iters, "outer_iters": info.outer_iters,
-               "relres": info.relres, "relres_true": info.relres_true}
+               "relres": info.relres, "relres_true": info.relres_true, "rhs_removed": info.rhs_removed,
+               "coef_pair": bool(info.coef_pair)}
         if hist is not None:
             res["hist"] = [hist[i] for i in range(info.hist_len)]
         return out, res
+
+    def fft_r2c(self, x, precision="fp64", out=None, stream=None):
+        """Half spectrum (complex tensor, shape (n2, n1, n0/2+1) with trailing axes dropped)
+        of the real field x: unnormalised forward DFT; float32 fields with precision="mixed"."""
+        import torch
+        prec = PRECISIONS[precision]
+        rdt, cdt = (torch.float32, torch.complex64) if prec == VD_PREC_MIXED else (torch.float64, torch.complex128)
+        if x.dtype != rdt or not x.is_cuda or tuple(x.shape) != self.shape:
+            raise VDError(VD_ERR_INVALID_ARG, f"x must be a {rdt} CUDA tensor of shape {self.shape}")
+        hshape = self.shape[:-1] + (self.n[0] // 2 + 1,)
+        if out is None:
+            out = torch.empty(hshape, dtype=cdt, device=self.device)
+        ws = self._workspace(vd_transform_ws_bytes(self.h, prec))
+        vd_fft_r2c(self.h, prec, x, out, ws, stream)
+        return out
+
+    def fft_c2r(self, xh, precision="fp64", out=None, stream=None):
+        """Real field of the half spectrum xh (inverse DFT divided by N)."""
+        import torch
+        prec = PRECISIONS[precision]
+        rdt, cdt = (torch.float32, torch.complex64) if prec == VD_PREC_MIXED else (torch.float64, torch.complex128)
+        hshape = self.shape[:-1] + (self.n[0] // 2 + 1,)
+        if xh.dtype != cdt or not xh.is_cuda or tuple(xh.shape) != hshape:
+            raise VDError(VD_ERR_INVALID_ARG, f"xh must be a {cdt} CUDA tensor of shape {hshape}")
+        if out is None:
+            out = torch.empty(self.shape, dtype=rdt, device=self.device)
+        ws = self._workspace(vd_transform_ws_bytes(self.h, prec))
+        vd_fft_c2r(self.h, prec, xh, out, ws, stream)
+        return out
 
     def divergence(self, u, stream=None):
         import torch

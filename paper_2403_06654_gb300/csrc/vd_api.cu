@@ -198,16 +198,33 @@ vd_status vd_grid_create(int ndim, const int n[3], const double L[3], vd_grid** 
       for (int j = 0; j < g.pz.n; ++j) put(g.pz.tw_off + j, j, g.pz.n);
     for (int k = 0; k <= nn[0] / 2; ++k) put(g.pk_off + k, k, nn[0]);
   }
+  // The tables are uploaded on a private stream that is synchronised before returning.  A plain
+  // cudaMemcpy from pageable memory may return while its DMA is still in flight, and kernels
+  // that a caller then launches on a non-blocking stream (server slots, torch side streams) are
+  // not ordered behind the legacy stream: they could read a partly written table.
+  cudaStream_t up = nullptr;
   cudaError_t e = cudaMalloc(&G->tw_d, tw.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&G->tw_f, twf.size() * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&G->tw_dd, twdd.size() * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemcpy(G->tw_d, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(G->tw_f, twf.data(), twf.size() * sizeof(float), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(G->tw_dd, twdd.data(), twdd.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&G->g.dev_err, 256);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemsetAsync(G->g.dev_err, 0, 256, up);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->tw_d, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, up);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->tw_f, twf.data(), twf.size() * sizeof(float), cudaMemcpyHostToDevice, up);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->tw_dd, twdd.data(), twdd.size() * sizeof(float), cudaMemcpyHostToDevice, up);
+  if (up) {
+    const cudaError_t es = cudaStreamSynchronize(up);
+    if (e == cudaSuccess) e = es;
+    cudaStreamDestroy(up);
+  }
   if (e != cudaSuccess) {
     if (G->tw_d) cudaFree(G->tw_d);
     if (G->tw_f) cudaFree(G->tw_f);
     if (G->tw_dd) cudaFree(G->tw_dd);
+    if (G->g.dev_err) cudaFree(G->g.dev_err);
     delete G;
     return cuda_fail(e, "vd_grid_create");
   }
@@ -220,6 +237,7 @@ vd_status vd_grid_destroy(vd_grid* G) {
   if (G->tw_d) cudaFree(G->tw_d);
   if (G->tw_f) cudaFree(G->tw_f);
   if (G->tw_dd) cudaFree(G->tw_dd);
+  if (G->g.dev_err) cudaFree(G->g.dev_err);
   delete G;
   return VD_OK;
 }
@@ -469,6 +487,7 @@ namespace vd {
 struct SolveLayout {
   KState* ks;
   OState* ost;           // refinement state of graph solves
+  double* removed;       // null-space shares removed from b by the range projection (2^d)
   double* partials;
   unsigned* counter;
   double* hist;
@@ -506,6 +525,7 @@ static SolveLayout solve_layout(const vd_grid* G, vd_op op, int solver, int rest
   L.counter = c.take<unsigned>(sizeof(unsigned) * 4);
   L.hist = c.take<double>(sizeof(double) * (size_t)(std::max(maxit, 1) + 2));
   L.ost = c.take<OState>(sizeof(OState));
+  L.removed = c.take<double>(sizeof(double) * 32);
   L.sym = c.take<double>(nc * 8);
   L.sym_f = nullptr;
   L.bh = c.take<cpx<double>>(len * 16);
@@ -540,16 +560,36 @@ static void apply_cb(const SpecSystem& sys, const void* in, void* out, bool with
   const vd_grid* G = sys.G;
   const T* sym = with_sym ? (const T*)sys.sym : nullptr;
   if (sys.ctx[1] == (void*)2) {
-    apply_krho_spec<T>(G, (const cpx<T>*)in, (cpx<T>*)out, sym, (const T*)sys.ctx[0], (cpx<T>*)sys.ctx[2], done, st);
+    apply_krho_spec<T>(G, (const cpx<T>*)in, (cpx<T>*)out, sym, (const T*)sys.ctx[0], (cpx<T>*)sys.ctx[2], done, st,
+                       sys.ctx[3]);
   } else if (sys.ncomp == 1 && sys.ctx[1] == nullptr) {
-    apply_pressure_spec<T>(G, (const cpx<T>*)in, (cpx<T>*)out, sym, (const T*)sys.ctx[0], (cpx<T>*)sys.ctx[2], done, st);
+    apply_pressure_spec<T>(G, (const cpx<T>*)in, (cpx<T>*)out, sym, (const T*)sys.ctx[0], (cpx<T>*)sys.ctx[2], done,
+                           st, sys.ctx[3]);
   } else {
     apply_velocity_spec<T>(G, (const cpx<T>*)in, (cpx<T>*)out, sym, sys.a, sys.inv_sc, (cpx<T>*)sys.ctx[2], done, st);
   }
 }
 
+// Density ratio above which the inner float operator of a mixed solve multiplies by 1/rho (or
+// the K_rho coefficient) in float-pair arithmetic: the multiply by a coefficient spanning a
+// wide range is kept at double-like accuracy while transforms and vectors stay float.
+constexpr double kPairRatio = 10.0;
+
+// Relative tolerance of the inner float solves of the refinement when the caller leaves it to
+// the library.  At high density ratios a float CG can stall above it (near kappa times the
+// float rounding; a ratio of 28.6 on a 512^2 slab stalled at 1.3e-5): the stall test of the
+// guarded inner solves (KState::guard) then ends the sweep and the refinement goes on.
+static double auto_inner_tol(const vd_grid*) { return 1e-5; }
+
+static bool coef_in_pairs(const vd_grid* G, vd_op op, int coef_pair) {
+  if (op == VD_OP_VELOCITY) return false;   // the velocity bracket multiplies by 1/rho in double
+  if (coef_pair != 0) return coef_pair > 0;
+  return G->rho_max > kPairRatio * G->rho_min;
+}
+
 template <typename T>
-static SpecSystem make_system(const vd_grid* G, vd_op op, const vd_op_params* p, const void* sym, void* tmp) {
+static SpecSystem make_system(const vd_grid* G, vd_op op, const vd_op_params* p, const void* sym, void* tmp,
+                              int coef_pair = 0) {
   SpecSystem s{};
   s.G = G;
   s.ncomp = op_ncomp(G, op);
@@ -566,6 +606,9 @@ static SpecSystem make_system(const vd_grid* G, vd_op op, const vd_op_params* p,
     s.ctx[1] = (op == VD_OP_VELOCITY) ? (void*)1 : nullptr;
   }
   s.ctx[2] = tmp;
+  s.ctx[3] = nullptr;
+  if (sizeof(T) == 4 && coef_in_pairs(G, op, coef_pair))
+    s.ctx[3] = (op == VD_OP_KRHO) ? (void*)G->kc_dd : (void*)G->rinv_s_dd;
   s.a = p ? p->a : 0.0;
   s.inv_sc = p ? p->inv_sc : 1.0;
   return s;
@@ -657,7 +700,7 @@ vd_status enqueue_solve_graph(const vd_grid* G, vd_op op, vd_solver solver, cons
     si.restart = restart;
     si.check_every = 1;
     si.x_zero = 1;
-    e = refine_enqueue_graph(sys64, sys32, &resid_cb, &rc, si, tol, 1e-5, maxit, L.bh, L.xh, L.rh, L.bh_f, L.xh_f,
+    e = refine_enqueue_graph(sys64, sys32, &resid_cb, &rc, si, tol, auto_inner_tol(G), maxit, L.bh, L.xh, L.rh, L.bh_f, L.xh_f,
                              L.vecs, kw, L.ost, info, st, body[0], body[1], body[2]);
     if (e != VD_OK) return e;
     if (dd) inv_transform_dd(G, L.xh, x, L.tmp, st);
@@ -734,6 +777,48 @@ vd_status vd_apply_precond(const vd_grid* G, vd_op op, const vd_op_params* p, co
   return VD_OK;
 }
 
+size_t vd_transform_ws_bytes(const vd_grid* G, int prec) {
+  if (!G) return 0;
+  const size_t el = (prec == VD_PREC_MIXED) ? sizeof(cpx<float>) : sizeof(cpx<double>);
+  return align256((size_t)G->g.ncplx * el);
+}
+
+vd_status vd_fft_r2c(const vd_grid* G, int prec, const void* in, void* out, void* ws, size_t ws_bytes,
+                     vd_stream stream) {
+  if (!G || !in || !out) return fail(VD_ERR_INVALID_ARG, "null argument");
+  if (prec != VD_PREC_FP64 && prec != VD_PREC_MIXED && prec != VD_PREC_MIXED_DD)
+    return fail(VD_ERR_INVALID_ARG, "unknown precision mode");
+  if (in == out) return fail(VD_ERR_INVALID_ARG, "in and out must not alias");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == VD_PREC_FP64) {
+    fwd_transform<double>(G, (const double*)in, (cpx<double>*)out, st);
+  } else if (prec == VD_PREC_MIXED) {
+    fwd_transform<float>(G, (const float*)in, (cpx<float>*)out, st);
+  } else {
+    if (!ws || ws_bytes < vd_transform_ws_bytes(G, prec)) return fail(VD_ERR_OOM, "transform workspace too small");
+    fwd_transform_dd(G, (const double*)in, (cpx<double>*)out, ws, st);
+  }
+  VD_CUDA(cudaGetLastError());
+  return VD_OK;
+}
+
+vd_status vd_fft_c2r(const vd_grid* G, int prec, const void* in, void* out, void* ws, size_t ws_bytes,
+                     vd_stream stream) {
+  if (!G || !in || !out) return fail(VD_ERR_INVALID_ARG, "null argument");
+  if (prec != VD_PREC_FP64 && prec != VD_PREC_MIXED && prec != VD_PREC_MIXED_DD)
+    return fail(VD_ERR_INVALID_ARG, "unknown precision mode");
+  if (in == out) return fail(VD_ERR_INVALID_ARG, "in and out must not alias");
+  if (G->g.ndim > 1 && (!ws || ws_bytes < vd_transform_ws_bytes(G, prec)))
+    return fail(VD_ERR_OOM, "transform workspace too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  Mult m;
+  if (prec == VD_PREC_FP64) inv_transform<double>(G, (const cpx<double>*)in, m, (double*)out, (cpx<double>*)ws, st);
+  else if (prec == VD_PREC_MIXED) inv_transform<float>(G, (const cpx<float>*)in, m, (float*)out, (cpx<float>*)ws, st);
+  else inv_transform_dd(G, (const cpx<double>*)in, (double*)out, ws, st);
+  VD_CUDA(cudaGetLastError());
+  return VD_OK;
+}
+
 vd_status vd_divergence(const vd_grid* G, const double* u, double* out, void* ws, size_t ws_bytes, vd_stream stream) {
   if (!G || !u || !out || !ws) return fail(VD_ERR_INVALID_ARG, "null argument");
   cudaStream_t st = (cudaStream_t)stream;
@@ -794,6 +879,9 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
   size_t need = 0;
   SolveLayout L = solve_layout(G, op, solver, restart, prm->max_it, prm->precision, ws, &need);
   if (ws_bytes < need) return fail(VD_ERR_OOM, "workspace too small");
+  // small 1D pressure problems: the whole solve in one kernel launch (vd_small.cu)
+  if (!(prm->range_tol > 0.0) && small_solve_eligible(G, op, solver, prm->precision, restart))
+    return small_solve_1d(G, solver, prm, restart, b, x, info, L.ks, L.hist, std::max(prm->max_it, 1) + 2, st);
   const GridDesc& g = G->g;
   const int ncomp = op_ncomp(G, op);
   const long long len = g.ncplx * ncomp;
@@ -807,7 +895,12 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
   const bool dd_io = prm->precision == VD_PREC_MIXED_DD && op != VD_OP_VELOCITY;
   if (dd_io) fwd_transform_dd(G, b, L.bh, L.tmp, st);
   else fwd_all(G, ncomp, b, L.bh, st);
-  if (op == VD_OP_PRESSURE) spec_project<double>(G, 1, L.bh, st);
+  // range projection (reading c4): the removed part's squared norm, in the weighted spectral
+  // norm of the solver, is kept in removed2 (pressure: read back with the results)
+  const int ncorner = 1 << g.ndim;
+  double removed2 = 0.0;
+  double removed_host[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (op == VD_OP_PRESSURE) spec_project<double>(G, 1, L.bh, st, L.removed);
   KWork kw{L.ks, L.partials, L.counter, L.hist};
   if (op == VD_OP_KRHO) {
     // remove the component along w = rho^-1/2 (the range of K~ is w-orthogonal)
@@ -817,6 +910,34 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
     s1.h0 = g.h0;
     const double d = spec_dot_host<double>(s1, L.bh, G->kw_hat, kw, st);
     spec_axpy<double>(len, -d, G->kw_hat, L.bh, st);
+    removed2 = d * d;   // w^ has unit weighted norm
+  }
+  SpecSystem sysn{};
+  sysn.G = G;
+  sysn.len = len;
+  sysn.h0 = g.h0;
+  if (prm->range_tol > 0.0 && op != VD_OP_VELOCITY) {
+    if (op == VD_OP_PRESSURE) {
+      VD_CUDA(cudaMemcpyAsync(removed_host, L.removed, sizeof(double) * ncorner, cudaMemcpyDeviceToHost, st));
+      VD_CUDA(cudaStreamSynchronize(st));
+      for (int k = 0; k < ncorner; ++k) removed2 += removed_host[k];
+    }
+    const double kept2 = spec_norm2_host<double>(sysn, L.bh, kw, st);
+    if (removed2 > prm->range_tol * prm->range_tol * (kept2 + removed2)) {
+      if (info) {
+        info->iters = 0;
+        info->outer_iters = 0;
+        info->status = VD_ERR_RHS_NOT_IN_RANGE;
+        info->relres = info->relres_true = 0.0;
+        info->hist_len = 0;
+        info->rhs_removed = std::sqrt(removed2 / (kept2 + removed2));
+        info->coef_pair = 0;
+      }
+      char buf[160];
+      std::snprintf(buf, sizeof buf, "right-hand side outside the range: ||Pi b - b|| / ||b|| = %.3e > range_tol",
+                    std::sqrt(removed2 / (kept2 + removed2)));
+      return fail(VD_ERR_RHS_NOT_IN_RANGE, buf);
+    }
   }
   if (prm->use_x0) {
     if (dd_io) fwd_transform_dd(G, x, L.xh, L.tmp, st);
@@ -839,6 +960,7 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
   const int hcap = hh ? std::min(info->hist_cap, prm->max_it + 2) : 0;
   SpecSystem sys64 = make_system<double>(G, op, opp, L.sym, L.tmp);
   bool x_phys_current = false;   // x already holds the inverse transform of the final L.xh
+  bool coef_pair_used = false;
   int outer = 0;
   double relres_true = 0.0;
   if (prm->precision == VD_PREC_FP64) {
@@ -847,7 +969,8 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
   } else {
     // iterative refinement: r = b - A64 x; inner float solve A32 d = r/|r|; x += |r| d
     fill_symbol<float>(G, symkind, opp ? opp->a : 0.0, L.sym_f, st);
-    SpecSystem sys32 = make_system<float>(G, op, opp, L.sym_f, L.tmp_f);
+    SpecSystem sys32 = make_system<float>(G, op, opp, L.sym_f, L.tmp_f, prm->coef_pair);
+    coef_pair_used = sys32.ctx[3] != nullptr;
     // residual operator of the refinement: double, or float-pair transforms (pressure)
     const bool use_dd = prm->precision == VD_PREC_MIXED_DD && op != VD_OP_VELOCITY;
     // With want_phys the float-pair pressure residual also writes the physical-space iterate
@@ -880,7 +1003,7 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
     int hlen = 0;
     if (hh && hcap > 0) hh[hlen++] = bnorm > 0 ? rnorm / bnorm : 0.0;
     res.status = VD_ERR_NOT_CONVERGED;
-    const double itol = prm->inner_tol > 0 ? prm->inner_tol : 1e-5;
+    const double itol = prm->inner_tol > 0 ? prm->inner_tol : auto_inner_tol(G);
     const int max_outer = 20;
     for (;;) {
       // a non-finite norm is reported as such (NaN > 0 is false: it must not read as a zero rhs)
@@ -905,6 +1028,7 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
       si.tol = std::max(itol, 0.5 * prm->tol / rel);
       si.maxit = prm->max_it - total;
       si.x_zero = 1;
+      si.guard = kInnerGuard;
       SolveOut ri{0, 0, 0.0};
       std::vector<double> ih;
       const int icap = hh ? std::min(std::max(0, hcap - hlen) + 1, prm->max_it + 2) : 0;
@@ -947,13 +1071,29 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
     if (info) info->hist_len = hh ? std::min(hcap, res.iters + 1) : 0;
   }
   VD_CUDA(cudaGetLastError());
+  if (op == VD_OP_PRESSURE && !(prm->range_tol > 0.0))
+    VD_CUDA(cudaMemcpyAsync(removed_host, L.removed, sizeof(double) * ncorner, cudaMemcpyDeviceToHost, st));
+  int dev_err = 0;
+  if (g.dev_err) VD_CUDA(cudaMemcpyAsync(&dev_err, g.dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   VD_CUDA(cudaStreamSynchronize(st));
+  if (dev_err) {
+    VD_CUDA(cudaMemsetAsync(g.dev_err, 0, sizeof(int), st));
+    VD_CUDA(cudaStreamSynchronize(st));
+    return fail(VD_ERR_TIMEOUT, "a transform pass gave up waiting for its staged input (bounded wait); "
+                                "the result is not valid");
+  }
+  if (op == VD_OP_PRESSURE && !(prm->range_tol > 0.0))
+    for (int k = 0; k < ncorner; ++k) removed2 += removed_host[k];
   if (info) {
     info->iters = res.iters;
     info->outer_iters = outer;
     info->status = res.status;
     info->relres = res.relres;
     info->relres_true = relres_true;
+    double kept2 = 0.0;
+    if (removed2 > 0.0) kept2 = spec_norm2_host<double>(sysn, L.bh, kw, st);
+    info->rhs_removed = removed2 > 0.0 ? std::sqrt(removed2 / (kept2 + removed2)) : 0.0;
+    info->coef_pair = coef_pair_used ? 1 : 0;
   }
   if (res.status != VD_OK) {
     char buf[160];

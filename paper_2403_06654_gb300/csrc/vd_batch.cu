@@ -202,6 +202,8 @@ vd_status vd_batch_run(vd_batch* B, vd_stream stream) {
 vd_status vd_batch_info(vd_batch* B, int index, vd_solve_info* vel, vd_solve_info* pres) {
   if (!B || index < 0 || index >= (int)B->items.size()) return vd::fail(VD_ERR_INVALID_ARG, "bad batch index");
   double rec[2 * kInfo];
+  // the graph may run on a non-blocking stream, which a legacy-stream copy does not wait for
+  VD_CUDA(cudaDeviceSynchronize());
   VD_CUDA(cudaMemcpy(rec, B->info + (size_t)index * 2 * kInfo, sizeof rec, cudaMemcpyDeviceToHost));
   auto fill = [](const double* r, vd_solve_info* o) {
     if (!o) return;

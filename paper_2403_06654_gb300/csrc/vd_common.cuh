@@ -89,6 +89,7 @@ struct GridDesc {
   FftPlan py;        // length n1 (ndim >= 2)
   FftPlan pz;        // length n2 (ndim == 3)
   int pk_off;        // packing twiddles W_{n0}^k, k = 0..n0/2
+  int* dev_err = nullptr;   // device error word of the grid (a bounded wait gave up), or null
 };
 
 // signed integer frequency of index m on an axis of n points, with the Nyquist index -> 0

@@ -84,9 +84,11 @@ void inv_transform(const vd_grid* G, const cpx<T>* in, const Mult& m, T* out, cp
 
 // Pressure operator in spectral space: out = L~ (S in) with S = symarr (if non-null) else 1.
 // tmp: 3 spectral fields (3D), 2 (2D), 0 (1D).  done: optional early-exit flag.
+// wf_pair (float only, may be null): 1/(N rho) as float pairs, multiplied in float-pair
+// arithmetic instead of rinv_s (the inner operator of mixed solves at high density ratios).
 template <typename T>
 void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, const T* rinv_s,
-                         cpx<T>* tmp, const int* done, cudaStream_t st);
+                         cpx<T>* tmp, const int* done, cudaStream_t st, const void* wf_pair = nullptr);
 
 // Pressure operator with float-pair transforms: double spectral fields in and out (no
 // preconditioner), float-pair intermediates in tmp (3 spectral fields of 16 bytes per element).
@@ -113,7 +115,7 @@ int pressure_tmp_fields(int ndim);
 // coef_s: c/N (physical, type T).  tmp: one spectral field (2D/3D), none (1D).
 template <typename T>
 void apply_krho_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, const T* coef_s,
-                     cpx<T>* tmp, const int* done, cudaStream_t st);
+                     cpx<T>* tmp, const int* done, cudaStream_t st, const void* wf_pair = nullptr);
 // the same with float-pair transforms: double spectral fields in and out, no preconditioner
 void apply_krho_spec_dd(const vd_grid* G, const cpx<double>* in, cpx<double>* out, void* tmp, const int* done,
                         cudaStream_t st);
@@ -124,6 +126,13 @@ int krho_tmp_fields(int ndim);
 // full-wavenumber Laplacian -|k|^2
 template <typename T>
 void fill_symbol(const vd_grid* G, int kind, double a, T* out, cudaStream_t st);
+
+// single-launch solves of 1D pressure problems in FP64 (vd_small.cu): eligibility, and the
+// solve itself (out_dev: a result record in device memory, hist_dev: hist_cap doubles)
+bool small_solve_eligible(const vd_grid* G, vd_op op, int solver, int precision, int restart);
+vd_status small_solve_1d(const vd_grid* G, int solver, const vd_solve_params* prm, int restart, const double* b,
+                         double* x, vd_solve_info* info, void* out_dev, double* hist_dev, int hist_cap,
+                         cudaStream_t st);
 
 // one solve recorded into the capture of st (see vd_api.cu); body: 3 streams for the
 // conditional bodies (one is enough in FP64)

@@ -145,6 +145,8 @@ __device__ void epilogue(int epi, const double (&t)[NV], KState* ks, double* his
       const double rel = sqrt(t[1] / t[0]);
       ks->relres = rel;
       ks->best = rel;
+      ks->ref = rel;
+      ks->ref_it = 0;
       ks->rr = t[1];
       if (epi == EPI_INIT_CG) ks->rz = t[NV > 2 ? 2 : 0];
       record(ks, hist, rel);
@@ -184,10 +186,24 @@ __device__ void epilogue(int epi, const double (&t)[NV], KState* ks, double* his
         finish(ks, 0);
         return;
       }
-      // residual-growth divergence test: RMR only (CG's residual norm is not monotone)
+      // residual-growth divergence test: RMR only (CG's residual norm is not monotone), except
+      // for guarded CG solves that have already converged well below their start
       if (epi == EPI_RMR_UPDATE && rel > 1e3 * ks->best) {
         finish(ks, VD_ERR_DIVERGED);
         return;
+      }
+      if (epi == EPI_CG_UPDATE && ks->guard > 0) {
+        if (rel < 0.5 * ks->ref) {
+          ks->ref = rel;
+          ks->ref_it = ks->iters;
+        } else if (ks->best < 1e-3 && ks->iters - ks->ref_it >= kStallWindow) {
+          finish(ks, VD_ERR_DIVERGED);   // stalled at its attainable accuracy
+          return;
+        }
+        if (ks->best < 1e-3 && rel > (double)ks->guard * ks->best) {
+          finish(ks, VD_ERR_DIVERGED);
+          return;
+        }
       }
       ks->best = fmin(ks->best, rel);
       if (epi == EPI_CG_UPDATE) {
@@ -656,7 +672,7 @@ __global__ void k_axpy_f2d(long long len, double a, const OState* o, const cpx<f
   }
 }
 template <typename T>
-__global__ void k_project(GridDesc g, int ncomp, cpx<T>* v) {
+__global__ void k_project(GridDesc g, int ncomp, cpx<T>* v, double* removed) {
   const int t = threadIdx.x;   // one thread per corner mode and component
   const int d = g.ndim;
   const int ncorner = 1 << d;
@@ -666,7 +682,10 @@ __global__ void k_project(GridDesc g, int ncomp, cpx<T>* v) {
   const int ky = (d >= 2 && (m & 2)) ? g.n1 / 2 : 0;
   const int kz = (d >= 3 && (m & 4)) ? g.n2 / 2 : 0;
   const long long e = ((long long)kz * g.n1 + ky) * g.h0 + kx;
-  v[(long long)c * g.ncplx + e] = mk<T>(T(0), T(0));
+  cpx<T>* q = v + (long long)c * g.ncplx + e;
+  // the removed coefficient's share of the squared norm (Parseval weight 1: kx is 0 or n0/2)
+  if (removed) removed[t] = (double)q->x * (double)q->x + (double)q->y * (double)q->y;
+  *q = mk<T>(T(0), T(0));
 }
 
 static inline Ix mkix(long long len, int h0, long long nc, int blocks, int threads) {
@@ -697,8 +716,8 @@ void spec_sub(long long len, const void* b, const void* q, void* r, cudaStream_t
   { ProfScope ps_(sizeof(T) == 4 ? PC_VEC32 : PC_VEC64, st, (double)3 * len * sizeof(cpx<T>), 0.0); k_sub<T><<<ew_blocks(len), 256, 0, st>>>(len, (const cpx<T>*)b, (const cpx<T>*)q, (cpx<T>*)r, nullptr); }
 }
 template <typename T>
-void spec_project(const vd_grid* G, int ncomp, void* v, cudaStream_t st) {
-  { k_project<T><<<1, 32, 0, st>>>(G->g, ncomp, (cpx<T>*)v); count_launch(); }
+void spec_project(const vd_grid* G, int ncomp, void* v, cudaStream_t st, double* removed) {
+  { k_project<T><<<1, 32, 0, st>>>(G->g, ncomp, (cpx<T>*)v, removed); count_launch(); }
 }
 
 template <typename T>
@@ -760,7 +779,7 @@ size_t krylov_vec_bytes(const SpecSystem& sys, int solver, int restart) {
 
 struct KHead {   // host mirror of the first fields of KState
   double bb, tol2bb, rr, rz, pq, alpha, beta, rw, ww, best, relres;
-  int iters, maxit, status, done, hist_cap, m, k, cycle_done, pad;
+  int iters, maxit, status, done, hist_cap, m, k, cycle_done, guard;
 };
 static_assert(offsetof(KState, bb) == 0, "layout");
 
@@ -867,6 +886,7 @@ vd_status krylov_solve(const SpecSystem& sys, const SolveOpts& o, const void* b,
   h0s.status = KS_RUNNING;
   h0s.hist_cap = host_hist_cap > 0 ? std::min(host_hist_cap, 1 << 20) : 0;
   h0s.m = m;
+  h0s.guard = o.guard;
   VD_CUDA(cudaMemcpyAsync(kw.ks, &h0s, sizeof(KHead), cudaMemcpyHostToDevice, st));
   VD_CUDA(cudaMemsetAsync(kw.counter, 0, sizeof(unsigned), st));
 
@@ -1046,6 +1066,7 @@ __global__ void k_ks_reset_dev(KState* ks, const OState* o, int m, cudaGraphCond
   h->maxit = o->maxit - o->total;
   h->status = KS_RUNNING;
   h->m = m;
+  h->guard = kInnerGuard;
   ks->dtol = o->itol;
 }
 
@@ -1433,8 +1454,8 @@ template void spec_axpy<double>(long long, double, const void*, void*, cudaStrea
 template void spec_axpy<float>(long long, double, const void*, void*, cudaStream_t);
 template void spec_sub<double>(long long, const void*, const void*, void*, cudaStream_t);
 template void spec_sub<float>(long long, const void*, const void*, void*, cudaStream_t);
-template void spec_project<double>(const vd_grid*, int, void*, cudaStream_t);
-template void spec_project<float>(const vd_grid*, int, void*, cudaStream_t);
+template void spec_project<double>(const vd_grid*, int, void*, cudaStream_t, double*);
+template void spec_project<float>(const vd_grid*, int, void*, cudaStream_t, double*);
 template double spec_dot_host<double>(const SpecSystem&, const void*, const void*, const KWork&, cudaStream_t);
 template double spec_norm2_host<double>(const SpecSystem&, const void*, const KWork&, cudaStream_t);
 template double spec_norm2_host<float>(const SpecSystem&, const void*, const KWork&, cudaStream_t);

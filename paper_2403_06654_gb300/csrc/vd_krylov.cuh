@@ -15,6 +15,8 @@ namespace vd {
 constexpr int kMaxRestart = 64;
 constexpr int kRedBlocks = 608;   // fixed block count of every reduction (deterministic; 4 per SM on 152 SMs)
 constexpr int kRedThreads = 256;
+constexpr int kInnerGuard = 100;  // divergence guard of the inner float CG solves (see KState::guard)
+constexpr int kStallWindow = 8;   // iterations without a halving of the residual that count as a stall
 
 // device-resident scalar state of one solve
 struct KState {
@@ -25,13 +27,18 @@ struct KState {
   double relres;
   int iters, maxit, status, done;
   int hist_cap;
-  // GMRES
-  int m, k, cycle_done, pad;
+  // GMRES (m, k, cycle_done); guard > 0 (the inner float CG solves of the refinement): past
+  // its attainable accuracy a float CG stalls and then drifts away, so a guarded CG solve that
+  // is below 1e-3 stops (status VD_ERR_DIVERGED, the refinement goes on) when its monitored
+  // residual has not halved for kStallWindow iterations, or exceeds guard x its best value
+  int m, k, cycle_done, guard;
   double beta0;
   double H[(kMaxRestart + 1) * kMaxRestart];   // column-major: H[i + j*(m+1)]
   double cs[kMaxRestart], sn[kMaxRestart], gv[kMaxRestart + 1], y[kMaxRestart];
   double h1[kMaxRestart + 1], h2[kMaxRestart + 1];
   double dtol;     // tolerance read by the epilogues when the launch passes a negative one
+  double ref;      // guarded CG: residual at the last halving of the monitored residual ...
+  int ref_it;      // ... and its iteration (stall test)
 };
 
 // device-resident state of an iterative-refinement loop recorded into a graph
@@ -76,6 +83,7 @@ struct SolveOpts {
   int restart;
   int check_every;
   int x_zero;   // x is known to be zero on entry: the first residual is b (no operator apply)
+  int guard = 0;   // KState::guard of the solve
   const OState* dev_outer = nullptr;   // graph form: tolerance and iteration budget from the device
 };
 
@@ -130,9 +138,10 @@ double spec_norm2_host(const SpecSystem& sys, const void* v, const KWork& kw, cu
 // weighted inner product (a, b) of two spectral vectors, returned to the host
 template <typename T>
 double spec_dot_host(const SpecSystem& sys, const void* a, const void* b, const KWork& kw, cudaStream_t st);
-// zero the 2^d null-space coefficients of each component
+// zero the 2^d null-space coefficients of each component; removed (device, may be null,
+// 2^d ncomp doubles) receives each removed coefficient's share of the squared weighted norm
 template <typename T>
-void spec_project(const vd_grid* G, int ncomp, void* v, cudaStream_t st);
+void spec_project(const vd_grid* G, int ncomp, void* v, cudaStream_t st, double* removed = nullptr);
 // refinement steps on double vectors, each one pass: out = float(in * s) (narrowed right-hand
 // side of the inner solve); y += a * double(xf) (correction); r = b - q returning |r|^2
 // (weighted) to the host

@@ -23,14 +23,17 @@
 
 namespace vd {
 
-// 32 MiB: enough for 3D grids up to 64^3, 2D up to 512 x 1024, any 1D length.
+// 32 MiB: enough for 3D grids up to 64^3, 2D up to 512 x 1024 and 1D lengths up to 1024 (the
+// axis-length limit every entry point applies).
 constexpr size_t kNoAllocScratchBytes = 32ull << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 static std::mutex g_na_mu;
 static void* g_na_ptr[64] = {nullptr};
 
-// device address of the scratch array on the current device (set up once per device)
+// device address of the scratch array on the current device, looked up once per device and
+// kept for the life of the process (a cudaDeviceReset of that device would leave it stale:
+// the entry point must not be used across one)
 static vd_status noalloc_scratch(void** out) {
   int dev = 0;
   VD_CUDA(cudaGetDevice(&dev));

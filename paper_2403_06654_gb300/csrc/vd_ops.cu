@@ -197,9 +197,14 @@ void inv_transform_dd(const vd_grid* G, const cpx<double>* in, double* out, void
 // conv: the float-pair instantiation reads `in` and writes `out` as double fields
 // phys_out (may be null): the fused x pass also writes the inverse transform of `in` there,
 // equal bit for bit to the separate inverse transform when the apply is unpreconditioned
+// wf_pair (float programs, may be null): 1/(N rho) as float pairs, used instead of rinv_s so
+// that the multiply runs in float-pair arithmetic (high density ratios)
 template <typename T>
 static void pressure_impl(const vd_grid* G, const void* in, void* out, const T* symarr, const void* rinv_s,
-                          cpx<T>* tmp, const int* done, cudaStream_t st, int conv, void* phys_out = nullptr) {
+                          cpx<T>* tmp, const int* done, cudaStream_t st, int conv, void* phys_out = nullptr,
+                          const void* wf_pair = nullptr) {
+  const int wf_dd = (std::is_same<T, float>::value && wf_pair) ? 1 : 0;
+  if (wf_dd) rinv_s = wf_pair;
   const GridDesc& g = G->g;
   const int S = symarr ? MUL_SYM : 0;
   if (symarr) phys_out = nullptr;   // the by-product is the inverse of `in` itself: unpreconditioned applies only
@@ -214,6 +219,7 @@ static void pressure_impl(const vd_grid* G, const void* in, void* out, const T* 
     X.pre[0] = S | MUL_IK;
     X.post[0] = MUL_IK;
     X.wfield = rinv_s;
+    X.wf_dd = wf_dd;
     X.aux_out = phys_out;
     X.aux_scale = 1.0 / (double)g.nreal;
     X.aux_conv = conv;
@@ -252,6 +258,7 @@ static void pressure_impl(const vd_grid* G, const void* in, void* out, const T* 
     X.in[1] = T1;
     X.out[1] = T1;
     X.wfield = rinv_s;
+    X.wf_dd = wf_dd;
     X.aux_out = phys_out;
     X.aux_scale = 1.0 / (double)g.nreal;
     X.aux_conv = conv;
@@ -318,6 +325,7 @@ static void pressure_impl(const vd_grid* G, const void* in, void* out, const T* 
     X.in[2] = T1;
     X.out[2] = T1;
     X.wfield = rinv_s;
+    X.wf_dd = wf_dd;
     X.aux_out = phys_out;
     X.aux_scale = 1.0 / (double)g.nreal;
     X.aux_conv = conv;
@@ -359,8 +367,8 @@ static void pressure_impl(const vd_grid* G, const void* in, void* out, const T* 
 
 template <typename T>
 void apply_pressure_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, const T* rinv_s,
-                         cpx<T>* tmp, const int* done, cudaStream_t st) {
-  pressure_impl<T>(G, in, out, symarr, rinv_s, tmp, done, st, 0);
+                         cpx<T>* tmp, const int* done, cudaStream_t st, const void* wf_pair) {
+  pressure_impl<T>(G, in, out, symarr, rinv_s, tmp, done, st, 0, nullptr, wf_pair);
 }
 
 void apply_pressure_spec_dd(const vd_grid* G, const cpx<double>* in, cpx<double>* out, void* tmp, const int* done,
@@ -419,8 +427,10 @@ static void krho_local(const vd_grid* G, const void* in, void* out, bool with_in
 // out = F(c F^-1(S in)) through the pass chain; conv: float-pair arithmetic on double fields
 template <typename T>
 static void krho_transforms(const vd_grid* G, const void* in, void* out, const T* symarr, const void* coef_s,
-                            cpx<T>* tmp, const int* done, cudaStream_t st, int conv) {
+                            cpx<T>* tmp, const int* done, cudaStream_t st, int conv, const void* wf_pair = nullptr) {
   const GridDesc& g = G->g;
+  const int wf_dd = (std::is_same<T, float>::value && wf_pair) ? 1 : 0;
+  if (wf_dd) coef_s = wf_pair;
   const int S = symarr ? MUL_SYM : 0;
   const void* tw = twtab<T>(G);
   if (g.ndim == 1) {
@@ -431,6 +441,7 @@ static void krho_transforms(const vd_grid* G, const void* in, void* out, const T
     X.out[0] = out;
     X.pre[0] = S;
     X.wfield = coef_s;
+    X.wf_dd = wf_dd;
     X.scale = 0.5;
     X.symarr = symarr;
     X.done = done;
@@ -478,6 +489,7 @@ static void krho_transforms(const vd_grid* G, const void* in, void* out, const T
     X.in[0] = tmp;
     X.out[0] = tmp;
     X.wfield = coef_s;
+    X.wf_dd = wf_dd;
     X.scale = 0.5;
     X.done = done;
     launch_xpass<T>(X, g, tw, st);
@@ -509,8 +521,8 @@ static void krho_transforms(const vd_grid* G, const void* in, void* out, const T
 
 template <typename T>
 void apply_krho_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, const T* coef_s,
-                     cpx<T>* tmp, const int* done, cudaStream_t st) {
-  krho_transforms<T>(G, in, out, symarr, coef_s, tmp, done, st, 0);
+                     cpx<T>* tmp, const int* done, cudaStream_t st, const void* wf_pair) {
+  krho_transforms<T>(G, in, out, symarr, coef_s, tmp, done, st, 0, wf_pair);
   krho_local<T>(G, in, out, symarr != nullptr, done, st);
 }
 
@@ -685,13 +697,13 @@ template void inv_transform<double>(const vd_grid*, const cpx<double>*, const Mu
                                     cudaStream_t);
 template void inv_transform<float>(const vd_grid*, const cpx<float>*, const Mult&, float*, cpx<float>*, cudaStream_t);
 template void apply_krho_spec<double>(const vd_grid*, const cpx<double>*, cpx<double>*, const double*,
-                                      const double*, cpx<double>*, const int*, cudaStream_t);
+                                      const double*, cpx<double>*, const int*, cudaStream_t, const void*);
 template void apply_krho_spec<float>(const vd_grid*, const cpx<float>*, cpx<float>*, const float*, const float*,
-                                     cpx<float>*, const int*, cudaStream_t);
+                                     cpx<float>*, const int*, cudaStream_t, const void*);
 template void apply_pressure_spec<double>(const vd_grid*, const cpx<double>*, cpx<double>*, const double*,
-                                          const double*, cpx<double>*, const int*, cudaStream_t);
+                                          const double*, cpx<double>*, const int*, cudaStream_t, const void*);
 template void apply_pressure_spec<float>(const vd_grid*, const cpx<float>*, cpx<float>*, const float*, const float*,
-                                         cpx<float>*, const int*, cudaStream_t);
+                                         cpx<float>*, const int*, cudaStream_t, const void*);
 template void apply_velocity_spec<double>(const vd_grid*, const cpx<double>*, cpx<double>*, const double*, double,
                                           double, cpx<double>*, const int*, cudaStream_t);
 template void apply_velocity_spec<float>(const vd_grid*, const cpx<float>*, cpx<float>*, const float*, double,

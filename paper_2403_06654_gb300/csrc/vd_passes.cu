@@ -1,6 +1,9 @@
 // Transform pass kernels: strided-axis passes (y, z) and the fused contiguous x pass.
 #include "vd_passes.cuh"
 #include "vd_fft.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include "vd_dd.cuh"
 #include "vd_prof.h"
 
@@ -10,6 +13,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 
@@ -61,6 +65,15 @@ __device__ __forceinline__ T scale_t(double s, float hi, float lo) {
   if constexpr (std::is_same<T, dd>::value) return dd(hi, lo);
   else if constexpr (std::is_same<T, float>::value) return hi;
   else return s;
+}
+
+// z * (wh + wl) rounded once to float: the product with the high part is split exactly by an
+// FMA (Dekker's two-product), the low part's product is added to its error term before the
+// final rounding
+__device__ __forceinline__ float mul_pair(float z, float wh, float wl) {
+  const float p = z * wh;
+  const float e = fmaf(z, wh, -p);
+  return p + fmaf(z, wl, e);
 }
 
 constexpr int kThreads = 256;
@@ -222,6 +235,7 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 
 // ---------------------------------------------------------------------------------------
 
 constexpr int kRLines = 16;
+constexpr int kTmaMaxIn = 4;   // inputs a TMA-staged program may read
 
 template <typename T, int S, int N1, int N2>
 __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(const AxisProg P, const GridDesc g,
@@ -366,6 +380,200 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(con
 }
 
 // ---------------------------------------------------------------------------------------
+// z pass, register four-step transform with TMA-staged input (float, n = 128 / 256)
+//
+// The same arithmetic as k_axis_r, in a persistent grid: each block walks its tiles (16
+// adjacent columns, i.e. 16 z-lines) and, for every tile, the transforms of the program.  The
+// input of the next (tile, transform) item is fetched by the tensor memory accelerator
+// (cp.async.bulk.tensor, one 2D box of N rows x 128 bytes) into a shared-memory buffer while
+// the current item is transformed and stored, so loads stay in flight without registers.
+// A z tile is a box of the field viewed as a 2D tensor [n2][2 n1 h0] of floats: its rows
+// (z planes) are n1 h0 8 bytes apart, a multiple of 16 for even n1, and a tile starts at a
+// multiple of 128 bytes.  Columns past the end of a plane arrive as zeros (box fill) and are
+// neither transformed into anything stored nor written.
+// Every wait on the transfer barrier is bounded; a block that gives up raises the grid's error
+// word (reported by the solve as VD_ERR_TIMEOUT), waits (bounded) for its own transfer in
+// flight and returns.
+// ---------------------------------------------------------------------------------------
+
+struct TmaMaps {
+  CUtensorMap m[kTmaMaxIn];
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the phase `parity` of the barrier; false if it did not complete
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+template <int S, int N1, int N2>
+__global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
+    k_axis_tma(const AxisProg P, const GridDesc g, const cpx<float>* __restrict__ twg, const __grid_constant__ TmaMaps maps) {
+  using T = float;
+  constexpr int N = N1 * N2;
+  constexpr int C = N1 / N2;
+  constexpr int LS = N + 1;
+  constexpr int NT = kRLines * N2;
+  constexpr unsigned kBoxBytes = (unsigned)(N * kRLines * sizeof(cpx<T>));
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  if (P.done && *P.done) return;
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);                       // N rows x 16 columns
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + kBoxBytes);
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw + kBoxBytes + 16);
+  cpx<T>* Y = tw + N;
+  const int tid = threadIdx.x;
+  for (int j = tid; j < N; j += NT) tw[j] = twg[g.pz.tw_off + j];
+  if (tid == 0) mbar_init(bar, 1);
+  __syncthreads();
+
+  const int line_stride = g.n1 * g.h0;   // z pass: lines are columns of the flattened (y, x) plane
+  const int inner_n = line_stride;
+  const int tiles = (inner_n + kRLines - 1) / kRLines;
+  const int w = tid % kRLines;
+  const int t = tid / kRLines;
+  const int nx = P.nxf;
+  // items of this block: (tile, transform), tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int my_tiles = (blockIdx.x < tiles) ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int nitems = my_tiles * nx;
+  if (nitems == 0) return;
+  auto issue = [&](int item) {
+    const int tile = (int)blockIdx.x + (item / nx) * (int)gridDim.x;
+    const int x = item % nx;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, kBoxBytes);
+    tma_load_2d(buf, &maps.m[P.xf[x].src], 2 * tile * kRLines, 0, bar);
+  };
+  if (tid == 0) issue(0);
+  const T kfa = kfac_t<T>(g, 2);
+  const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr);
+  cpx<T>* Yl = Y + w * LS;
+
+  for (int it = 0; it < nitems; ++it) {
+    const int tile = (int)blockIdx.x + (it / nx) * (int)gridDim.x;
+    const Xf xf = P.xf[it % nx];
+    const int col = tile * kRLines + w;
+    const bool colok = col < inner_n;
+    const int gbase = col;
+    T kperp2;
+    {
+      const int kyi = col / g.h0;
+      const int kxi = col - kyi * g.h0;
+      const T kx = kfac_t<T>(g, 0) * (T)freq_tilde(kxi, g.n0);
+      const T ky = kfac_t<T>(g, 1) * (T)freq_tilde(kyi, g.n1);
+      kperp2 = kx * kx + ky * ky;
+    }
+    auto mult = [&](int flags, int i, int go, T base) -> T {
+      const T ka = kfa * (T)freq_tilde(i, N);
+      T c = base;
+      if (flags & MUL_IK) c *= ka;
+      if (flags & MUL_IK2) c *= -ka * ka;
+      if (flags & MUL_SYM) c *= symarr[go];
+      if (flags & MUL_NEGK2) c *= -(ka * ka + kperp2);
+      return c;
+    };
+    const bool ok = mbar_wait_bounded(bar, (unsigned)(it & 1));
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        if (g.dev_err) atomicExch(g.dev_err, 1);
+        mbar_wait_bounded(bar, (unsigned)(it & 1));   // the transfer in flight, if it ever lands
+      }
+      __syncthreads();
+      return;
+    }
+    void* dst = P.out[xf.dst];
+    const T scale = scale_t<T>(xf.scale, xf.scale_hi, xf.scale_lo);
+    cpx<T> u[N1];
+#pragma unroll
+    for (int j = 0; j < N1; ++j) {
+      const int i = N2 * j + t;
+      u[j] = buf[i * kRLines + w];
+      if (xf.pre) {
+        u[j] = scal(u[j], mult(xf.pre, i, gbase + i * line_stride, T(1)));
+        if (xf.pre & MUL_IK) u[j] = mul_i(u[j]);
+      }
+    }
+    // every thread has read the staged tile, and the previous item's transpose reads are done:
+    // the buffer takes the next item's input while this one is transformed and stored
+    __syncthreads();
+    if (tid == 0 && it + 1 < nitems) issue(it + 1);
+    dftR<T, S, N1>(u);
+#pragma unroll
+    for (int k1 = 1; k1 < N1; ++k1) {
+      const cpx<T> wv = tw[t * k1];
+      u[k1] = (S < 0) ? cmul(u[k1], wv) : cmulc(u[k1], wv);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) Yl[t * N1 + k1] = u[k1];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int k1 = t + N2 * c;
+      cpx<T> v[N2];
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) v[n2] = Yl[n2 * N1 + k1];
+      dftR<T, S, N2>(v);
+      if (colok) {
+        cpx<T>* q = reinterpret_cast<cpx<T>*>(dst);
+        constexpr int PB = N2 < 4 ? N2 : 4;
+#pragma unroll
+        for (int k0 = 0; k0 < N2; k0 += PB) {
+          cpx<T> prev[PB];
+          if (!xf.first) {
+#pragma unroll
+            for (int b = 0; b < PB; ++b) prev[b] = q[gbase + (k1 + N1 * (k0 + b)) * line_stride];
+          }
+#pragma unroll
+          for (int b = 0; b < PB; ++b) {
+            const int i = k1 + N1 * (k0 + b);
+            const int go = gbase + i * line_stride;
+            cpx<T> vv = v[k0 + b];
+            if (xf.post) {
+              vv = scal(vv, mult(xf.post, i, go, scale));
+              if (xf.post & MUL_IK) vv = mul_i(vv);
+            } else {
+              vv = scal(vv, scale);
+            }
+            q[go] = xf.first ? vv : (prev[b] + vv);
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // contiguous x pass (real <-> half spectrum through a complex FFT of length n0/2)
 // ---------------------------------------------------------------------------------------
 
@@ -457,12 +665,27 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)
         continue;
       }
       if (P.wfield && lok) {
-        const cpx<T>* __restrict__ wf = reinterpret_cast<const cpx<T>*>(P.wfield) + (line0 + line) * m;
+        bool done_pair = false;
+        if constexpr (std::is_same<T, float>::value) {
+          if (P.wf_dd) {
+            const float4* __restrict__ wf4 = reinterpret_cast<const float4*>(P.wfield) + (line0 + line) * m;
 #pragma unroll 4
-        for (int j = t0; j < m; j += TPL) {
-          const cpx<T> z = res[lofs + j];
-          const cpx<T> wv = wf[j];
-          res[lofs + j] = mk<T>(z.x * wv.x, z.y * wv.y);
+            for (int j = t0; j < m; j += TPL) {
+              const cpx<T> z = res[lofs + j];
+              const float4 w = wf4[j];
+              res[lofs + j] = mk<T>(mul_pair(z.x, w.x, w.y), mul_pair(z.y, w.z, w.w));
+            }
+            done_pair = true;
+          }
+        }
+        if (!done_pair) {
+          const cpx<T>* __restrict__ wf = reinterpret_cast<const cpx<T>*>(P.wfield) + (line0 + line) * m;
+#pragma unroll 4
+          for (int j = t0; j < m; j += TPL) {
+            const cpx<T> z = res[lofs + j];
+            const cpx<T> wv = wf[j];
+            res[lofs + j] = mk<T>(z.x * wv.x, z.y * wv.y);
+          }
         }
       }
       cpx<T>* other = (res == A) ? B : A;
@@ -613,11 +836,21 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_xpass_r(const
         continue;
       }
       if (P.wfield && lok) {
-        const cpx<T>* __restrict__ wf = reinterpret_cast<const cpx<T>*>(P.wfield) + rb;
+        if (P.wf_dd) {
+          // the float pairs of the two reals of u[q]: one 16-byte load
+          const float4* __restrict__ wf4 = reinterpret_cast<const float4*>(P.wfield) + rb;
 #pragma unroll
-        for (int q = 0; q < M1; ++q) {
-          const cpx<T> wv = wf[M2 * q + t];
-          u[q] = mk<T>(u[q].x * wv.x, u[q].y * wv.y);
+          for (int q = 0; q < M1; ++q) {
+            const float4 w = wf4[M2 * q + t];
+            u[q] = mk<T>(mul_pair(u[q].x, w.x, w.y), mul_pair(u[q].y, w.z, w.w));
+          }
+        } else {
+          const cpx<T>* __restrict__ wf = reinterpret_cast<const cpx<T>*>(P.wfield) + rb;
+#pragma unroll
+          for (int q = 0; q < M1; ++q) {
+            const cpx<T> wv = wf[M2 * q + t];
+            u[q] = mk<T>(u[q].x * wv.x, u[q].y * wv.y);
+          }
         }
       }
     }
@@ -802,14 +1035,86 @@ static void split_scale(double s, float* hi, float* lo) {
   *lo = (float)(s - (double)*hi);
 }
 
+// tensor-map encoder of the driver, looked up once through the runtime (no libcuda link)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// 2D map of a half-spectrum field for z tiles: [n2][2 n1 h0] floats, box 16 columns x N rows
+static bool encode_z_tiles(CUtensorMap* m, const void* base, const GridDesc& g, int N) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || (reinterpret_cast<uintptr_t>(base) & 15u)) return false;
+  const cuuint64_t inner = (cuuint64_t)g.n1 * (cuuint64_t)g.h0;
+  cuuint64_t dims[2] = {2 * inner, (cuuint64_t)g.n2};
+  cuuint64_t strides[1] = {inner * sizeof(cpx<float>)};
+  cuuint32_t box[2] = {2 * kRLines, (cuuint32_t)N};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (!cached[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 152;
+  }
+  return cached[dev];
+}
+
+// the TMA-staged z kernel takes programs whose transforms all run an FFT and read in[0..3]
+static bool tma_program_ok(const AxisProg& P) {
+  if (P.axis != 2 || P.conv_in || P.conv_out) return false;
+  for (int t = 0; t < P.nxf; ++t)
+    if (P.xf[t].nofft || P.xf[t].src >= kTmaMaxIn) return false;
+  return P.nxf > 0;
+}
+
+template <int S, int N1, int N2>
+static bool launch_axis_tma(const AxisProg& P, const GridDesc& g, const cpx<float>* tw, cudaStream_t st) {
+  constexpr int N = N1 * N2;
+  TmaMaps maps;
+  std::memset(&maps, 0, sizeof maps);
+  unsigned used = 0;
+  for (int t = 0; t < P.nxf; ++t) used |= 1u << P.xf[t].src;
+  for (int k = 0; k < kTmaMaxIn; ++k)
+    if ((used >> k) & 1u)
+      if (!encode_z_tiles(&maps.m[k], P.in[k], g, N)) return false;
+  const long long inner = (long long)g.n1 * g.h0;
+  const long long tiles = (inner + kRLines - 1) / kRLines;
+  const int per_sm = (N2 == 16) ? 3 : 6;
+  const long long blocks = std::min<long long>(tiles, (long long)per_sm * sm_count());
+  const size_t smem = sizeof(cpx<float>) * (size_t)(N * kRLines) + 16 + sizeof(cpx<float>) * (size_t)(N + kRLines * (N + 1));
+  ensure_smem(reinterpret_cast<const void*>(k_axis_tma<S, N1, N2>), smem);
+  k_axis_tma<S, N1, N2><<<(unsigned)blocks, kRLines * N2, smem, st>>>(P, g, tw, maps);
+  return true;
+}
+
 template <typename T>
 void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw, cudaStream_t st) {
   AxisProg P = P0;
   for (int t = 0; t < P.nxf; ++t) split_scale(P.xf[t].scale, &P.xf[t].scale_hi, &P.xf[t].scale_lo);
   const int n = (P.axis == 2) ? g.pz.n : g.py.n;
-  const int choice = tune_get(0, type_code<T>(), n, P.axis, dir);
+  int choice = tune_get(0, type_code<T>(), n, P.axis, dir);
   const bool reg_ok = std::is_same<T, float>::value && (n == 256 || n == 128);
-  const int W = choice > 0 ? choice : tile_width(n, kEPT<T>);
+  if (choice == kChoiceStaged && !(reg_ok && tma_program_ok(P))) choice = 0;   // not applicable: register kernel
+  const int W = (choice > 0 && choice != kChoiceStaged) ? choice : tile_width(n, kEPT<T>);
   long long inner_n, outer_n;
   if (P.axis == 2) {
     inner_n = (long long)g.n1 * g.h0;
@@ -837,6 +1142,14 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
   ProfScope ps(std::is_same<T, dd>::value ? PC_AXISDD : (sizeof(T) == 8 ? PC_AXIS64 : PC_AXIS32), st, bytes,
                flops);
   if constexpr (std::is_same<T, float>::value) {
+    const cpx<float>* twf = reinterpret_cast<const cpx<float>*>(tw);
+    if (choice == kChoiceStaged) {
+      bool ok;
+      if (n == 256) ok = (dir < 0) ? launch_axis_tma<-1, 16, 16>(P, g, twf, st) : launch_axis_tma<+1, 16, 16>(P, g, twf, st);
+      else ok = (dir < 0) ? launch_axis_tma<-1, 16, 8>(P, g, twf, st) : launch_axis_tma<+1, 16, 8>(P, g, twf, st);
+      if (ok) return;
+      choice = 0;   // no tensor map (encoder unavailable or unaligned field): the register kernel
+    }
     // register-resident four-step kernel for the common lengths (unless tuned otherwise)
     if (reg_ok && choice <= 0) {
       if (n == 256) {
@@ -901,7 +1214,7 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
   double bytes = 0, flops = 0;
   const double real_fft = (double)g.nreal * 2.5 * std::log2((double)g.n0);   // one real transform of every line
   if (P.mode == 0) {
-    bytes = P.ncomp * 2.0 * fc + (P.wfield ? fr : 0.0);
+    bytes = P.ncomp * 2.0 * fc + (P.wfield ? (P.wf_dd ? 2.0 * fr : fr) : 0.0);
     flops = P.ncomp * 2.0 * real_fft;
   } else {
     bytes = P.ncomp * (fc + fr);

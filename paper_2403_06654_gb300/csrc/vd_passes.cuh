@@ -64,6 +64,9 @@ struct XProg {
   int pre[4];
   int post[4];
   const void* wfield;
+  // float programs only: wfield holds a float pair (hi, lo) per real point, and the multiply
+  // z * (hi + lo) is carried in float-pair arithmetic, rounded to float once
+  int wf_dd;
   double scale;
   float scale_hi, scale_lo;   // float-pair split of scale (set by launch_xpass)
   const void* symarr;
@@ -88,6 +91,9 @@ void launch_xpass(const XProg& P, const GridDesc& g, const void* tw, cudaStream_
 // launch-shape table (vd_passes.cu).  kind 0: y/z pass (key: type, length, axis, direction);
 // kind 1: x pass (key: type, n0/2, axis 0, mode).  type: 0 double, 1 float, 2 float-pair.
 // choice: 0 register four-step kernel, > 0 lines per block, < 0 (get) absent / (set) erase.
+// kind 0 choice kChoiceStaged: the register kernel with TMA-staged input (float z passes of
+// length 128 / 256)
+constexpr int kChoiceStaged = 128;
 int tune_get(int kind, int type, int n, int axis, int dir);
 void tune_set(int kind, int type, int n, int axis, int dir, int choice);
 int tune_table(int* out, int max);   // 6 ints per entry; returns the entry count

@@ -1,7 +1,9 @@
 // Launch counter and per-class event timing of the transform passes.
 #include "vd_prof.h"
 #include "vd_internal.h"
+#include "vd_dd.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -133,11 +135,89 @@ void prof_discard(long long mark, cudaStream_t st) {
     if (p.seq >= mark && p.st == st) p.dropped = true;
 }
 
+// ---------------------------------------------------------------------------------------
+// arithmetic-rate microbenchmark (roofline denominators of the ALU-bound passes)
+// ---------------------------------------------------------------------------------------
+
+// written only when a chain ends on an impossible value, so that the chains stay live
+static __device__ double g_alu_sink;
+
+constexpr int kAluChains = 8;
+
+// kAluChains independent chains a <- a * m + c per thread; values stay near 1 (m < 1, c small)
+template <typename T>
+__global__ void __launch_bounds__(256) k_alu_fma(int iters, T m, T c) {
+  T a[kAluChains];
+#pragma unroll
+  for (int k = 0; k < kAluChains; ++k) a[k] = T(1) + T(threadIdx.x + k) * T(1e-3);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int k = 0; k < kAluChains; ++k) a[k] = fma(a[k], m, c);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < kAluChains; ++k) s += a[k];
+  if (s == T(-1)) g_alu_sink = (double)s;
+}
+
+// the same chains in float-pair arithmetic (one float-pair multiply and one add per step)
+__global__ void __launch_bounds__(256) k_alu_dd(int iters, float mh, float ml, float ch, float cl) {
+  const dd m(mh, ml), c(ch, cl);
+  dd a[kAluChains];
+#pragma unroll
+  for (int k = 0; k < kAluChains; ++k) a[k] = dd(1.0f + (float)(threadIdx.x + k) * 1e-3f, 0.0f);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int k = 0; k < kAluChains; ++k) a[k] = a[k] * m + c;
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kAluChains; ++k) s += a[k].hi + a[k].lo;
+  if (s == -1.0f) g_alu_sink = (double)s;
+}
+
 }  // namespace vd
 
 using namespace vd;
 
 extern "C" {
+
+vd_status vd_alu_rate(int kind, double* flops_per_s, vd_stream stream) {
+  if (kind < 0 || kind > 2 || !flops_per_s) return fail(VD_ERR_INVALID_ARG, "kind must be 0, 1 or 2");
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  VD_CUDA(cudaGetDevice(&dev));
+  VD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = 8 * sms, threads = 256;
+  // about 10-40 ms per launch on a GB300
+  const int iters = (kind == 0) ? 512 : (kind == 1 ? 16384 : 2048);
+  cudaEvent_t e0, e1;
+  VD_CUDA(cudaEventCreate(&e0));
+  VD_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {   // the first launch warms up
+    VD_CUDA(cudaEventRecord(e0, st));
+    if (kind == 0) k_alu_fma<double><<<blocks, threads, 0, st>>>(iters, 0.999999999, 1e-9);
+    else if (kind == 1) k_alu_fma<float><<<blocks, threads, 0, st>>>(iters, 0.9999f, 1e-5f);
+    else k_alu_dd<<<blocks, threads, 0, st>>>(iters, 0.9999f, 1e-12f, 1e-5f, 1e-13f);
+    count_launch();
+    VD_CUDA(cudaGetLastError());
+    VD_CUDA(cudaEventRecord(e1, st));
+    VD_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    VD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (rep > 0) best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const double steps = (double)blocks * threads * iters * 4.0 * kAluChains;
+  *flops_per_s = 2.0 * steps / (best * 1e-3);
+  return VD_OK;
+}
 
 long long vd_launch_count(void) { return g_launches.load(); }
 

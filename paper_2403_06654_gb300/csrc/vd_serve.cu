@@ -205,7 +205,7 @@ struct vd_server {
     sp.restart = r.restart > 0 ? r.restart : 30;
     sp.use_x0 = 0;
     sp.precision = r.precision;
-    sp.inner_tol = 1e-5;
+    sp.inner_tol = 0.0;   // automatic
     sp.check_every = 1;
     return sp;
   }

@@ -451,7 +451,7 @@ vd_status vd_flow_step(vd_flow* F, double dt, vd_step_info* info, vd_stream stre
   sp.restart = p.restart;
   sp.use_x0 = 1;
   sp.precision = p.precision;
-  sp.inner_tol = 1e-5;
+  sp.inner_tol = 0.0;   // automatic
   sp.check_every = 1;
   vd_solve_info iv{};
   vd_status sv = vd_solve(G, VD_OP_VELOCITY, (vd_solver)p.vel_solver, &opp, &sp, F->rhs, F->ustar, &iv, F->ws,

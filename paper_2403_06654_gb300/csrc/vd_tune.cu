@@ -85,6 +85,7 @@ vd_status tune_type(const vd_grid* G, const void* tw, void* a, void* b, cudaStre
     std::vector<int> cand;
     const bool reg = type == 1 && (n == 128 || n == 256);
     if (reg) cand.push_back(0);
+    if (reg && axis == 2) cand.push_back(kChoiceStaged);
     for (int W = 1; W <= 64; W *= 2) {
       if (sizeof(cpx<T>) * (size_t)(n + 2 * W * n) > kSmemCap) break;
       if (W > 1 && W > 2 * inner) break;
@@ -190,7 +191,8 @@ int vd_autotune_table(int* out, int max) { return vd::tune_table(out, max); }
 
 vd_status vd_autotune_set(int kind, int type, int n, int axis, int dir, int choice) {
   if (kind < 0 || kind > 1 || type < 0 || type > 2 || n <= 0) return vd::fail(VD_ERR_INVALID_ARG, "bad tuning key");
-  if (choice > 64 || (choice > 0 && (choice & (choice - 1)))) return vd::fail(VD_ERR_INVALID_ARG, "bad choice");
+  if (choice != vd::kChoiceStaged && (choice > 64 || (choice > 0 && (choice & (choice - 1)))))
+    return vd::fail(VD_ERR_INVALID_ARG, "bad choice");
   vd::tune_set(kind, type, n, axis, dir, choice);
   return VD_OK;
 }

@@ -3,7 +3,7 @@
 Tolerances (FP64): transforms, derivatives and operator applies are compared element by
 element with a relative max-norm bound of 1e-12 (the rounding of a few FFT passes on
 O(1e3..1e5)-sized operator norms stays far below); solutions solved to 1e-12/1e-13 on both
-sides must agree to 1e-10 in relative 2-norm (the benchmark spec's bound), and iterates after a
+sides must agree to 1e-10 in relative 2-norm (the parity bound), and iterates after a
 fixed number k of iterations from the same start must agree to 1e-10.
 Sizes span several tiles with ragged tails (h0 = n0/2 + 1 columns never a multiple of the
 tile width) and radix 2, 3 and 5 lengths.
