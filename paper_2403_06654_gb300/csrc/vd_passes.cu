@@ -19,6 +19,7 @@
 
 namespace vd {
 static void ensure_smem(const void* func, size_t smem);
+static int sm_count();
 }
 
 namespace vd {
@@ -380,15 +381,17 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(con
 }
 
 // ---------------------------------------------------------------------------------------
-// z pass, register four-step transform with TMA-staged input (float, n = 128 / 256)
+// y and z passes, register four-step transform with TMA-staged input (float, n = 128 / 256)
 //
 // The same arithmetic as k_axis_r, in a persistent grid: each block walks its tiles (16
-// adjacent columns, i.e. 16 z-lines) and, for every tile, the transforms of the program.  The
+// adjacent columns, i.e. 16 lines) and, for every tile, the transforms of the program.  The
 // input of the next (tile, transform) item is fetched by the tensor memory accelerator
-// (cp.async.bulk.tensor, one 2D box of N rows x 128 bytes) into a shared-memory buffer while
-// the current item is transformed and stored, so loads stay in flight without registers.
+// (cp.async.bulk.tensor, one box of N rows x 128 bytes) into a shared-memory buffer while the
+// current item is transformed and stored, so loads stay in flight without registers.
 // A z tile is a box of the field viewed as a 2D tensor [n2][2 n1 h0] of floats: its rows
-// (z planes) are n1 h0 8 bytes apart, a multiple of 16 for even n1, and a tile starts at a
+// (z planes) are n1 h0 8 bytes apart, a multiple of 16 for even n1.  A y tile is a box of the
+// 3D tensor [n2][n1][2 h0]: its rows are 8 h0 bytes apart, a multiple of 16 only for even h0
+// (n0 = 2 mod 4); with odd h0 the y passes keep the register kernel.  A tile starts at a
 // multiple of 128 bytes.  Columns past the end of a plane arrive as zeros (box fill) and are
 // neither transformed into anything stored nor written.
 // Every wait on the transfer barrier is bounded; a block that gives up raises the grid's error
@@ -438,7 +441,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-template <int S, int N1, int N2>
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+template <int S, int N1, int N2, int AX>
 __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
     k_axis_tma(const AxisProg P, const GridDesc g, const cpx<float>* __restrict__ twg, const __grid_constant__ TmaMaps maps) {
   using T = float;
@@ -447,20 +458,27 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
   constexpr int LS = N + 1;
   constexpr int NT = kRLines * N2;
   constexpr unsigned kBoxBytes = (unsigned)(N * kRLines * sizeof(cpx<T>));
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char smem_tma[];
+  unsigned char* smem_raw = smem_tma;
   if (P.done && *P.done) return;
+  constexpr int axis = AX;   // 1 = y, 2 = z (compiled apart: the z form keeps its register budget)
+  const FftPlan& pl = (axis == 2) ? g.pz : g.py;
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);                       // N rows x 16 columns
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + kBoxBytes);
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw + kBoxBytes + 16);
   cpx<T>* Y = tw + N;
   const int tid = threadIdx.x;
-  for (int j = tid; j < N; j += NT) tw[j] = twg[g.pz.tw_off + j];
+  for (int j = tid; j < N; j += NT) tw[j] = twg[pl.tw_off + j];
   if (tid == 0) mbar_init(bar, 1);
   __syncthreads();
 
-  const int line_stride = g.n1 * g.h0;   // z pass: lines are columns of the flattened (y, x) plane
+  // z pass: lines are the columns of the flattened (y, x) plane (one "plane" of tiles);
+  // y pass: lines are the x columns of each z plane o
+  const int line_stride = (axis == 2) ? g.n1 * g.h0 : g.h0;
   const int inner_n = line_stride;
-  const int tiles = (inner_n + kRLines - 1) / kRLines;
+  const int outer_stride = (axis == 2) ? 0 : g.n1 * g.h0;
+  const int tpp = (inner_n + kRLines - 1) / kRLines;   // tiles per plane
+  const int tiles = tpp * ((axis == 2) ? 1 : g.n2);
   const int w = tid % kRLines;
   const int t = tid / kRLines;
   const int nx = P.nxf;
@@ -471,28 +489,39 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
   auto issue = [&](int item) {
     const int tile = (int)blockIdx.x + (item / nx) * (int)gridDim.x;
     const int x = item % nx;
+    const int o = tile / tpp;
+    const int col0 = (tile - o * tpp) * kRLines;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, kBoxBytes);
-    tma_load_2d(buf, &maps.m[P.xf[x].src], 2 * tile * kRLines, 0, bar);
+    if (axis == 2) tma_load_2d(buf, &maps.m[P.xf[x].src], 2 * col0, 0, bar);
+    else tma_load_3d(buf, &maps.m[P.xf[x].src], 2 * col0, 0, o, bar);
   };
   if (tid == 0) issue(0);
-  const T kfa = kfac_t<T>(g, 2);
+  const T kfa = kfac_t<T>(g, axis);
   const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr);
   cpx<T>* Yl = Y + w * LS;
 
   for (int it = 0; it < nitems; ++it) {
     const int tile = (int)blockIdx.x + (it / nx) * (int)gridDim.x;
     const Xf xf = P.xf[it % nx];
-    const int col = tile * kRLines + w;
+    const int o = tile / tpp;
+    const int col = (tile - o * tpp) * kRLines + w;
     const bool colok = col < inner_n;
-    const int gbase = col;
+    const int gbase = o * outer_stride + col;
     T kperp2;
-    {
+    if (axis == 2) {
       const int kyi = col / g.h0;
       const int kxi = col - kyi * g.h0;
       const T kx = kfac_t<T>(g, 0) * (T)freq_tilde(kxi, g.n0);
       const T ky = kfac_t<T>(g, 1) * (T)freq_tilde(kyi, g.n1);
       kperp2 = kx * kx + ky * ky;
+    } else {
+      const T kx = kfac_t<T>(g, 0) * (T)freq_tilde(col, g.n0);
+      kperp2 = kx * kx;
+      if (g.ndim == 3) {
+        const T kz = kfac_t<T>(g, 2) * (T)freq_tilde(o, g.n2);
+        kperp2 += kz * kz;
+      }
     }
     auto mult = [&](int flags, int i, int go, T base) -> T {
       const T ka = kfa * (T)freq_tilde(i, N);
@@ -885,6 +914,178 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_xpass_r(const
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// fused x pass (mode 0), register four-step transforms with TMA-staged input lines (float)
+//
+// The arithmetic of k_xpass_r in a persistent grid over (group of LINES lines, component)
+// items.  A group's half-spectrum lines are contiguous in memory (LINES x pitch complex
+// values; 16-byte aligned for an even group size), so the tensor memory accelerator fetches
+// the next item's lines with one bulk copy (cp.async.bulk) into a shared-memory stage while
+// the current item is transformed, weighted and stored.  Packing reads the stage directly.
+// Bounded waits as in k_axis_tma.
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+template <int M1, int M2>
+__global__ void __launch_bounds__(256, 3) k_xpass_tma(const XProg P, const GridDesc g, const cpx<float>* __restrict__ twg) {
+  using T = float;
+  using X = XR<T, M1, M2>;
+  constexpr int M = X::M, LINES = X::LINES, LS = X::LS;
+  extern __shared__ __align__(1024) unsigned char smem_tma[];
+  unsigned char* smem_raw = smem_tma;
+  if (P.done && *P.done) return;
+  const int h0 = g.h0;
+  const int pitch = h0;
+  const unsigned stage_bytes = (unsigned)(LINES * pitch * sizeof(cpx<T>));   // multiple of 16 (LINES even)
+  cpx<T>* stage = reinterpret_cast<cpx<T>*>(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + stage_bytes);
+  cpx<T>* twm = reinterpret_cast<cpx<T>*>(smem_raw + stage_bytes + 16);
+  cpx<T>* pk = twm + M;
+  cpx<T>* buf = pk + (M + 2);
+  const int tid = threadIdx.x;
+  for (int j = tid; j < M; j += 256) twm[j] = twg[g.px.tw_off + j];
+  for (int j = tid; j <= M; j += 256) pk[j] = twg[g.pk_off + j];
+  if (tid == 0) mbar_init(bar, 1);
+  __syncthreads();
+  const long long nlines = (long long)g.n1 * g.n2;
+  const int groups = (int)((nlines + LINES - 1) / LINES);
+  const int nc = P.ncomp;
+  const int my_groups = ((int)blockIdx.x < groups) ? (groups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int nitems = my_groups * nc;
+  if (nitems == 0) return;
+  auto issue = [&](int item) {
+    const long long line0 = (long long)((int)blockIdx.x + (item / nc) * (int)gridDim.x) * LINES;
+    const int c = item % nc;
+    const int nl = (int)min((long long)LINES, nlines - line0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const unsigned bytes = (unsigned)(nl * pitch * sizeof(cpx<T>));
+    mbar_expect_tx(bar, bytes);
+    bulk_load(stage, reinterpret_cast<const cpx<T>*>(P.in[c]) + line0 * pitch, bytes, bar);
+  };
+  if (tid == 0) issue(0);
+  const int line = tid / M2;
+  const int t = tid % M2;
+  cpx<T>* Yl = buf + line * LS;
+  const cpx<T>* Sl = stage + line * pitch;
+  const T kfx = kfac_t<T>(g, 0);
+  const T scale = scale_t<T>(P.scale, P.scale_hi, P.scale_lo);
+
+  for (int it = 0; it < nitems; ++it) {
+    const long long line0 = (long long)((int)blockIdx.x + (it / nc) * (int)gridDim.x) * LINES;
+    const int c = it % nc;
+    const bool lok = line0 + line < nlines;
+    const int lb = (int)((line0 + line) * pitch);
+    const int rb = (int)((line0 + line) * M);
+    const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr) + (line0 + line) * h0;
+    const int pre = P.pre[c], post = P.post[c];
+    auto premul = [&](int k, cpx<T> v) -> cpx<T> {
+      if (!pre) return v;
+      const T kx = kfx * (T)freq_tilde(k, g.n0);
+      T cc = T(1);
+      if (pre & MUL_IK) cc *= kx;
+      if (pre & MUL_SYM) cc *= symarr[k];
+      if (pre & (MUL_NEGK2 | MUL_IK2)) cc *= -kx * kx;
+      v = scal(v, cc);
+      if (pre & MUL_IK) v = mul_i(v);
+      return v;
+    };
+    const bool ok = mbar_wait_bounded(bar, (unsigned)(it & 1));
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        if (g.dev_err) atomicExch(g.dev_err, 1);
+        mbar_wait_bounded(bar, (unsigned)(it & 1));
+      }
+      __syncthreads();
+      return;
+    }
+    cpx<T> u[M1];
+#pragma unroll
+    for (int q = 0; q < M1; ++q) {
+      const int j = M2 * q + t;
+      const cpx<T> Xv = premul(j, Sl[j]);
+      const cpx<T> Xc = conjg(premul(M - j, Sl[M - j]));
+      u[q] = (Xv + Xc) + mul_i(cmulc(Xv - Xc, pk[j]));
+    }
+    // the stage is consumed: it takes the next item's lines while this one is transformed
+    __syncthreads();
+    if (tid == 0 && it + 1 < nitems) issue(it + 1);
+    fourstep<T, +1, M1, M2>(u, Yl, twm, t);
+    if (P.wfield && lok) {
+      if (P.wf_dd) {
+        const float4* __restrict__ wf4 = reinterpret_cast<const float4*>(P.wfield) + rb;
+#pragma unroll
+        for (int q = 0; q < M1; ++q) {
+          const float4 w = wf4[M2 * q + t];
+          u[q] = mk<T>(mul_pair(u[q].x, w.x, w.y), mul_pair(u[q].y, w.z, w.w));
+        }
+      } else {
+        const cpx<T>* __restrict__ wf = reinterpret_cast<const cpx<T>*>(P.wfield) + rb;
+#pragma unroll
+        for (int q = 0; q < M1; ++q) {
+          const cpx<T> wv = wf[M2 * q + t];
+          u[q] = mk<T>(u[q].x * wv.x, u[q].y * wv.y);
+        }
+      }
+    }
+    fourstep<T, -1, M1, M2>(u, Yl, twm, t);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < M1; ++q) Yl[M2 * q + t] = u[q];
+    __syncthreads();
+    if (lok) {
+      auto unpack = [&](int k) {
+        const cpx<T> Z = Yl[k == M ? 0 : k];
+        const cpx<T> Zc = conjg(Yl[k == 0 ? 0 : M - k]);
+        cpx<T> Xv = (Z + Zc) - mul_i(cmul(Z - Zc, pk[k]));
+        T cc = scale;
+        if (post) {
+          const T kx = kfx * (T)freq_tilde(k, g.n0);
+          if (post & MUL_IK) cc *= kx;
+          if (post & MUL_SYM) cc *= symarr[k];
+          if (post & (MUL_NEGK2 | MUL_IK2)) cc *= -kx * kx;
+        }
+        Xv = scal(Xv, cc);
+        if (post & MUL_IK) Xv = mul_i(Xv);
+        reinterpret_cast<cpx<T>*>(P.out[c])[lb + k] = Xv;
+      };
+#pragma unroll
+      for (int q = 0; q < M1; ++q) unpack(t + M2 * q);
+      if (t == 0) unpack(M);
+    }
+  }
+}
+
+// the staged x pass takes fused float programs with aligned fields and a whole-line stage
+static bool xpass_tma_ok(const XProg& P, const GridDesc& g, int lines) {
+  if (P.mode != 0 || P.aux_out || P.conv_in || P.conv_out || g.n1 * g.n2 < 2) return false;
+  const int pitch = g.h0;
+  if (((long long)lines * pitch * (long long)sizeof(cpx<float>)) % 16) return false;
+  for (int c = 0; c < P.ncomp; ++c)
+    if (reinterpret_cast<uintptr_t>(P.in[c]) & 15u) return false;
+  return true;
+}
+
+template <int M1, int M2>
+static bool launch_xpass_tma(const XProg& P, const GridDesc& g, const cpx<float>* tw, cudaStream_t st) {
+  using X = XR<float, M1, M2>;
+  if (!xpass_tma_ok(P, g, X::LINES)) return false;
+  const int pitch = g.h0;
+  const long long nlines = (long long)g.n1 * g.n2;
+  const long long groups = (nlines + X::LINES - 1) / X::LINES;
+  const long long blocks = std::min<long long>(groups, 3LL * sm_count());
+  const size_t smem = sizeof(cpx<float>) * (size_t)(X::LINES * pitch) + 16 +
+                      sizeof(cpx<float>) * (size_t)(X::M + (X::M + 2) + X::LINES * X::LS);
+  ensure_smem(reinterpret_cast<const void*>(k_xpass_tma<M1, M2>), smem);
+  k_xpass_tma<M1, M2><<<(unsigned)blocks, 256, smem, st>>>(P, g, tw);
+  return true;
+}
+
 template <typename T, int M1, int M2>
 static void launch_xpass_r(const XProg& P, const GridDesc& g, const cpx<T>* tw, cudaStream_t st) {
   using X = XR<T, M1, M2>;
@@ -1051,16 +1252,29 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// 2D map of a half-spectrum field for z tiles: [n2][2 n1 h0] floats, box 16 columns x N rows
-static bool encode_z_tiles(CUtensorMap* m, const void* base, const GridDesc& g, int N) {
+// map of a half-spectrum field for the tiles of an axis pass: z pass, 2D [n2][2 n1 h0] floats;
+// y pass, 3D [n2][n1][2 h0] (rows 8 h0 bytes apart: even h0 only); box 16 columns x N rows
+static bool encode_tiles(CUtensorMap* m, const void* base, const GridDesc& g, int axis, int N) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc || (reinterpret_cast<uintptr_t>(base) & 15u)) return false;
-  const cuuint64_t inner = (cuuint64_t)g.n1 * (cuuint64_t)g.h0;
-  cuuint64_t dims[2] = {2 * inner, (cuuint64_t)g.n2};
-  cuuint64_t strides[1] = {inner * sizeof(cpx<float>)};
-  cuuint32_t box[2] = {2 * kRLines, (cuuint32_t)N};
-  cuuint32_t es[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+  const cuuint64_t row = (cuuint64_t)g.h0 * sizeof(cpx<float>);
+  if (axis == 2) {
+    const cuuint64_t inner = (cuuint64_t)g.n1 * (cuuint64_t)g.h0;
+    cuuint64_t dims[2] = {2 * inner, (cuuint64_t)g.n2};
+    cuuint64_t strides[1] = {inner * sizeof(cpx<float>)};
+    cuuint32_t box[2] = {2 * kRLines, (cuuint32_t)N};
+    cuuint32_t es[2] = {1, 1};
+    if (strides[0] % 16) return false;
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
+  if (row % 16) return false;
+  cuuint64_t dims[3] = {2 * (cuuint64_t)g.h0, (cuuint64_t)g.n1, (cuuint64_t)g.n2};
+  cuuint64_t strides[2] = {row, row * (cuuint64_t)g.n1};
+  cuuint32_t box[3] = {2 * kRLines, (cuuint32_t)N, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -1078,15 +1292,17 @@ static int sm_count() {
   return cached[dev];
 }
 
-// the TMA-staged z kernel takes programs whose transforms all run an FFT and read in[0..3]
-static bool tma_program_ok(const AxisProg& P) {
-  if (P.axis != 2 || P.conv_in || P.conv_out) return false;
+// the TMA-staged kernel takes programs whose transforms all run an FFT and read in[0..3]; a y
+// pass needs rows on 16-byte boundaries (even h0)
+static bool tma_program_ok(const AxisProg& P, const GridDesc& g) {
+  if (P.conv_in || P.conv_out) return false;
+  if (P.axis == 1 && (g.h0 & 1)) return false;
   for (int t = 0; t < P.nxf; ++t)
     if (P.xf[t].nofft || P.xf[t].src >= kTmaMaxIn) return false;
   return P.nxf > 0;
 }
 
-template <int S, int N1, int N2>
+template <int S, int N1, int N2, int AX>
 static bool launch_axis_tma(const AxisProg& P, const GridDesc& g, const cpx<float>* tw, cudaStream_t st) {
   constexpr int N = N1 * N2;
   TmaMaps maps;
@@ -1095,14 +1311,14 @@ static bool launch_axis_tma(const AxisProg& P, const GridDesc& g, const cpx<floa
   for (int t = 0; t < P.nxf; ++t) used |= 1u << P.xf[t].src;
   for (int k = 0; k < kTmaMaxIn; ++k)
     if ((used >> k) & 1u)
-      if (!encode_z_tiles(&maps.m[k], P.in[k], g, N)) return false;
-  const long long inner = (long long)g.n1 * g.h0;
-  const long long tiles = (inner + kRLines - 1) / kRLines;
+      if (!encode_tiles(&maps.m[k], P.in[k], g, P.axis, N)) return false;
+  const long long cols = (P.axis == 2) ? (long long)g.n1 * g.h0 : g.h0;
+  const long long tiles = ((cols + kRLines - 1) / kRLines) * (P.axis == 2 ? 1 : g.n2);
   const int per_sm = (N2 == 16) ? 3 : 6;
   const long long blocks = std::min<long long>(tiles, (long long)per_sm * sm_count());
   const size_t smem = sizeof(cpx<float>) * (size_t)(N * kRLines) + 16 + sizeof(cpx<float>) * (size_t)(N + kRLines * (N + 1));
-  ensure_smem(reinterpret_cast<const void*>(k_axis_tma<S, N1, N2>), smem);
-  k_axis_tma<S, N1, N2><<<(unsigned)blocks, kRLines * N2, smem, st>>>(P, g, tw, maps);
+  ensure_smem(reinterpret_cast<const void*>(k_axis_tma<S, N1, N2, AX>), smem);
+  k_axis_tma<S, N1, N2, AX><<<(unsigned)blocks, kRLines * N2, smem, st>>>(P, g, tw, maps);
   return true;
 }
 
@@ -1113,7 +1329,7 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
   const int n = (P.axis == 2) ? g.pz.n : g.py.n;
   int choice = tune_get(0, type_code<T>(), n, P.axis, dir);
   const bool reg_ok = std::is_same<T, float>::value && (n == 256 || n == 128);
-  if (choice == kChoiceStaged && !(reg_ok && tma_program_ok(P))) choice = 0;   // not applicable: register kernel
+  if (choice == kChoiceStaged && !(reg_ok && tma_program_ok(P, g))) choice = 0;   // not applicable: register kernel
   const int W = (choice > 0 && choice != kChoiceStaged) ? choice : tile_width(n, kEPT<T>);
   long long inner_n, outer_n;
   if (P.axis == 2) {
@@ -1145,8 +1361,13 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
     const cpx<float>* twf = reinterpret_cast<const cpx<float>*>(tw);
     if (choice == kChoiceStaged) {
       bool ok;
-      if (n == 256) ok = (dir < 0) ? launch_axis_tma<-1, 16, 16>(P, g, twf, st) : launch_axis_tma<+1, 16, 16>(P, g, twf, st);
-      else ok = (dir < 0) ? launch_axis_tma<-1, 16, 8>(P, g, twf, st) : launch_axis_tma<+1, 16, 8>(P, g, twf, st);
+      if (P.axis == 2) {
+        if (n == 256) ok = (dir < 0) ? launch_axis_tma<-1, 16, 16, 2>(P, g, twf, st) : launch_axis_tma<+1, 16, 16, 2>(P, g, twf, st);
+        else ok = (dir < 0) ? launch_axis_tma<-1, 16, 8, 2>(P, g, twf, st) : launch_axis_tma<+1, 16, 8, 2>(P, g, twf, st);
+      } else {
+        if (n == 256) ok = (dir < 0) ? launch_axis_tma<-1, 16, 16, 1>(P, g, twf, st) : launch_axis_tma<+1, 16, 16, 1>(P, g, twf, st);
+        else ok = (dir < 0) ? launch_axis_tma<-1, 16, 8, 1>(P, g, twf, st) : launch_axis_tma<+1, 16, 8, 1>(P, g, twf, st);
+      }
       if (ok) return;
       choice = 0;   // no tensor map (encoder unavailable or unaligned field): the register kernel
     }
@@ -1202,8 +1423,8 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
   split_scale(P.scale, &P.scale_hi, &P.scale_lo);
   split_scale(P.aux_scale, &P.aux_scale_hi, &P.aux_scale_lo);
   const int m = g.n0 / 2;
-  const int choice = tune_get(1, type_code<T>(), m, 0, P.mode);
-  const int L = choice > 0 ? choice : lines_per_cta(m, kEPT<T>);
+  int choice = tune_get(1, type_code<T>(), m, 0, P.mode);
+  const int L = (choice > 0 && choice != kChoiceStaged) ? choice : lines_per_cta(m, kEPT<T>);
   const long long nlines = (long long)g.n1 * g.n2;
   const long long blocks = (nlines + L - 1) / L;
   const size_t smem = sizeof(cpx<T>) * (size_t)(m + (m + 2) + 2 * L * (m + 1));
@@ -1233,6 +1454,14 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
     // register-resident kernel (float; the float-pair version needs too many registers),
     // unless the tuner chose the Stockham engine for this length
     const cpx<T>* twp = reinterpret_cast<const cpx<T>*>(tw);
+    if (choice == kChoiceStaged) {
+      bool ok = false;
+      if (m == 128) ok = launch_xpass_tma<16, 8>(P, g, twp, st);
+      else if (m == 64) ok = launch_xpass_tma<8, 8>(P, g, twp, st);
+      else if (m == 256) ok = launch_xpass_tma<16, 16>(P, g, twp, st);
+      if (ok) return;
+      choice = 0;   // not a fused float program, or unaligned: the register kernel
+    }
     if (choice <= 0 && m == 128) {
       launch_xpass_r<T, 16, 8>(P, g, twp, st);
       return;

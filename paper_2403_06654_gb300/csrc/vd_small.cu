@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(NT) k_small_solve_1d(const SmallArgs a) {
 
 bool small_solve_eligible(const vd_grid* G, vd_op op, int solver, int precision, int restart) {
   if (op != VD_OP_PRESSURE || precision != VD_PREC_FP64 || G->g.ndim != 1) return false;
-  const int nt = (G->g.n0 > 512) ? 128 : 64;
+  const int nt = 128;   // four warps: every SM partition issues FP64 work
   return small_smem_bytes(G->g.n0, solver, restart, nt) <= 200 * 1024;
 }
 
@@ -582,15 +582,10 @@ vd_status small_solve_1d(const vd_grid* G, int solver, const vd_solve_params* pr
   a.maxit = prm->max_it;
   a.restart = restart;
   a.use_x0 = prm->use_x0 ? 1 : 0;
-  const int nt = (G->g.n0 > 512) ? 128 : 64;
+  const int nt = 128;   // four warps: every SM partition issues FP64 work
   const size_t smem = small_smem_bytes(G->g.n0, solver, restart, nt);
-  if (nt == 64) {
-    VD_CUDA(cudaFuncSetAttribute(k_small_solve_1d<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_small_solve_1d<64><<<1, 64, smem, st>>>(a);
-  } else {
-    VD_CUDA(cudaFuncSetAttribute(k_small_solve_1d<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_small_solve_1d<128><<<1, 128, smem, st>>>(a);
-  }
+  VD_CUDA(cudaFuncSetAttribute(k_small_solve_1d<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_small_solve_1d<128><<<1, 128, smem, st>>>(a);
   count_launch();
   VD_CUDA(cudaGetLastError());
   SmallOut o;

@@ -85,7 +85,7 @@ vd_status tune_type(const vd_grid* G, const void* tw, void* a, void* b, cudaStre
     std::vector<int> cand;
     const bool reg = type == 1 && (n == 128 || n == 256);
     if (reg) cand.push_back(0);
-    if (reg && axis == 2) cand.push_back(kChoiceStaged);
+    if (reg) cand.push_back(kChoiceStaged);
     for (int W = 1; W <= 64; W *= 2) {
       if (sizeof(cpx<T>) * (size_t)(n + 2 * W * n) > kSmemCap) break;
       if (W > 1 && W > 2 * inner) break;
@@ -128,6 +128,9 @@ vd_status tune_type(const vd_grid* G, const void* tw, void* a, void* b, cudaStre
     cand.push_back(L);
   }
   for (int mode = 0; mode <= 2; ++mode) {
+    // the fused form can also stage its input lines with TMA (float register kernels)
+    std::vector<int> cm = cand;
+    if (mode == 0 && type == 1 && (m == 64 || m == 128 || m == 256) && nlines >= 2) cm.push_back(kChoiceStaged);
     XProg X{};
     X.ncomp = 1;
     X.mode = mode;
@@ -140,7 +143,7 @@ vd_status tune_type(const vd_grid* G, const void* tw, void* a, void* b, cudaStre
     VD_CUDA(cudaGetLastError());
     int best = -1;
     float tbest = tdef * kSwitchGain;
-    for (int c : cand) {
+    for (int c : cm) {
       tune_set(1, type, m, 0, mode, c);
       const float ms = time_it([&] { launch_xpass<T>(X, g, tw, st); }, st, tm);
       VD_CUDA(cudaGetLastError());

@@ -62,7 +62,12 @@ def test_small_solve_matches_exact_and_oracle(n, solver):
     h = np.array(info["hist"])
     k = min(len(h), len(ref.history))
     assert np.allclose(h[:k], ref.history[:k], rtol=1e-6, atol=1e-14)
-    assert launches == 1   # the whole solve is one kernel
+    # the whole solve is one kernel, except GMRES(30) at n = 1024, whose 32 basis vectors do not
+    # fit in shared memory: it runs pass by pass
+    if solver == "gmres" and n > 512:
+        assert launches > 1
+    else:
+        assert launches == 1
 
 
 @pytest.mark.parametrize("solver", ["cg", "gmres", "rmr"])
