@@ -1148,8 +1148,11 @@ void tune_set(int kind, int type, int n, int axis, int dir, int choice) {
   else g_tune[tune_key(kind, type, n, axis, dir)] = choice;
 }
 
-int default_shape(int kind, int type, int n) {
+int default_shape(int kind, int type, int n, int axis) {
   const int ept = (type == 1) ? 16 : 8;
+  // float z passes of length 128/256: the TMA-staged kernel (its gain is largest on the
+  // multi-transform programs of the operators, which the tuner's single transform understates)
+  if (kind == 0 && type == 1 && axis == 2 && (n == 128 || n == 256)) return kChoiceStaged;
   if (kind == 0) return (type == 1 && (n == 128 || n == 256)) ? 0 : tile_width(n, ept);
   return (type == 1 && (n == 64 || n == 128 || n == 256)) ? 0 : lines_per_cta(n, ept);
 }
@@ -1329,6 +1332,7 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
   const int n = (P.axis == 2) ? g.pz.n : g.py.n;
   int choice = tune_get(0, type_code<T>(), n, P.axis, dir);
   const bool reg_ok = std::is_same<T, float>::value && (n == 256 || n == 128);
+  if (choice < 0) choice = default_shape(0, type_code<T>(), n, P.axis);
   if (choice == kChoiceStaged && !(reg_ok && tma_program_ok(P, g))) choice = 0;   // not applicable: register kernel
   const int W = (choice > 0 && choice != kChoiceStaged) ? choice : tile_width(n, kEPT<T>);
   long long inner_n, outer_n;

@@ -97,7 +97,7 @@ constexpr int kChoiceStaged = 128;
 int tune_get(int kind, int type, int n, int axis, int dir);
 void tune_set(int kind, int type, int n, int axis, int dir, int choice);
 int tune_table(int* out, int max);   // 6 ints per entry; returns the entry count
-int default_shape(int kind, int type, int n);   // the built-in choice (kind 1: n = n0/2)
+int default_shape(int kind, int type, int n, int axis = 0);   // the built-in choice (kind 1: n = n0/2)
 void tune_save();                    // write the table to $VD_TUNE_FILE (if set)
 
 // shared memory footprint (bytes) of the pass kernels, for the attribute setup

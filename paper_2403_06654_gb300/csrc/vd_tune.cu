@@ -114,7 +114,7 @@ vd_status tune_type(const vd_grid* G, const void* tw, void* a, void* b, cudaStre
         }
       }
       (void)reg;
-      tune_set(0, type, n, axis, dir, best >= 0 ? best : default_shape(0, type, n));
+      tune_set(0, type, n, axis, dir, best >= 0 ? best : default_shape(0, type, n, axis));
     }
   }
   // x pass: forward (mode 1), inverse (mode 2), fused (mode 0 with a weight field)

@@ -26,11 +26,18 @@ def test_set_list_erase():
 
 
 @pytest.mark.parametrize("bad", [(2, 0, 64, 1, 1, 4), (0, 3, 64, 1, 1, 4), (0, 0, 0, 1, 1, 4),
-                                 (0, 0, 64, 1, 1, 3), (0, 0, 64, 1, 1, 128)])
+                                 (0, 0, 64, 1, 1, 3), (0, 0, 64, 1, 1, 256), (0, 0, 64, 1, 1, 96)])
 def test_bad_keys_rejected(bad):
     with pytest.raises(vd.VDError) as e:
         vd.vd_autotune_set(*bad)
     assert e.value.status == vd.VD_ERR_INVALID_ARG
+
+
+def test_staged_choice_accepted():
+    """Choice 128 selects the TMA-staged kernels (float y/z passes, fused x pass)."""
+    vd.vd_autotune_set(0, 1, 256, 2, 1, 128)
+    assert (0, 1, 256, 2, 1, 128) in vd.vd_autotune_table()
+    vd.vd_autotune_set(0, 1, 256, 2, 1, -1)
 
 
 def test_file_read_by_a_fresh_process(tmp_path):
