@@ -94,13 +94,6 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
 
 __device__ __forceinline__ double pw(int k, int h0) { return (k == 0 || k == h0 - 1) ? 1.0 : 2.0; }
 
-// butterfly index of this thread in a transform stage: consecutive butterflies go to different
-// warps, so the few butterflies of a high-radix stage (16 for radix 8 at m = 128) spread over
-// every SM partition instead of one warp (FP64 issue is the limit of these solves)
-template <int NT>
-__device__ __forceinline__ int fly(int tid) {
-  return (tid & 31) * (NT / 32) + (tid >> 5);
-}
 
 // o = A (S v) with S the symbol (with_sym) or 1: i k~ F[ (1/(N rho)) F^-1( i k~ S v ) ] through the
 // x-pass arithmetic (pack, inverse complex FFT of length m, weight, forward FFT, unpack, 1/2)
@@ -119,13 +112,13 @@ __device__ void apply1d(const SmallSmem& s, const GridDesc& g, const cpx<double>
     const cpx<double> Xc = conjg(s.B[m - k]);
     s.A[k] = (X + Xc) + mul_i(cmulc(X - Xc, s.pk[k]));
   }
-  cpx<double>* res = fft_lines<double, +1>(s.A, s.B, 1, 0, fly<NT>(tid), NT, g.px, s.twm);
+  cpx<double>* res = fft_lines<double, +1>(s.A, s.B, 1, 0, tid, NT, g.px, s.twm);
   for (int j = tid; j < m; j += NT) {
     const cpx<double> z = res[j];
     res[j] = mk<double>(z.x * s.rinv[2 * j], z.y * s.rinv[2 * j + 1]);
   }
   cpx<double>* other = (res == s.A) ? s.B : s.A;
-  res = fft_lines<double, -1>(res, other, 1, 0, fly<NT>(tid), NT, g.px, s.twm);
+  res = fft_lines<double, -1>(res, other, 1, 0, tid, NT, g.px, s.twm);
   for (int k = tid; k <= m; k += NT) {
     const cpx<double> Z = res[k == m ? 0 : k];
     const cpx<double> Zc = conjg(res[k == 0 ? 0 : m - k]);
@@ -141,7 +134,7 @@ __device__ void forward1d(const SmallSmem& s, const GridDesc& g, const double* f
   const int m = g.n0 / 2, tid = threadIdx.x;
   __syncthreads();
   for (int j = tid; j < m; j += NT) s.A[j] = mk<double>(f[2 * j], f[2 * j + 1]);
-  cpx<double>* res = fft_lines<double, -1>(s.A, s.B, 1, 0, fly<NT>(tid), NT, g.px, s.twm);
+  cpx<double>* res = fft_lines<double, -1>(s.A, s.B, 1, 0, tid, NT, g.px, s.twm);
   for (int k = tid; k <= m; k += NT) {
     const cpx<double> Z = res[k == m ? 0 : k];
     const cpx<double> Zc = conjg(res[k == 0 ? 0 : m - k]);
@@ -160,7 +153,7 @@ __device__ void inverse1d(const SmallSmem& s, const GridDesc& g, const cpx<doubl
     const cpx<double> Xc = conjg(v[m - k]);
     s.A[k] = (X + Xc) + mul_i(cmulc(X - Xc, s.pk[k]));
   }
-  cpx<double>* res = fft_lines<double, +1>(s.A, s.B, 1, 0, fly<NT>(tid), NT, g.px, s.twm);
+  cpx<double>* res = fft_lines<double, +1>(s.A, s.B, 1, 0, tid, NT, g.px, s.twm);
   const double sc = 1.0 / (double)g.nreal;
   for (int j = tid; j < m; j += NT) {
     const cpx<double> z = scal(res[j], sc);
