@@ -237,6 +237,7 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 
 
 constexpr int kRLines = 16;
 constexpr int kTmaMaxIn = 4;   // inputs a TMA-staged program may read
+constexpr int kPairCols = 18;  // columns of a y-pass box (16 + 2: a 16-byte aligned start for odd rows)
 
 template <typename T, int S, int N1, int N2>
 __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(const AxisProg P, const GridDesc g,
@@ -389,11 +390,14 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(con
 // (cp.async.bulk.tensor, one box of N rows x 128 bytes) into a shared-memory buffer while the
 // current item is transformed and stored, so loads stay in flight without registers.
 // A z tile is a box of the field viewed as a 2D tensor [n2][2 n1 h0] of floats: its rows
-// (z planes) are n1 h0 8 bytes apart, a multiple of 16 for even n1.  A y tile is a box of the
-// 3D tensor [n2][n1][2 h0]: its rows are 8 h0 bytes apart, a multiple of 16 only for even h0
-// (n0 = 2 mod 4); with odd h0 the y passes keep the register kernel.  A tile starts at a
-// multiple of 128 bytes.  Columns past the end of a plane arrive as zeros (box fill) and are
-// neither transformed into anything stored nor written.
+// (z planes) are n1 h0 8 bytes apart, a multiple of 16 for even n1.  A y row is 8 h0 bytes, not
+// a multiple of 16 when h0 is odd (n0 a multiple of 4), so a y tile is fetched as two boxes of
+// the plane viewed as n1/2 "pair rows" (y rows 2r and 2r+1 back to back, 16 h0 bytes): the even
+// rows from the pair row's column col0, the odd rows from column h0 + col0 - 1 (one column early
+// when h0 is odd, so that the box starts on a 16-byte boundary; 18 columns wide).  A tile starts
+// at a multiple of 128 bytes.  Columns past the end of a row or plane arrive as zeros (box fill)
+// or belong to the neighbouring row; they are neither transformed into anything stored nor
+// written.
 // Every wait on the transfer barrier is bounded; a block that gives up raises the grid's error
 // word (reported by the solve as VD_ERR_TIMEOUT), waits (bounded) for its own transfer in
 // flight and returns.
@@ -457,13 +461,15 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
   constexpr int C = N1 / N2;
   constexpr int LS = N + 1;
   constexpr int NT = kRLines * N2;
-  constexpr unsigned kBoxBytes = (unsigned)(N * kRLines * sizeof(cpx<T>));
+  // staged tile: z pass, one box of N rows x 16 columns; y pass, two boxes of N/2 pair rows x 18
+  // columns (even and odd y rows, see below)
+  constexpr unsigned kBoxBytes = (unsigned)(N * (AX == 2 ? kRLines : kPairCols) * sizeof(cpx<T>));
   extern __shared__ __align__(1024) unsigned char smem_tma[];
   unsigned char* smem_raw = smem_tma;
   if (P.done && *P.done) return;
   constexpr int axis = AX;   // 1 = y, 2 = z (compiled apart: the z form keeps its register budget)
   const FftPlan& pl = (axis == 2) ? g.pz : g.py;
-  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);                       // N rows x 16 columns
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);                       // the staged tile
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + kBoxBytes);
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw + kBoxBytes + 16);
   cpx<T>* Y = tw + N;
@@ -493,13 +499,22 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
     const int col0 = (tile - o * tpp) * kRLines;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, kBoxBytes);
-    if (axis == 2) tma_load_2d(buf, &maps.m[P.xf[x].src], 2 * col0, 0, bar);
-    else tma_load_3d(buf, &maps.m[P.xf[x].src], 2 * col0, 0, o, bar);
+    if (axis == 2) {
+      tma_load_2d(buf, &maps.m[P.xf[x].src], 2 * col0, 0, bar);
+    } else {
+      // even y rows: columns col0.. of the first half of each pair row; odd y rows: from column
+      // h0 - (h0 & 1) + col0 of the pair row, one column early when h0 is odd (16-byte start)
+      tma_load_3d(buf, &maps.m[P.xf[x].src], 2 * col0, 0, o, bar);
+      tma_load_3d(buf + (N / 2) * kPairCols, &maps.m[P.xf[x].src], 2 * (g.h0 - (g.h0 & 1) + col0), 0, o, bar);
+    }
   };
   if (tid == 0) issue(0);
   const T kfa = kfac_t<T>(g, axis);
   const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr);
   cpx<T>* Yl = Y + w * LS;
+  // y pass: this thread's rows all have the parity of t (N2 is even): even rows in the first
+  // box, odd rows in the second, whose column 0 is the row's column -1 when h0 is odd
+  const cpx<T>* ybase = (t & 1) ? buf + (N / 2) * kPairCols + (g.h0 & 1) : buf;
 
   for (int it = 0; it < nitems; ++it) {
     const int tile = (int)blockIdx.x + (it / nx) * (int)gridDim.x;
@@ -547,7 +562,7 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
 #pragma unroll
     for (int j = 0; j < N1; ++j) {
       const int i = N2 * j + t;
-      u[j] = buf[i * kRLines + w];
+      u[j] = (AX == 2) ? buf[i * kRLines + w] : ybase[(i >> 1) * kPairCols + w];
       if (xf.pre) {
         u[j] = scal(u[j], mult(xf.pre, i, gbase + i * line_stride, T(1)));
         if (xf.pre & MUL_IK) u[j] = mul_i(u[j]);
@@ -1272,11 +1287,13 @@ static bool encode_tiles(CUtensorMap* m, const void* base, const GridDesc& g, in
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   }
-  if (row % 16) return false;
-  cuuint64_t dims[3] = {2 * (cuuint64_t)g.h0, (cuuint64_t)g.n1, (cuuint64_t)g.n2};
-  cuuint64_t strides[2] = {row, row * (cuuint64_t)g.n1};
-  cuuint32_t box[3] = {2 * kRLines, (cuuint32_t)N, 1};
+  // y pass: each z plane viewed as n1/2 pair rows (y rows 2r and 2r+1 back to back, 16 h0 bytes:
+  // 16-byte aligned whatever the parity of h0), boxes of 18 columns x N/2 pair rows
+  cuuint64_t dims[3] = {4 * (cuuint64_t)g.h0, (cuuint64_t)(g.n1 / 2), (cuuint64_t)g.n2};
+  cuuint64_t strides[2] = {2 * row, row * (cuuint64_t)g.n1};
+  cuuint32_t box[3] = {2 * kPairCols, (cuuint32_t)(N / 2), 1};
   cuuint32_t es[3] = {1, 1, 1};
+  if ((g.n1 & 1) || strides[0] % 16 || strides[1] % 16) return false;
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -1295,11 +1312,10 @@ static int sm_count() {
   return cached[dev];
 }
 
-// the TMA-staged kernel takes programs whose transforms all run an FFT and read in[0..3]; a y
-// pass needs rows on 16-byte boundaries (even h0)
+// the TMA-staged kernel takes programs whose transforms all run an FFT and read in[0..3]
 static bool tma_program_ok(const AxisProg& P, const GridDesc& g) {
   if (P.conv_in || P.conv_out) return false;
-  if (P.axis == 1 && (g.h0 & 1)) return false;
+  if (P.axis == 1 && (g.n1 & 1)) return false;
   for (int t = 0; t < P.nxf; ++t)
     if (P.xf[t].nofft || P.xf[t].src >= kTmaMaxIn) return false;
   return P.nxf > 0;
@@ -1319,7 +1335,8 @@ static bool launch_axis_tma(const AxisProg& P, const GridDesc& g, const cpx<floa
   const long long tiles = ((cols + kRLines - 1) / kRLines) * (P.axis == 2 ? 1 : g.n2);
   const int per_sm = (N2 == 16) ? 3 : 6;
   const long long blocks = std::min<long long>(tiles, (long long)per_sm * sm_count());
-  const size_t smem = sizeof(cpx<float>) * (size_t)(N * kRLines) + 16 + sizeof(cpx<float>) * (size_t)(N + kRLines * (N + 1));
+  const size_t stage = sizeof(cpx<float>) * (size_t)(N * (AX == 2 ? kRLines : kPairCols));
+  const size_t smem = stage + 16 + sizeof(cpx<float>) * (size_t)(N + kRLines * (N + 1));
   ensure_smem(reinterpret_cast<const void*>(k_axis_tma<S, N1, N2, AX>), smem);
   k_axis_tma<S, N1, N2, AX><<<(unsigned)blocks, kRLines * N2, smem, st>>>(P, g, tw, maps);
   return true;

@@ -6,8 +6,8 @@ loads), so every result must be bit-for-bit the same: plain float transforms (fo
 inverse z passes), and whole mixed-precision solves whose inner operator chains use the y and
 z passes with derivative, symbol and accumulating transforms.  Grids cover lengths 128 and 256,
 planes whose column count is not a multiple of the 16-column tile (box fill at the end), odd
-and even h0 (y passes are staged only for even h0), 2D and 3D, and the transforms are also
-checked against the oracle's DFT.
+and even h0 (the odd-row box of a y tile starts one column early when h0 is odd), 2D and 3D,
+and the transforms are also checked against the oracle's DFT.
 """
 
 import math
@@ -60,10 +60,11 @@ def test_staged_transforms_bitwise_equal_register_kernel(n, L):
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-5
 
 
-# y passes are staged where the rows of their inputs start on 16-byte boundaries: an even h0
-# (n0 = 30, 90: h0 = 16, 46); with odd h0 they fall back to the register kernel
+# y tiles are two pair-row boxes, one column early for the odd rows when h0 is odd: both
+# parities of h0 (n0 = 30, 90: h0 = 16, 46; n0 = 32, 64: h0 = 17, 33), y lengths 128 and 256
 SOLVE_GRIDS = [((32, 24, 256), (2 * math.pi, 1.0, 2 * math.pi)), ((30, 128, 128), (2 * math.pi,) * 3),
-               ((90, 256, 16), (2 * math.pi, 2.0, 1.0)), ((30, 256), (2 * math.pi, 3.0)), ((64, 256), (1.0, 3.0))]
+               ((32, 128, 128), (2 * math.pi, 1.0, 2.0)), ((90, 256, 16), (2 * math.pi, 2.0, 1.0)),
+               ((30, 256), (2 * math.pi, 3.0)), ((64, 256), (1.0, 3.0))]
 
 
 @pytest.mark.parametrize("precision", ["mixed", "mixed_dd"])
