@@ -239,6 +239,55 @@ constexpr int kRLines = 16;
 constexpr int kTmaMaxIn = 4;   // inputs a TMA-staged program may read
 constexpr int kPairCols = 18;  // columns of a y-pass box (16 + 2: a 16-byte aligned start for odd rows)
 
+// The common multipliers (none, or i k~ along the axis) with a scale of one, in loops of their
+// own, so that the flag tests and the wavenumber arithmetic of the general case stay out of the
+// unrolled element loops.  katab[i] = k~ of index i along the axis, the same float product the
+// general case forms; x * 1 is exact, so both paths give the same bits.
+template <typename T, int N1, int N2>
+__device__ __forceinline__ void pre_ik(cpx<T>* u, int t, const T* katab) {
+#pragma unroll
+  for (int j = 0; j < N1; ++j) u[j] = mul_i(scal(u[j], katab[N2 * j + t]));
+}
+
+// row k1 + N1 k2 of a line <- v[k2] (times i k~ if IK), added to what the row holds unless FIRST
+// (partial sums read in batches of 4 before their stores, so that their latencies overlap)
+template <typename T, int N1, int N2, bool IK, bool FIRST>
+__device__ __forceinline__ void store_rows(cpx<T>* __restrict__ q, int gbase, int ls, int k1, const cpx<T>* v,
+                                           const T* katab) {
+  constexpr int PB = N2 < 4 ? N2 : 4;
+#pragma unroll
+  for (int k0 = 0; k0 < N2; k0 += PB) {
+    cpx<T> prev[PB];
+    if constexpr (!FIRST) {
+#pragma unroll
+      for (int b = 0; b < PB; ++b) prev[b] = q[gbase + (k1 + N1 * (k0 + b)) * ls];
+    }
+#pragma unroll
+    for (int b = 0; b < PB; ++b) {
+      const int i = k1 + N1 * (k0 + b);
+      cpx<T> vv = v[k0 + b];
+      if constexpr (IK) vv = mul_i(scal(vv, katab[i]));
+      if constexpr (FIRST) q[gbase + i * ls] = vv;
+      else q[gbase + i * ls] = prev[b] + vv;
+    }
+  }
+}
+
+// the store of one output line: the common cases, or false for the general one
+template <typename T, int N1, int N2>
+__device__ __forceinline__ bool store_rows_common(const Xf& xf, T scale, cpx<T>* q, int gbase, int ls, int k1,
+                                                  const cpx<T>* v, const T* katab) {
+  if (scale != T(1) || (xf.post != 0 && xf.post != MUL_IK)) return false;
+  if (xf.post == 0) {
+    if (xf.first) store_rows<T, N1, N2, false, true>(q, gbase, ls, k1, v, katab);
+    else store_rows<T, N1, N2, false, false>(q, gbase, ls, k1, v, katab);
+  } else {
+    if (xf.first) store_rows<T, N1, N2, true, true>(q, gbase, ls, k1, v, katab);
+    else store_rows<T, N1, N2, true, false>(q, gbase, ls, k1, v, katab);
+  }
+  return true;
+}
+
 template <typename T, int S, int N1, int N2>
 __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(const AxisProg P, const GridDesc g,
                                                         const cpx<T>* __restrict__ twg) {
@@ -252,10 +301,18 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(con
   const FftPlan& pl = (axis == 2) ? g.pz : g.py;
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* Y = tw + N;
+  T* katab = reinterpret_cast<T*>(Y + kRLines * LS);   // k~ of every index along the axis
   const int tid = threadIdx.x;
-  for (int j = tid; j < N; j += kRLines * N2) tw[j] = twg[pl.tw_off + j];
-  __syncthreads();   // the twiddle table is read by every thread before the first transpose
+  const T kfa = kfac_t<T>(g, axis);
+  for (int j = tid; j < N; j += kRLines * N2) {
+    tw[j] = twg[pl.tw_off + j];
+    katab[j] = kfa * (T)freq_tilde(j, N);
+  }
+  __syncthreads();   // the tables are read by every thread before the first transpose
 
+  // lines: z pass, the columns of the flattened (y, x) plane; y pass, the x columns of each z
+  // plane (tiles of 16 columns, the last one of a plane ragged: numbering the lines across
+  // plane boundaries instead, so that no tile is ragged, measured slower)
   int line_stride, inner_n, outer_stride;
   if (axis == 2) {
     line_stride = g.n1 * g.h0;
@@ -290,7 +347,6 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(con
       kperp2 += kz * kz;
     }
   }
-  const T kfa = kfac_t<T>(g, axis);
   auto mult = [&](int flags, int i, int go, T base) -> T {
     const T ka = kfa * (T)freq_tilde(i, N);
     T c = base;
@@ -325,10 +381,15 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(con
 #pragma unroll
     for (int j = 0; j < N1; ++j) {
       const int i = N2 * j + t;
-      const int go = gbase + i * line_stride;
-      u[j] = colok ? ld_el<T>(src, cin, go) : mk<T>(T(0), T(0));
-      if (xf.pre) {
-        u[j] = scal(u[j], mult(xf.pre, i, go, T(1)));
+      u[j] = colok ? ld_el<T>(src, cin, gbase + i * line_stride) : mk<T>(T(0), T(0));
+    }
+    if (xf.pre == MUL_IK) {
+      pre_ik<T, N1, N2>(u, t, katab);
+    } else if (xf.pre && colok) {   // (lines past the end read no symbol)
+#pragma unroll
+      for (int j = 0; j < N1; ++j) {
+        const int i = N2 * j + t;
+        u[j] = scal(u[j], mult(xf.pre, i, gbase + i * line_stride, T(1)));
         if (xf.pre & MUL_IK) u[j] = mul_i(u[j]);
       }
     }
@@ -349,7 +410,8 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(con
 #pragma unroll
       for (int n2 = 0; n2 < N2; ++n2) v[n2] = Yl[n2 * N1 + k1];
       dftR<T, S, N2>(v);
-      if (colok) {
+      if (colok && !store_rows_common<T, N1, N2>(xf, scale, reinterpret_cast<cpx<T>*>(dst), gbase, line_stride, k1,
+                                                  v, katab)) {
         // a transform that accumulates reads all of its partial sums before its first store,
         // so their latencies overlap (the compiler cannot move a load of dst above a store to
         // dst); the partials were written by this thread, so the order is unchanged
@@ -473,8 +535,13 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + kBoxBytes);
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw + kBoxBytes + 16);
   cpx<T>* Y = tw + N;
+  T* katab = reinterpret_cast<T*>(Y + kRLines * LS);   // k~ of every index along the axis
   const int tid = threadIdx.x;
-  for (int j = tid; j < N; j += NT) tw[j] = twg[pl.tw_off + j];
+  const T kfa = kfac_t<T>(g, axis);
+  for (int j = tid; j < N; j += NT) {
+    tw[j] = twg[pl.tw_off + j];
+    katab[j] = kfa * (T)freq_tilde(j, N);
+  }
   if (tid == 0) mbar_init(bar, 1);
   __syncthreads();
 
@@ -509,7 +576,6 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
     }
   };
   if (tid == 0) issue(0);
-  const T kfa = kfac_t<T>(g, axis);
   const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr);
   cpx<T>* Yl = Y + w * LS;
   // y pass: this thread's rows all have the parity of t (N2 is even): even rows in the first
@@ -523,19 +589,21 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
     const int col = (tile - o * tpp) * kRLines + w;
     const bool colok = col < inner_n;
     const int gbase = o * outer_stride + col;
-    T kperp2;
-    if (axis == 2) {
-      const int kyi = col / g.h0;
-      const int kxi = col - kyi * g.h0;
-      const T kx = kfac_t<T>(g, 0) * (T)freq_tilde(kxi, g.n0);
-      const T ky = kfac_t<T>(g, 1) * (T)freq_tilde(kyi, g.n1);
-      kperp2 = kx * kx + ky * ky;
-    } else {
-      const T kx = kfac_t<T>(g, 0) * (T)freq_tilde(col, g.n0);
-      kperp2 = kx * kx;
-      if (g.ndim == 3) {
-        const T kz = kfac_t<T>(g, 2) * (T)freq_tilde(o, g.n2);
-        kperp2 += kz * kz;
+    T kperp2 = T(0);   // the perpendicular |k~|^2 of this line, for the multipliers that need it
+    if ((xf.pre | xf.post) & MUL_NEGK2) {
+      if (axis == 2) {
+        const int kyi = col / g.h0;
+        const int kxi = col - kyi * g.h0;
+        const T kx = kfac_t<T>(g, 0) * (T)freq_tilde(kxi, g.n0);
+        const T ky = kfac_t<T>(g, 1) * (T)freq_tilde(kyi, g.n1);
+        kperp2 = kx * kx + ky * ky;
+      } else {
+        const T kx = kfac_t<T>(g, 0) * (T)freq_tilde(col, g.n0);
+        kperp2 = kx * kx;
+        if (g.ndim == 3) {
+          const T kz = kfac_t<T>(g, 2) * (T)freq_tilde(o, g.n2);
+          kperp2 += kz * kz;
+        }
       }
     }
     auto mult = [&](int flags, int i, int go, T base) -> T {
@@ -563,7 +631,13 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
     for (int j = 0; j < N1; ++j) {
       const int i = N2 * j + t;
       u[j] = (AX == 2) ? buf[i * kRLines + w] : ybase[(i >> 1) * kPairCols + w];
-      if (xf.pre) {
+    }
+    if (xf.pre == MUL_IK) {
+      pre_ik<T, N1, N2>(u, t, katab);
+    } else if (xf.pre && colok) {   // (columns past the end read no symbol)
+#pragma unroll
+      for (int j = 0; j < N1; ++j) {
+        const int i = N2 * j + t;
         u[j] = scal(u[j], mult(xf.pre, i, gbase + i * line_stride, T(1)));
         if (xf.pre & MUL_IK) u[j] = mul_i(u[j]);
       }
@@ -588,7 +662,8 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
 #pragma unroll
       for (int n2 = 0; n2 < N2; ++n2) v[n2] = Yl[n2 * N1 + k1];
       dftR<T, S, N2>(v);
-      if (colok) {
+      if (colok && !store_rows_common<T, N1, N2>(xf, scale, reinterpret_cast<cpx<T>*>(dst), gbase, line_stride, k1,
+                                                  v, katab)) {
         cpx<T>* q = reinterpret_cast<cpx<T>*>(dst);
         constexpr int PB = N2 < 4 ? N2 : 4;
 #pragma unroll
@@ -1244,7 +1319,7 @@ template <typename T, int S, int N1, int N2>
 static void launch_axis_r(const AxisProg& P, const GridDesc& g, const cpx<T>* tw, long long inner_n,
                           long long outer_n, cudaStream_t st) {
   const long long blocks = outer_n * ((inner_n + kRLines - 1) / kRLines);
-  const size_t smem = sizeof(cpx<T>) * (size_t)(N1 * N2 + kRLines * (N1 * N2 + 1));
+  const size_t smem = sizeof(cpx<T>) * (size_t)(N1 * N2 + kRLines * (N1 * N2 + 1)) + sizeof(T) * (size_t)(N1 * N2);
   ensure_smem(reinterpret_cast<const void*>(k_axis_r<T, S, N1, N2>), smem);
   k_axis_r<T, S, N1, N2><<<(unsigned)blocks, kRLines * N2, smem, st>>>(P, g, tw);
 }
@@ -1312,13 +1387,18 @@ static int sm_count() {
   return cached[dev];
 }
 
-// the TMA-staged kernel takes programs whose transforms all run an FFT and read in[0..3]
+// The TMA-staged kernel takes programs whose transforms all run an FFT and read in[0..3].  It
+// fetches the input of the next (tile, transform) item while the current one stores, so no
+// transform may read a field that an earlier transform of the program writes.
 static bool tma_program_ok(const AxisProg& P, const GridDesc& g) {
-  if (P.conv_in || P.conv_out) return false;
+  if (P.conv_in || P.conv_out || P.nxf <= 0) return false;
   if (P.axis == 1 && (g.n1 & 1)) return false;
   for (int t = 0; t < P.nxf; ++t)
     if (P.xf[t].nofft || P.xf[t].src >= kTmaMaxIn) return false;
-  return P.nxf > 0;
+  for (int b = 1; b < P.nxf; ++b)
+    for (int a = 0; a < b; ++a)
+      if (P.in[P.xf[b].src] == P.out[P.xf[a].dst]) return false;
+  return true;
 }
 
 template <int S, int N1, int N2, int AX>
@@ -1336,7 +1416,7 @@ static bool launch_axis_tma(const AxisProg& P, const GridDesc& g, const cpx<floa
   const int per_sm = (N2 == 16) ? 3 : 6;
   const long long blocks = std::min<long long>(tiles, (long long)per_sm * sm_count());
   const size_t stage = sizeof(cpx<float>) * (size_t)(N * (AX == 2 ? kRLines : kPairCols));
-  const size_t smem = stage + 16 + sizeof(cpx<float>) * (size_t)(N + kRLines * (N + 1));
+  const size_t smem = stage + 16 + sizeof(cpx<float>) * (size_t)(N + kRLines * (N + 1)) + sizeof(float) * (size_t)N;
   ensure_smem(reinterpret_cast<const void*>(k_axis_tma<S, N1, N2, AX>), smem);
   k_axis_tma<S, N1, N2, AX><<<(unsigned)blocks, kRLines * N2, smem, st>>>(P, g, tw, maps);
   return true;
@@ -1351,7 +1431,7 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
   const bool reg_ok = std::is_same<T, float>::value && (n == 256 || n == 128);
   if (choice < 0) choice = default_shape(0, type_code<T>(), n, P.axis);
   if (choice == kChoiceStaged && !(reg_ok && tma_program_ok(P, g))) choice = 0;   // not applicable: register kernel
-  const int W = (choice > 0 && choice != kChoiceStaged) ? choice : tile_width(n, kEPT<T>);
+  const int W = (choice > 0 && choice <= 64) ? choice : tile_width(n, kEPT<T>);
   long long inner_n, outer_n;
   if (P.axis == 2) {
     inner_n = (long long)g.n1 * g.h0;
@@ -1445,7 +1525,7 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
   split_scale(P.aux_scale, &P.aux_scale_hi, &P.aux_scale_lo);
   const int m = g.n0 / 2;
   int choice = tune_get(1, type_code<T>(), m, 0, P.mode);
-  const int L = (choice > 0 && choice != kChoiceStaged) ? choice : lines_per_cta(m, kEPT<T>);
+  const int L = (choice > 0 && choice <= 64) ? choice : lines_per_cta(m, kEPT<T>);
   const long long nlines = (long long)g.n1 * g.n2;
   const long long blocks = (nlines + L - 1) / L;
   const size_t smem = sizeof(cpx<T>) * (size_t)(m + (m + 2) + 2 * L * (m + 1));

@@ -91,7 +91,7 @@ void launch_xpass(const XProg& P, const GridDesc& g, const void* tw, cudaStream_
 // launch-shape table (vd_passes.cu).  kind 0: y/z pass (key: type, length, axis, direction);
 // kind 1: x pass (key: type, n0/2, axis 0, mode).  type: 0 double, 1 float, 2 float-pair.
 // choice: 0 register four-step kernel, > 0 lines per block, < 0 (get) absent / (set) erase.
-// kind 0 choice kChoiceStaged: the register kernel with TMA-staged input (float z passes of
+// kind 0 choice kChoiceStaged: the register kernel with TMA-staged input (float y/z passes of
 // length 128 / 256)
 constexpr int kChoiceStaged = 128;
 int tune_get(int kind, int type, int n, int axis, int dir);
