@@ -288,6 +288,34 @@ __device__ __forceinline__ bool store_rows_common(const Xf& xf, T scale, cpx<T>*
   return true;
 }
 
+// Twiddles W_m^{t k1} (k1 in [1, M1)) of one thread's first four-step layer.  Float: as the
+// product W_m^{4 t a} W_m^{t b} (k1 = 4 a + b) of six values read once per kernel (one float
+// complex product, within ~1.5 ulp of the table), so that the x pass does not read a twiddle
+// from shared memory per element; other types: the table.
+template <typename T, int M1>
+struct StepTw {
+  const cpx<T>* tw;
+  int t;
+  __device__ __forceinline__ StepTw(const cpx<T>* tab, int tt) : tw(tab), t(tt) {}
+  __device__ __forceinline__ cpx<T> operator()(int k1) const { return tw[t * k1]; }
+};
+template <int M1>
+struct StepTw<float, M1> {
+  cpx<float> a[M1 / 4], b[4];   // a[i] = W^{4 t i}, b[i] = W^{t i}
+  __device__ __forceinline__ StepTw(const cpx<float>* tab, int t) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = tab[t * i];
+#pragma unroll
+    for (int i = 0; i < M1 / 4; ++i) a[i] = tab[4 * t * i];
+  }
+  __device__ __forceinline__ cpx<float> operator()(int k1) const {
+    const int i = k1 >> 2, j = k1 & 3;
+    if (i == 0) return b[j];
+    if (j == 0) return a[i];
+    return cmul(a[i], b[j]);
+  }
+};
+
 template <typename T, int S, int N1, int N2>
 __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 2)) k_axis_r(const AxisProg P, const GridDesc g,
                                                         const cpx<T>* __restrict__ twg) {
@@ -844,6 +872,57 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)
 // stride LS chosen so the transposes are free of bank conflicts).
 // ---------------------------------------------------------------------------------------
 
+// cos and sin of pi q / M1 (M1 = 8 or 16), q in [0, M1): a switch on a constant index after
+// unrolling, so the values become immediates
+template <int M1>
+__device__ __forceinline__ float cospi_q(int q) {
+  if constexpr (M1 == 8) {
+    switch (q) {
+      case 0: return 1.0f;
+      case 1: return 0.923879533f;
+      case 2: return 0.707106781f;
+      case 3: return 0.382683432f;
+      case 4: return 0.0f;
+      case 5: return -0.382683432f;
+      case 6: return -0.707106781f;
+      default: return -0.923879533f;
+    }
+  } else {
+    switch (q) {
+      case 0: return 1.0f;
+      case 1: return 0.980785280f;
+      case 2: return 0.923879533f;
+      case 3: return 0.831469612f;
+      case 4: return 0.707106781f;
+      case 5: return 0.555570233f;
+      case 6: return 0.382683432f;
+      case 7: return 0.195090322f;
+      case 8: return 0.0f;
+      case 9: return -0.195090322f;
+      case 10: return -0.382683432f;
+      case 11: return -0.555570233f;
+      case 12: return -0.707106781f;
+      case 13: return -0.831469612f;
+      case 14: return -0.923879533f;
+      default: return -0.980785280f;
+    }
+  }
+}
+template <int M1>
+__device__ __forceinline__ float sinpi_q(int q) {
+  return (q == 0) ? 0.0f : cospi_q<M1>((q + M1 / 2) % M1) * ((q + M1 / 2 >= M1) ? -1.0f : 1.0f) * -1.0f;
+}
+
+// Packing twiddle W_{n0}^k of the float register x passes for k = M2 q + t (n0 = 2 M1 M2):
+// W_{n0}^{M2 q} = exp(-i pi q / M1) from compile-time constants times this thread's W_{n0}^t
+// (one float complex product, within ~1 ulp of the table value) instead of a shared-memory
+// read per element: the x pass is limited by its shared-memory instruction rate.
+template <int M1>
+__device__ __forceinline__ cpx<float> pk_q(int q, cpx<float> wt) {
+  const float c = cospi_q<M1>(q), s = sinpi_q<M1>(q);   // W_{n0}^{M2 q} = c - i s
+  return mk<float>(c * wt.x + s * wt.y, c * wt.y - s * wt.x);
+}
+
 template <typename T, int M1, int M2>
 struct XR {
   static constexpr int M = M1 * M2;
@@ -857,13 +936,13 @@ struct XR {
 // one four-step transform of length M1*M2 on registers u[M1] (input z[M2 q + t] in u[q]);
 // on return u[c + C k2] = output[t + M2 c + M1 k2].  Yl: this line's buffer.
 template <typename T, int S, int M1, int M2>
-__device__ __forceinline__ void fourstep(cpx<T> (&u)[M1], cpx<T>* Yl, const cpx<T>* tw, int t) {
+__device__ __forceinline__ void fourstep(cpx<T> (&u)[M1], cpx<T>* Yl, const StepTw<T, M1>& tw, int t) {
   constexpr int RS = M1 + 1;
   constexpr int C = M1 / M2;
   dftR<T, S, M1>(u);
 #pragma unroll
   for (int k1 = 1; k1 < M1; ++k1) {
-    const cpx<T> w = tw[t * k1];
+    const cpx<T> w = tw(k1);
     u[k1] = (S < 0) ? cmul(u[k1], w) : cmulc(u[k1], w);
   }
   __syncthreads();
@@ -918,6 +997,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_xpass_r(const
     return v;
   };
 
+  __syncthreads();   // the tables are complete
+  const StepTw<T, M1> stw(twm, t);
   for (int c = 0; c < P.ncomp; ++c) {
     const int cin = (P.conv_in >> c) & 1, cout = (P.conv_out >> c) & 1;
     cpx<T> u[M1];
@@ -944,9 +1025,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_xpass_r(const
         const int j = M2 * q + t;
         const cpx<T> Xv = Yl[j];
         const cpx<T> Xc = conjg(Yl[M - j]);
-        u[q] = (Xv + Xc) + mul_i(cmulc(Xv - Xc, pk[j]));
+        cpx<T> w;
+        if constexpr (std::is_same<T, float>::value) w = pk_q<M1>(q, pk[t]);
+        else w = pk[j];
+        u[q] = (Xv + Xc) + mul_i(cmulc(Xv - Xc, w));
       }
-      fourstep<T, +1, M1, M2>(u, Yl, twm, t);
+      fourstep<T, +1, M1, M2>(u, Yl, stw, t);
       if (P.mode == 2) {
         if (lok) {
 #pragma unroll
@@ -973,7 +1057,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_xpass_r(const
         }
       }
     }
-    fourstep<T, -1, M1, M2>(u, Yl, twm, t);
+    fourstep<T, -1, M1, M2>(u, Yl, stw, t);
     // unpack the length-m spectrum into the half spectrum
     __syncthreads();
 #pragma unroll
@@ -982,10 +1066,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_xpass_r(const
     if (lok) {
       const int post = P.post[c];
       // entries k = t + M2 q (q < M1) and, for thread 0, k = M: a fixed count, unrolled
-      auto unpack = [&](int k) {
+      auto unpack = [&](int k, cpx<T> w) {
         const cpx<T> Z = Yl[k == M ? 0 : k];
         const cpx<T> Zc = conjg(Yl[k == 0 ? 0 : M - k]);
-        cpx<T> Xv = (Z + Zc) - mul_i(cmul(Z - Zc, pk[k]));
+        cpx<T> Xv = (Z + Zc) - mul_i(cmul(Z - Zc, w));
         T cc = scale;
         if (post) {
           const T kx = kfx * (T)freq_tilde(k, g.n0);
@@ -998,8 +1082,11 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_xpass_r(const
         st_el<T>(P.out[c], cout, lb + k, Xv, true);
       };
 #pragma unroll
-      for (int q = 0; q < M1; ++q) unpack(t + M2 * q);
-      if (t == 0) unpack(M);
+      for (int q = 0; q < M1; ++q) {
+        if constexpr (std::is_same<T, float>::value) unpack(t + M2 * q, pk_q<M1>(q, pk[t]));
+        else unpack(t + M2 * q, pk[t + M2 * q]);
+      }
+      if (t == 0) unpack(M, pk[M]);
     }
   }
 }
@@ -1061,6 +1148,7 @@ __global__ void __launch_bounds__(256, 3) k_xpass_tma(const XProg P, const GridD
   if (tid == 0) issue(0);
   const int line = tid / M2;
   const int t = tid % M2;
+  const StepTw<T, M1> stw(twm, t);   // (the tables were completed before the first barrier)
   cpx<T>* Yl = buf + line * LS;
   const cpx<T>* Sl = stage + line * pitch;
   const T kfx = kfac_t<T>(g, 0);
@@ -1100,12 +1188,12 @@ __global__ void __launch_bounds__(256, 3) k_xpass_tma(const XProg P, const GridD
       const int j = M2 * q + t;
       const cpx<T> Xv = premul(j, Sl[j]);
       const cpx<T> Xc = conjg(premul(M - j, Sl[M - j]));
-      u[q] = (Xv + Xc) + mul_i(cmulc(Xv - Xc, pk[j]));
+      u[q] = (Xv + Xc) + mul_i(cmulc(Xv - Xc, pk_q<M1>(q, pk[t])));
     }
     // the stage is consumed: it takes the next item's lines while this one is transformed
     __syncthreads();
     if (tid == 0 && it + 1 < nitems) issue(it + 1);
-    fourstep<T, +1, M1, M2>(u, Yl, twm, t);
+    fourstep<T, +1, M1, M2>(u, Yl, stw, t);
     if (P.wfield && lok) {
       if (P.wf_dd) {
         const float4* __restrict__ wf4 = reinterpret_cast<const float4*>(P.wfield) + rb;
@@ -1123,16 +1211,16 @@ __global__ void __launch_bounds__(256, 3) k_xpass_tma(const XProg P, const GridD
         }
       }
     }
-    fourstep<T, -1, M1, M2>(u, Yl, twm, t);
+    fourstep<T, -1, M1, M2>(u, Yl, stw, t);
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < M1; ++q) Yl[M2 * q + t] = u[q];
     __syncthreads();
     if (lok) {
-      auto unpack = [&](int k) {
+      auto unpack = [&](int k, cpx<T> w) {
         const cpx<T> Z = Yl[k == M ? 0 : k];
         const cpx<T> Zc = conjg(Yl[k == 0 ? 0 : M - k]);
-        cpx<T> Xv = (Z + Zc) - mul_i(cmul(Z - Zc, pk[k]));
+        cpx<T> Xv = (Z + Zc) - mul_i(cmul(Z - Zc, w));
         T cc = scale;
         if (post) {
           const T kx = kfx * (T)freq_tilde(k, g.n0);
@@ -1145,8 +1233,8 @@ __global__ void __launch_bounds__(256, 3) k_xpass_tma(const XProg P, const GridD
         reinterpret_cast<cpx<T>*>(P.out[c])[lb + k] = Xv;
       };
 #pragma unroll
-      for (int q = 0; q < M1; ++q) unpack(t + M2 * q);
-      if (t == 0) unpack(M);
+      for (int q = 0; q < M1; ++q) unpack(t + M2 * q, pk_q<M1>(q, pk[t]));
+      if (t == 0) unpack(M, pk[M]);
     }
   }
 }
