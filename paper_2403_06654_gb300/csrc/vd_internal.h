@@ -108,6 +108,7 @@ template <typename T>
 void apply_velocity_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, double a,
                          double inv_sc, cpx<T>* tmp, const int* done, cudaStream_t st);
 int velocity_tmp_fields(int ndim);   // spectral-field-sized temporaries
+int velocity_spec_tmps(int ndim);    // of which spectral scratch (the rest hold physical fields)
 int pressure_tmp_fields(int ndim);
 
 // K_rho operator in spectral space: out = K~ (S in) = Lap S in + F(c F^-1(S in)); with S the

@@ -36,7 +36,10 @@ static const void* twtab(const vd_grid* G) {
 }
 
 int pressure_tmp_fields(int ndim) { return ndim == 3 ? 3 : (ndim == 2 ? 2 : 0); }
-int velocity_tmp_fields(int ndim) { return 1 + ndim * ndim + 2 * ndim; }
+// spectral temporaries of the velocity apply: the shared inverse passes of a component (3D:
+// four fields, 2D: three) and the forward transforms of the d brackets
+int velocity_spec_tmps(int ndim) { return ndim == 3 ? 4 : (ndim == 2 ? 3 : 1); }
+int velocity_tmp_fields(int ndim) { return velocity_spec_tmps(ndim) + ndim * ndim + 2 * ndim; }
 
 // ---------------------------------------------------------------------------------------
 // plain transforms
@@ -549,36 +552,146 @@ void apply_velocity_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const 
   const size_t nc = (size_t)g.ncplx;
   const size_t nr = (size_t)g.nreal;
   // physical scratch carved from spectral-sized temporaries (a spectral field holds >= nreal reals)
-  cpx<T>* ttmp = tmp;                                      // 1 field: transform scratch
-  T* u = reinterpret_cast<T*>(tmp + nc);                   // d fields
-  T* du = reinterpret_cast<T*>(tmp + nc * (1 + d));        // d*d fields
-  T* lap = reinterpret_cast<T*>(tmp + nc * (1 + d + d * d));  // d fields
+  cpx<T>* ttmp = tmp;                                      // spectral temporaries: ttmp[0..ns)
+  const int ns = velocity_spec_tmps(d);
+  T* u = reinterpret_cast<T*>(tmp + nc * ns);              // d fields
+  T* du = reinterpret_cast<T*>(tmp + nc * (ns + d));       // d*d fields
+  T* lap = reinterpret_cast<T*>(tmp + nc * (ns + d + d * d));  // d fields
   static_assert(sizeof(cpx<T>) == 2 * sizeof(T), "layout");
-  // u = F^-1(S in_i), du_ij = F^-1(i k_j S in_i), lap_i = F^-1(-|k|^2 S in_i)
+  const void* tw = twtab<T>(G);
+  const int S = symarr ? MUL_SYM : 0;
+  // u_i = F^-1(S in_i), du_ij = F^-1(i k_j S in_i), lap_i = F^-1(-|k|^2 S in_i): the d + 2
+  // inverse transforms of a component share their passes.  Each output gets the multipliers
+  // of its own inverse transform, in the same passes, so the fields equal those of d + 2
+  // separate inverse transforms bit for bit.
   for (int i = 0; i < d; ++i) {
     const cpx<T>* vi = in + i * nc;
-    Mult m;
-    m.sym = symarr ? 1 : 0;
-    m.symarr = symarr;
-    inv_transform<T>(G, vi, m, u + i * nr, ttmp, st);
-    for (int j = 0; j < d; ++j) {
-      Mult mj = m;
-      mj.deriv[j] = 1;
-      inv_transform<T>(G, vi, mj, du + (i * d + j) * nr, ttmp, st);
+    XProg X{};
+    X.mode = 2;
+    X.symarr = symarr;
+    X.done = done;
+    X.scale = 1.0 / (double)g.nreal;
+    if (d == 1) {
+      // u (S), du (i k S), lap (-k^2 S) straight from the spectrum
+      X.ncomp = 3;
+      X.in[0] = X.in[1] = X.in[2] = vi;
+      X.pre[0] = S;
+      X.pre[1] = S | MUL_IK;
+      X.pre[2] = S | MUL_NEGK2;
+      X.out[0] = u + i * nr;
+      X.out[1] = du + i * nr;
+      X.out[2] = lap + i * nr;
+      launch_xpass<T>(X, g, tw, st);
+      continue;
     }
-    Mult ml = m;
-    ml.negk2 = 1;
-    inv_transform<T>(G, vi, ml, lap + i * nr, ttmp, st);
+    cpx<T>* A = ttmp;            // S v, then its y inverse
+    cpx<T>* B = ttmp + nc;       // i k_y S v after the y inverse (3D: from A)
+    cpx<T>* Cf = ttmp + 2 * nc;  // -|k|^2 S v
+    cpx<T>* Z = ttmp + 3 * nc;   // 3D: i k_z S v
+    if (d == 3) {
+      // z inverse: A = F_z^-1(S v), Z = F_z^-1(i k_z S v), Cf = F_z^-1(-|k|^2 S v)
+      AxisProg P{};
+      P.nxf = 3;
+      P.xf[0] = mkxf(0, 0, S, 0, true, true);
+      P.xf[1] = mkxf(0, 1, S | MUL_IK, 0, true, true);
+      P.xf[2] = mkxf(0, 2, S | MUL_NEGK2, 0, true, true);
+      P.in[0] = vi;
+      P.out[0] = A;
+      P.out[1] = Z;
+      P.out[2] = Cf;
+      P.symarr = symarr;
+      P.done = done;
+      P.axis = 2;
+      launch_axis<T>(P, +1, g, tw, st);
+      // y inverse: B = F_y^-1(i k_y A) before A is transformed in place; Z, Cf in place
+      AxisProg Q{};
+      Q.nxf = 4;
+      Q.xf[0] = mkxf(0, 1, MUL_IK, 0, true, true);
+      Q.xf[1] = mkxf(0, 0, 0, 0, true, true);
+      Q.xf[2] = mkxf(1, 2, 0, 0, true, true);
+      Q.xf[3] = mkxf(2, 3, 0, 0, true, true);
+      Q.in[0] = A;
+      Q.in[1] = Z;
+      Q.in[2] = Cf;
+      Q.out[0] = A;
+      Q.out[1] = B;
+      Q.out[2] = Z;
+      Q.out[3] = Cf;
+      Q.done = done;
+      Q.axis = 1;
+      launch_axis<T>(Q, +1, g, tw, st);
+    } else {
+      // y inverse of the spectrum: A = F_y^-1(S v), B = F_y^-1(i k_y S v), Cf = F_y^-1(-|k|^2 S v)
+      AxisProg Q{};
+      Q.nxf = 3;
+      Q.xf[0] = mkxf(0, 0, S, 0, true, true);
+      Q.xf[1] = mkxf(0, 1, S | MUL_IK, 0, true, true);
+      Q.xf[2] = mkxf(0, 2, S | MUL_NEGK2, 0, true, true);
+      Q.in[0] = vi;
+      Q.out[0] = A;
+      Q.out[1] = B;
+      Q.out[2] = Cf;
+      Q.symarr = symarr;
+      Q.done = done;
+      Q.axis = 1;
+      launch_axis<T>(Q, +1, g, tw, st);
+    }
+    // x inverse: u (A), du_x (i k_x A), du_y (B), du_z (Z), lap (Cf)
+    X.ncomp = 3;
+    X.in[0] = A;
+    X.pre[0] = 0;
+    X.out[0] = u + i * nr;
+    X.in[1] = A;
+    X.pre[1] = MUL_IK;
+    X.out[1] = du + (i * d + 0) * nr;
+    X.in[2] = B;
+    X.pre[2] = 0;
+    X.out[2] = du + (i * d + 1) * nr;
+    if (d == 3) {
+      X.ncomp = 4;
+      X.in[3] = Z;
+      X.pre[3] = 0;
+      X.out[3] = du + (i * d + 2) * nr;
+    }
+    launch_xpass<T>(X, g, tw, st);
+    XProg L = X;
+    L.ncomp = 1;
+    L.in[0] = Cf;
+    L.pre[0] = 0;
+    L.out[0] = lap + i * nr;
+    launch_xpass<T>(L, g, tw, st);
   }
   // pointwise bracket g_i = rho^-1 (lap_i + Sc^-1 sum_j (u_j D_j D_i rho + D_j rho D_j u_i)),
   // written over lap_i
   velocity_combine_launch(G, (int)sizeof(T), u, du, lap, inv_sc, done, st);
+  // F(g_i) for all components at once (each as its own forward transform), then
   // out_i = S in_i - a F(g_i)
-  for (int i = 0; i < d; ++i) {
-    fwd_transform<T>(G, lap + i * nr, ttmp, st);
-    // out_i = S in_i - a ttmp  (diagonal combine in spectral space)
-    spec_axpby_sym_launch(G, (int)sizeof(T), in + i * nc, symarr, 1.0, ttmp, -a, out + i * nc, done, st);
+  {
+    XProg X{};
+    X.ncomp = d;
+    X.mode = 1;
+    for (int i = 0; i < d; ++i) {
+      X.in[i] = lap + i * nr;
+      X.out[i] = ttmp + i * nc;
+    }
+    X.scale = 0.5;
+    X.done = done;
+    launch_xpass<T>(X, g, tw, st);
+    for (int axis = 1; axis < d; ++axis) {
+      AxisProg P{};
+      P.nxf = d;
+      for (int i = 0; i < d; ++i) {
+        P.xf[i] = mkxf(i, i, 0, 0, true, true);
+        P.in[i] = ttmp + i * nc;
+        P.out[i] = ttmp + i * nc;
+      }
+      P.done = done;
+      P.axis = axis;
+      launch_axis<T>(P, -1, g, tw, st);
+    }
   }
+  for (int i = 0; i < d; ++i)
+    spec_axpby_sym_launch(G, (int)sizeof(T), in + i * nc, symarr, 1.0, ttmp + i * nc, -a, out + i * nc, done, st);
 }
 
 // ---------------------------------------------------------------------------------------
