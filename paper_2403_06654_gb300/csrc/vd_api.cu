@@ -325,7 +325,7 @@ static DensLayout dens_layout(const vd_grid* G, vd_op op, void* base, size_t* by
   if (op == VD_OP_VELOCITY) {
     L.grho = c.take<double>(nr * 8 * g.ndim);
     L.hrho = c.take<double>(nr * 8 * 6);   // indexed by hidx(i, j) in [0, 6)
-    L.s0 = c.take<cpx<double>>(nc * 16 * 2);
+    L.s0 = c.take<cpx<double>>(nc * 16 * 4);   // spectrum of rho + 3 derivative scratch fields
   }
   if (op == VD_OP_KRHO) {
     L.kw = c.take<double>(nr * 8);
@@ -422,21 +422,18 @@ vd_status vd_density_set(vd_grid* G, vd_op op, const double* rho, void* ws, size
     cpx<double>* rh = L.s0;
     cpx<double>* tmp = L.s0 + nc;
     fwd_transform<double>(G, L.rho, rh, st);
+    double* grad[3] = {nullptr, nullptr, nullptr};
+    double* hess[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     for (int j = 0; j < d; ++j) {
-      Mult m;
-      m.deriv[j] = 1;
-      inv_transform<double>(G, rh, m, L.grho + j * nr, tmp, st);
-      G->grho[j] = L.grho + j * nr;
+      grad[j] = L.grho + j * nr;
+      G->grho[j] = grad[j];
     }
     for (int i = 0; i < d; ++i)
       for (int j = i; j < d; ++j) {
-        Mult m;
-        m.deriv[i] += 1;
-        m.deriv[j] += 1;
-        double* dst = L.hrho + hidx(i, j) * nr;
-        inv_transform<double>(G, rh, m, dst, tmp, st);
-        G->hrho[hidx(i, j)] = dst;
+        hess[hidx(i, j)] = L.hrho + hidx(i, j) * nr;
+        G->hrho[hidx(i, j)] = hess[hidx(i, j)];
       }
+    derivative_fields(G, rh, grad, hess, tmp, st);
     VD_CUDA(cudaGetLastError());
     G->has_velocity_data = 1;
   }
@@ -630,17 +627,15 @@ static vd_status check_op(const vd_grid* G, vd_op op, const vd_op_params* p) {
   return VD_OK;
 }
 
-// forward transform of every component (physical double -> spectral double)
+// forward transform of every component (physical double -> spectral double), one launch per
+// pass for all components
 static void fwd_all(const vd_grid* G, int ncomp, const double* in, cpx<double>* out, cudaStream_t st) {
-  for (int c = 0; c < ncomp; ++c)
-    fwd_transform<double>(G, in + (size_t)c * G->g.nreal, out + (size_t)c * G->g.ncplx, st);
+  fwd_transform_n<double>(G, ncomp, in, out, st);
 }
+// inverse likewise; tmp: ncomp spectral fields (the operator's temporaries hold that many)
 static void inv_all(const vd_grid* G, int ncomp, const cpx<double>* in, double* out, cpx<double>* tmp,
                     cudaStream_t st) {
-  for (int c = 0; c < ncomp; ++c) {
-    Mult m;
-    inv_transform<double>(G, in + (size_t)c * G->g.ncplx, m, out + (size_t)c * G->g.nreal, tmp, st);
-  }
+  inv_transform_n<double>(G, ncomp, in, out, tmp, st);
 }
 
 // One FP64 solve as a capturable graph fragment on st (loop bodies captured on body_st):

@@ -81,6 +81,13 @@ void fwd_transform(const vd_grid* G, const T* in, cpx<T>* out, cudaStream_t st);
 // spectral -> physical with multiplier. tmp: one spectral field (2D/3D); `in` untouched.
 template <typename T>
 void inv_transform(const vd_grid* G, const cpx<T>* in, const Mult& m, T* out, cpx<T>* tmp, cudaStream_t st);
+// the plain transforms of ncomp (<= 3) fields stored back to back, one launch per pass (each
+// field's arithmetic as in fwd_transform / inv_transform; the inverse needs ncomp spectral tmp
+// fields in 2D/3D)
+template <typename T>
+void fwd_transform_n(const vd_grid* G, int ncomp, const T* in, cpx<T>* out, cudaStream_t st);
+template <typename T>
+void inv_transform_n(const vd_grid* G, int ncomp, const cpx<T>* in, T* out, cpx<T>* tmp, cudaStream_t st);
 
 // Pressure operator in spectral space: out = L~ (S in) with S = symarr (if non-null) else 1.
 // tmp: 3 spectral fields (3D), 2 (2D), 0 (1D).  done: optional early-exit flag.
@@ -109,6 +116,9 @@ void apply_velocity_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const 
                          double inv_sc, cpx<T>* tmp, const int* done, cudaStream_t st);
 int velocity_tmp_fields(int ndim);   // spectral-field-sized temporaries
 int velocity_spec_tmps(int ndim);    // of which spectral scratch (the rest hold physical fields)
+// grad[j] = F^-1(i k_j rh), hess[hidx(a, b)] = F^-1((i k_a)(i k_b) rh) in double; tmp: 3 spectral fields
+void derivative_fields(const vd_grid* G, const cpx<double>* rh, double* const grad[3], double* const hess[6],
+                       cpx<double>* tmp, cudaStream_t st);
 int pressure_tmp_fields(int ndim);
 
 // K_rho operator in spectral space: out = K~ (S in) = Lap S in + F(c F^-1(S in)); with S the

@@ -115,6 +115,156 @@ void inv_transform(const vd_grid* G, const cpx<T>* in, const Mult& mu, T* out, c
   launch_xpass<T>(X, g, twtab<T>(G), st);
 }
 
+template <typename T>
+void fwd_transform_n(const vd_grid* G, int ncomp, const T* in, cpx<T>* out, cudaStream_t st) {
+  const GridDesc& g = G->g;
+  const size_t nc = (size_t)g.ncplx, nr = (size_t)g.nreal;
+  XProg X{};
+  X.ncomp = ncomp;
+  X.mode = 1;
+  for (int c = 0; c < ncomp; ++c) {
+    X.in[c] = in + c * nr;
+    X.out[c] = out + c * nc;
+  }
+  X.scale = 0.5;
+  launch_xpass<T>(X, g, twtab<T>(G), st);
+  for (int axis = 1; axis < g.ndim; ++axis) {
+    AxisProg P{};
+    P.nxf = ncomp;
+    for (int c = 0; c < ncomp; ++c) {
+      P.xf[c] = mkxf(c, c, 0, 0, true, true);
+      P.in[c] = out + c * nc;
+      P.out[c] = out + c * nc;
+    }
+    P.axis = axis;
+    launch_axis<T>(P, -1, g, twtab<T>(G), st);
+  }
+}
+
+template <typename T>
+void inv_transform_n(const vd_grid* G, int ncomp, const cpx<T>* in, T* out, cpx<T>* tmp, cudaStream_t st) {
+  const GridDesc& g = G->g;
+  const size_t nc = (size_t)g.ncplx, nr = (size_t)g.nreal;
+  const cpx<T>* cur = in;
+  for (int axis = g.ndim - 1; axis >= 1; --axis) {
+    AxisProg P{};
+    P.nxf = ncomp;
+    for (int c = 0; c < ncomp; ++c) {
+      P.xf[c] = mkxf(c, c, 0, 0, true, true);
+      P.in[c] = cur + c * nc;
+      P.out[c] = tmp + c * nc;
+    }
+    P.axis = axis;
+    launch_axis<T>(P, +1, g, twtab<T>(G), st);
+    cur = tmp;
+  }
+  XProg X{};
+  X.ncomp = ncomp;
+  X.mode = 2;
+  for (int c = 0; c < ncomp; ++c) {
+    X.in[c] = cur + c * nc;
+    X.out[c] = out + c * nr;
+  }
+  X.scale = 1.0 / (double)g.nreal;
+  launch_xpass<T>(X, g, twtab<T>(G), st);
+}
+
+// First and second derivatives of a field from its spectrum rh (double): grad[j] = F^-1(i k_j rh),
+// hess[hidx(a, b)] = F^-1((i k_a)(i k_b) rh).  The inverse transforms sharing a z multiplier
+// share their z and y passes (each output gets its own transform's multipliers in the same
+// passes: the fields are those of separate inverse transforms bit for bit).  tmp: three
+// spectral fields.
+void derivative_fields(const vd_grid* G, const cpx<double>* rh, double* const grad[3], double* const hess[6],
+                       cpx<double>* tmp, cudaStream_t st) {
+  const GridDesc& g = G->g;
+  const int d = g.ndim;
+  const size_t nc = (size_t)g.ncplx;
+  const void* tw = G->tw_d;
+  auto fl = [](int k) { return k == 1 ? MUL_IK : (k == 2 ? MUL_IK2 : 0); };
+  // x pass over a list of (spectral input, x derivative order, output)
+  auto xpass = [&](int n, const cpx<double>* const* in, const int* kx, double* const* out) {
+    XProg X{};
+    X.ncomp = n;
+    X.mode = 2;
+    for (int c = 0; c < n; ++c) {
+      X.in[c] = in[c];
+      X.pre[c] = fl(kx[c]);
+      X.out[c] = out[c];
+    }
+    X.scale = 1.0 / (double)g.nreal;
+    launch_xpass<double>(X, g, tw, st);
+  };
+  if (d == 1) {
+    const cpx<double>* in[2] = {rh, rh};
+    const int kx[2] = {1, 2};
+    double* out[2] = {grad[0], hess[hidx(0, 0)]};
+    xpass(2, in, kx, out);
+    return;
+  }
+  // outputs by (z order, y order): x orders and destinations
+  struct Out {
+    int kz, ky, kx;
+    double* dst;
+  };
+  Out outs[9];
+  int no = 0;
+  for (int j = 0; j < d; ++j) {
+    int k[3] = {0, 0, 0};
+    k[j] = 1;
+    outs[no++] = {k[2], k[1], k[0], grad[j]};
+  }
+  for (int a = 0; a < d; ++a)
+    for (int b = a; b < d; ++b) {
+      int k[3] = {0, 0, 0};
+      k[a] += 1;
+      k[b] += 1;
+      outs[no++] = {k[2], k[1], k[0], hess[hidx(a, b)]};
+    }
+  for (int kz = 0; kz <= (d == 3 ? 2 : 0); ++kz) {
+    const cpx<double>* zin = rh;
+    if (d == 3) {
+      // z inverse with this z multiplier into tmp[0]
+      AxisProg P{};
+      P.nxf = 1;
+      P.xf[0] = mkxf(0, 0, fl(kz), 0, true, true);
+      P.in[0] = rh;
+      P.out[0] = tmp;
+      P.axis = 2;
+      launch_axis<double>(P, +1, g, tw, st);
+      zin = tmp;
+    }
+    // y inverse: one output per y order used by this group; the y order 0 in place last
+    int ys[3] = {-1, -1, -1};   // y order -> tmp slot
+    for (int o = 0; o < no; ++o)
+      if (outs[o].kz == kz) ys[outs[o].ky] = 0;
+    AxisProg Q{};
+    int slot = (d == 3) ? 1 : 0;
+    for (int ky = 2; ky >= 0; --ky) {
+      if (ys[ky] < 0) continue;
+      const bool inplace = (d == 3 && ky == 0);
+      ys[ky] = inplace ? 0 : slot++;
+      Q.xf[Q.nxf] = mkxf(0, Q.nxf, fl(ky), 0, true, true);
+      Q.out[Q.nxf] = tmp + (size_t)ys[ky] * nc;
+      ++Q.nxf;
+    }
+    Q.in[0] = zin;
+    Q.axis = 1;
+    launch_axis<double>(Q, +1, g, tw, st);
+    const cpx<double>* in[kMaxXComp];
+    int kx[kMaxXComp];
+    double* out[kMaxXComp];
+    int n = 0;
+    for (int o = 0; o < no; ++o) {
+      if (outs[o].kz != kz) continue;
+      in[n] = tmp + (size_t)ys[outs[o].ky] * nc;
+      kx[n] = outs[o].kx;
+      out[n] = outs[o].dst;
+      ++n;
+    }
+    xpass(n, in, kx, out);
+  }
+}
+
 // Plain transforms with float-pair arithmetic; double fields in and out, float-pair
 // intermediates in tmp (one spectral field of 16-byte elements).
 void fwd_transform_dd(const vd_grid* G, const double* in, cpx<double>* out, void* tmp, cudaStream_t st) {
@@ -539,8 +689,8 @@ void apply_krho_spec_dd(const vd_grid* G, const cpx<double>* in, cpx<double>* ou
 // velocity operator
 // ---------------------------------------------------------------------------------------
 
-void spec_axpby_sym_launch(const vd_grid* G, int sz, const void* x, const void* symarr, double alpha, const void* y,
-                           double beta, void* out, const int* done, cudaStream_t st);
+void spec_axpby_sym_launch(const vd_grid* G, int sz, int ncomp, const void* x, const void* symarr, double alpha,
+                           const void* y, double beta, void* out, const int* done, cudaStream_t st);
 void velocity_combine_launch(const vd_grid* G, int sz, const void* u, const void* du, void* lap, double inv_sc,
                              const int* done, cudaStream_t st);
 
@@ -636,87 +786,55 @@ void apply_velocity_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const 
       Q.axis = 1;
       launch_axis<T>(Q, +1, g, tw, st);
     }
-    // x inverse: u (A), du_x (i k_x A), du_y (B), du_z (Z), lap (Cf)
-    X.ncomp = 3;
-    X.in[0] = A;
-    X.pre[0] = 0;
-    X.out[0] = u + i * nr;
-    X.in[1] = A;
-    X.pre[1] = MUL_IK;
-    X.out[1] = du + (i * d + 0) * nr;
-    X.in[2] = B;
-    X.pre[2] = 0;
-    X.out[2] = du + (i * d + 1) * nr;
-    if (d == 3) {
-      X.ncomp = 4;
-      X.in[3] = Z;
-      X.pre[3] = 0;
-      X.out[3] = du + (i * d + 2) * nr;
+    // x inverse: u (A), du_x (i k_x A), du_y (B), [du_z (Z),] lap (Cf)
+    const cpx<T>* xin[5] = {A, A, B, Z, Cf};
+    T* xout[5] = {u + i * nr, du + (i * d + 0) * nr, du + (i * d + 1) * nr, du + (i * d + 2) * nr, lap + i * nr};
+    const int xpre[5] = {0, MUL_IK, 0, 0, 0};
+    X.ncomp = 0;
+    for (int c = 0; c < 5; ++c) {
+      if (d == 2 && c == 3) continue;   // no z derivative
+      X.in[X.ncomp] = xin[c];
+      X.out[X.ncomp] = xout[c];
+      X.pre[X.ncomp] = xpre[c];
+      ++X.ncomp;
     }
     launch_xpass<T>(X, g, tw, st);
-    XProg L = X;
-    L.ncomp = 1;
-    L.in[0] = Cf;
-    L.pre[0] = 0;
-    L.out[0] = lap + i * nr;
-    launch_xpass<T>(L, g, tw, st);
   }
   // pointwise bracket g_i = rho^-1 (lap_i + Sc^-1 sum_j (u_j D_j D_i rho + D_j rho D_j u_i)),
   // written over lap_i
   velocity_combine_launch(G, (int)sizeof(T), u, du, lap, inv_sc, done, st);
   // F(g_i) for all components at once (each as its own forward transform), then
   // out_i = S in_i - a F(g_i)
-  {
-    XProg X{};
-    X.ncomp = d;
-    X.mode = 1;
-    for (int i = 0; i < d; ++i) {
-      X.in[i] = lap + i * nr;
-      X.out[i] = ttmp + i * nc;
-    }
-    X.scale = 0.5;
-    X.done = done;
-    launch_xpass<T>(X, g, tw, st);
-    for (int axis = 1; axis < d; ++axis) {
-      AxisProg P{};
-      P.nxf = d;
-      for (int i = 0; i < d; ++i) {
-        P.xf[i] = mkxf(i, i, 0, 0, true, true);
-        P.in[i] = ttmp + i * nc;
-        P.out[i] = ttmp + i * nc;
-      }
-      P.done = done;
-      P.axis = axis;
-      launch_axis<T>(P, -1, g, tw, st);
-    }
-  }
-  for (int i = 0; i < d; ++i)
-    spec_axpby_sym_launch(G, (int)sizeof(T), in + i * nc, symarr, 1.0, ttmp + i * nc, -a, out + i * nc, done, st);
+  fwd_transform_n<T>(G, d, lap, ttmp, st);
+  spec_axpby_sym_launch(G, (int)sizeof(T), d, in, symarr, 1.0, ttmp, -a, out, done, st);
 }
 
 // ---------------------------------------------------------------------------------------
 // small pointwise kernels used above
 // ---------------------------------------------------------------------------------------
 
+// over ncomp fields of nc elements stored back to back, the symbol indexed per field
 template <typename T>
-__global__ void k_spec_axpby_sym(long long n, const cpx<T>* __restrict__ x, const T* __restrict__ sym, T alpha,
-                                 const cpx<T>* __restrict__ y, T beta, cpx<T>* __restrict__ out, const int* done) {
+__global__ void k_spec_axpby_sym(long long n, long long nc, const cpx<T>* __restrict__ x, const T* __restrict__ sym,
+                                 T alpha, const cpx<T>* __restrict__ y, T beta, cpx<T>* __restrict__ out,
+                                 const int* done) {
   if (done && *done) return;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const T s = sym ? sym[e] * alpha : alpha;
+    const T s = sym ? sym[e % nc] * alpha : alpha;
     out[e] = scal(x[e], s) + scal(y[e], beta);
   }
 }
 
-void spec_axpby_sym_launch(const vd_grid* G, int sz, const void* x, const void* symarr, double alpha, const void* y,
-                           double beta, void* out, const int* done, cudaStream_t st) {
-  const long long n = G->g.ncplx;
+void spec_axpby_sym_launch(const vd_grid* G, int sz, int ncomp, const void* x, const void* symarr, double alpha,
+                           const void* y, double beta, void* out, const int* done, cudaStream_t st) {
+  const long long nc = G->g.ncplx;
+  const long long n = nc * ncomp;
   const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
   if (sz == 8)
-    { k_spec_axpby_sym<double><<<blocks, 256, 0, st>>>(n, (const cpx<double>*)x, (const double*)symarr, alpha,
+    { k_spec_axpby_sym<double><<<blocks, 256, 0, st>>>(n, nc, (const cpx<double>*)x, (const double*)symarr, alpha,
                                                      (const cpx<double>*)y, beta, (cpx<double>*)out, done); count_launch(); }
   else
-    { k_spec_axpby_sym<float><<<blocks, 256, 0, st>>>(n, (const cpx<float>*)x, (const float*)symarr, (float)alpha,
+    { k_spec_axpby_sym<float><<<blocks, 256, 0, st>>>(n, nc, (const cpx<float>*)x, (const float*)symarr, (float)alpha,
                                                     (const cpx<float>*)y, (float)beta, (cpx<float>*)out, done); count_launch(); }
 }
 
@@ -805,6 +923,10 @@ void fill_symbol(const vd_grid* G, int kind, double a, T* out, cudaStream_t st) 
 }
 
 template void fwd_transform<double>(const vd_grid*, const double*, cpx<double>*, cudaStream_t);
+template void fwd_transform_n<double>(const vd_grid*, int, const double*, cpx<double>*, cudaStream_t);
+template void fwd_transform_n<float>(const vd_grid*, int, const float*, cpx<float>*, cudaStream_t);
+template void inv_transform_n<double>(const vd_grid*, int, const cpx<double>*, double*, cpx<double>*, cudaStream_t);
+template void inv_transform_n<float>(const vd_grid*, int, const cpx<float>*, float*, cpx<float>*, cudaStream_t);
 template void fwd_transform<float>(const vd_grid*, const float*, cpx<float>*, cudaStream_t);
 template void inv_transform<double>(const vd_grid*, const cpx<double>*, const Mult&, double*, cpx<double>*,
                                     cudaStream_t);

@@ -56,13 +56,15 @@ struct AxisProg {
 // multiply by wfield (real, n0 per line; nullptr = 1) -> forward real FFT -> post -> out[c].
 // mode 0: fused as described; mode 1: real in (in[c] is T*), forward only; mode 2: inverse
 // only, real out (out[c] is T*).  scale multiplies the result.
+constexpr int kMaxXComp = 6;
+
 struct XProg {
-  int ncomp;
+  int ncomp;   // <= kMaxXComp
   int mode;
-  const void* in[4];
-  void* out[4];
-  int pre[4];
-  int post[4];
+  const void* in[kMaxXComp];
+  void* out[kMaxXComp];
+  int pre[kMaxXComp];
+  int post[kMaxXComp];
   const void* wfield;
   // float programs only: wfield holds a float pair (hi, lo) per real point, and the multiply
   // z * (hi + lo) is carried in float-pair arithmetic, rounded to float once
