@@ -80,7 +80,7 @@ DTYPES = {"mixed_dd": "f32 inner / f64 refinement, residual transforms in float-
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel class,
 # averaged over its launches in one ncu capture of this workload, with the capture it came
 # from; reported only for that class, and only while the kernel is unchanged since.
-MEASURED_TRAFFIC = {"axis_f32": (229.4e6, "profiles/sections_jet256_mixed_dd.md (kernels of commit dc550e0)")}
+MEASURED_TRAFFIC = {"axis_f32": (229.4e6, "profiles/sections_jet256_mixed_dd.md (capture of commit 1459b41; float axis kernels unchanged since dc550e0)")}
 
 
 class ClockSampler:
