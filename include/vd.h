@@ -78,11 +78,13 @@ typedef enum {
   VD_PREC_MIXED = 1, /* inner Krylov solve with float transforms and preconditioner, double
                         dot products, inside a double iterative-refinement loop whose true
                         residual uses the double operator */
-  VD_PREC_MIXED_DD = 2 /* as VD_PREC_MIXED, but the refinement residual b - A x of the pressure
-                        operator is formed with float-pair transforms (two floats per value,
-                        ~2^-48 relative rounding, on the FP32 pipes; storage stays double).
-                        On GB300 double arithmetic runs at 1/69 of the float rate, which makes
-                        this much faster; the velocity operator keeps the double residual. */
+  VD_PREC_MIXED_DD = 2 /* as VD_PREC_MIXED, but the refinement residual b - A x is formed with
+                        float-pair transforms (two floats per value, ~2^-48 relative rounding,
+                        on the FP32 pipes; storage stays double; the velocity operator's
+                        pointwise bracket stays double).  On GB300 double arithmetic runs at
+                        1/69 of the float rate, which makes this much faster.  The residual
+                        that certifies tol carries the float-pair error, normwise
+                        ~2^-47 |A| |x| / |b|. */
 } vd_precision;
 
 /* Parameters of the velocity operator: a = dt/(2 Re) (Eq. VDINSE.Vrho), inv_sc = 1/Sc. */

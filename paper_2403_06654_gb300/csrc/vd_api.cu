@@ -653,6 +653,7 @@ static void resid_cb(const void* c, const void* x, void* y, cudaStream_t st) {
   const cpx<double>* xi = (const cpx<double>*)x;
   cpx<double>* yo = (cpx<double>*)y;
   if (r.dd && r.op == VD_OP_KRHO) apply_krho_spec_dd(r.G, xi, yo, r.tmp, nullptr, st);
+  else if (r.dd && r.op == VD_OP_VELOCITY) apply_velocity_spec_dd(r.G, xi, yo, r.sys64->a, r.sys64->inv_sc, r.tmp, nullptr, st);
   else if (r.dd) apply_pressure_spec_dd(r.G, xi, yo, r.tmp, nullptr, st);
   else r.sys64->apply(*r.sys64, xi, yo, false, nullptr, st);
 }
@@ -687,7 +688,9 @@ vd_status enqueue_solve_graph(const vd_grid* G, vd_op op, vd_solver solver, cons
     fill_symbol<float>(G, op_symbol(op), opp ? opp->a : 0.0, L.sym_f, st);
     SpecSystem sys64 = make_system<double>(G, op, opp, L.sym, L.tmp);
     SpecSystem sys32 = make_system<float>(G, op, opp, L.sym_f, L.tmp_f);
-    ResidCtx rc{G, op, dd, &sys64, L.tmp};
+    // the refinement residual in float pairs for every operator (the entry and exit transforms of
+    // the velocity components stay double)
+    ResidCtx rc{G, op, precision == VD_PREC_MIXED_DD, &sys64, L.tmp};
     SolveOpts si;
     si.solver = solver;
     si.tol = 0.0;
@@ -966,8 +969,8 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
     fill_symbol<float>(G, symkind, opp ? opp->a : 0.0, L.sym_f, st);
     SpecSystem sys32 = make_system<float>(G, op, opp, L.sym_f, L.tmp_f, prm->coef_pair);
     coef_pair_used = sys32.ctx[3] != nullptr;
-    // residual operator of the refinement: double, or float-pair transforms (pressure)
-    const bool use_dd = prm->precision == VD_PREC_MIXED_DD && op != VD_OP_VELOCITY;
+    // residual operator of the refinement: double, or float-pair transforms
+    const bool use_dd = prm->precision == VD_PREC_MIXED_DD;
     // With want_phys the float-pair pressure residual also writes the physical-space iterate
     // into x (its fused x pass carries the inverse transform of the iterate); when the loop
     // ends right after such a residual the final inverse transform is skipped.  It is asked
@@ -976,6 +979,9 @@ vd_status vd_solve(const vd_grid* G, vd_op op, vd_solver solver, const vd_op_par
     auto resid_apply = [&](const cpx<double>* xin, cpx<double>* yout, bool want_phys) {
       if (use_dd && op == VD_OP_KRHO) {
         apply_krho_spec_dd(G, xin, yout, L.tmp, nullptr, st);
+        x_phys_current = false;
+      } else if (use_dd && op == VD_OP_VELOCITY) {
+        apply_velocity_spec_dd(G, xin, yout, sys64.a, sys64.inv_sc, L.tmp, nullptr, st);
         x_phys_current = false;
       } else if (use_dd) {
         apply_pressure_spec_dd(G, xin, yout, L.tmp, nullptr, st, want_phys ? x : nullptr);

@@ -114,6 +114,9 @@ void inv_transform_dd(const vd_grid* G, const cpx<double>* in, double* out, void
 template <typename T>
 void apply_velocity_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const T* symarr, double a,
                          double inv_sc, cpx<T>* tmp, const int* done, cudaStream_t st);
+// the same without preconditioner in float-pair arithmetic, double fields in and out
+void apply_velocity_spec_dd(const vd_grid* G, const cpx<double>* in, cpx<double>* out, double a, double inv_sc,
+                            void* tmp, const int* done, cudaStream_t st);
 int velocity_tmp_fields(int ndim);   // spectral-field-sized temporaries
 int velocity_spec_tmps(int ndim);    // of which spectral scratch (the rest hold physical fields)
 // grad[j] = F^-1(i k_j rh), hess[hidx(a, b)] = F^-1((i k_a)(i k_b) rh) in double; tmp: 3 spectral fields

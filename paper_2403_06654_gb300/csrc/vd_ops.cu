@@ -809,6 +809,141 @@ void apply_velocity_spec(const vd_grid* G, const cpx<T>* in, cpx<T>* out, const 
   spec_axpby_sym_launch(G, (int)sizeof(T), d, in, symarr, 1.0, ttmp, -a, out, done, st);
 }
 
+// The velocity operator without preconditioner in float-pair arithmetic (the refinement
+// residual of mixed_dd): double spectral fields in and out, the transforms of
+// apply_velocity_spec in float pairs (split from double on the first pass's loads, summed to
+// double on the last pass's stores), the physical fields u, du, lap in double so that the
+// pointwise bracket is the double one.  tmp: velocity_tmp_fields(d) fields of 16-byte complex
+// elements (the float-pair spectral scratch takes the same room as double).
+void apply_velocity_spec_dd(const vd_grid* G, const cpx<double>* in, cpx<double>* out, double a, double inv_sc,
+                            void* tmp_, const int* done, cudaStream_t st) {
+  const GridDesc& g = G->g;
+  const int d = g.ndim;
+  const size_t nc = (size_t)g.ncplx;
+  const size_t nr = (size_t)g.nreal;
+  cpx<dd>* ttmp = reinterpret_cast<cpx<dd>*>(tmp_);
+  cpx<double>* dtmp = reinterpret_cast<cpx<double>*>(tmp_);
+  const int ns = velocity_spec_tmps(d);
+  double* u = reinterpret_cast<double*>(dtmp + nc * ns);
+  double* du = reinterpret_cast<double*>(dtmp + nc * (ns + d));
+  double* lap = reinterpret_cast<double*>(dtmp + nc * (ns + d + d * d));
+  const void* tw = G->tw_dd;
+  for (int i = 0; i < d; ++i) {
+    const cpx<double>* vi = in + i * nc;
+    XProg X{};
+    X.mode = 2;
+    X.done = done;
+    X.scale = 1.0 / (double)g.nreal;
+    if (d == 1) {
+      X.ncomp = 3;
+      X.in[0] = X.in[1] = X.in[2] = vi;
+      X.pre[0] = 0;
+      X.pre[1] = MUL_IK;
+      X.pre[2] = MUL_NEGK2;
+      X.out[0] = u + i * nr;
+      X.out[1] = du + i * nr;
+      X.out[2] = lap + i * nr;
+      X.conv_in = 7;
+      X.conv_out = 7;
+      launch_xpass<dd>(X, g, tw, st);
+      continue;
+    }
+    cpx<dd>* A = ttmp;
+    cpx<dd>* B = ttmp + nc;
+    cpx<dd>* Cf = ttmp + 2 * nc;
+    cpx<dd>* Z = ttmp + 3 * nc;
+    if (d == 3) {
+      AxisProg P{};
+      P.nxf = 3;
+      P.xf[0] = mkxf(0, 0, 0, 0, true, true);
+      P.xf[1] = mkxf(0, 1, MUL_IK, 0, true, true);
+      P.xf[2] = mkxf(0, 2, MUL_NEGK2, 0, true, true);
+      P.in[0] = vi;
+      P.conv_in = 1;
+      P.out[0] = A;
+      P.out[1] = Z;
+      P.out[2] = Cf;
+      P.done = done;
+      P.axis = 2;
+      launch_axis<dd>(P, +1, g, tw, st);
+      AxisProg Q{};
+      Q.nxf = 4;
+      Q.xf[0] = mkxf(0, 1, MUL_IK, 0, true, true);
+      Q.xf[1] = mkxf(0, 0, 0, 0, true, true);
+      Q.xf[2] = mkxf(1, 2, 0, 0, true, true);
+      Q.xf[3] = mkxf(2, 3, 0, 0, true, true);
+      Q.in[0] = A;
+      Q.in[1] = Z;
+      Q.in[2] = Cf;
+      Q.out[0] = A;
+      Q.out[1] = B;
+      Q.out[2] = Z;
+      Q.out[3] = Cf;
+      Q.done = done;
+      Q.axis = 1;
+      launch_axis<dd>(Q, +1, g, tw, st);
+    } else {
+      AxisProg Q{};
+      Q.nxf = 3;
+      Q.xf[0] = mkxf(0, 0, 0, 0, true, true);
+      Q.xf[1] = mkxf(0, 1, MUL_IK, 0, true, true);
+      Q.xf[2] = mkxf(0, 2, MUL_NEGK2, 0, true, true);
+      Q.in[0] = vi;
+      Q.conv_in = 1;
+      Q.out[0] = A;
+      Q.out[1] = B;
+      Q.out[2] = Cf;
+      Q.done = done;
+      Q.axis = 1;
+      launch_axis<dd>(Q, +1, g, tw, st);
+    }
+    const cpx<dd>* xin[5] = {A, A, B, Z, Cf};
+    double* xout[5] = {u + i * nr, du + (i * d + 0) * nr, du + (i * d + 1) * nr, du + (i * d + 2) * nr, lap + i * nr};
+    const int xpre[5] = {0, MUL_IK, 0, 0, 0};
+    X.ncomp = 0;
+    for (int c = 0; c < 5; ++c) {
+      if (d == 2 && c == 3) continue;
+      X.in[X.ncomp] = xin[c];
+      X.out[X.ncomp] = xout[c];
+      X.pre[X.ncomp] = xpre[c];
+      ++X.ncomp;
+    }
+    X.conv_out = (1 << X.ncomp) - 1;
+    launch_xpass<dd>(X, g, tw, st);
+  }
+  velocity_combine_launch(G, 8, u, du, lap, inv_sc, done, st);
+  // F(g_i): x pass from the double brackets, y (and z) passes, the last one summing to double
+  cpx<double>* F = dtmp;   // over the float-pair scratch, element by element on the last pass
+  {
+    XProg X{};
+    X.ncomp = d;
+    X.mode = 1;
+    for (int i = 0; i < d; ++i) {
+      X.in[i] = lap + i * nr;
+      X.out[i] = ttmp + i * nc;
+    }
+    X.conv_in = (1 << d) - 1;
+    if (d == 1) X.conv_out = 1;
+    X.scale = 0.5;
+    X.done = done;
+    launch_xpass<dd>(X, g, tw, st);
+    for (int axis = 1; axis < d; ++axis) {
+      AxisProg P{};
+      P.nxf = d;
+      for (int i = 0; i < d; ++i) {
+        P.xf[i] = mkxf(i, i, 0, 0, true, true);
+        P.in[i] = ttmp + i * nc;
+        P.out[i] = ttmp + i * nc;
+      }
+      if (axis == d - 1) P.conv_out = (1 << d) - 1;
+      P.done = done;
+      P.axis = axis;
+      launch_axis<dd>(P, -1, g, tw, st);
+    }
+  }
+  spec_axpby_sym_launch(G, 8, d, in, nullptr, 1.0, F, -a, out, done, st);
+}
+
 // ---------------------------------------------------------------------------------------
 // small pointwise kernels used above
 // ---------------------------------------------------------------------------------------
