@@ -420,8 +420,11 @@ vd_status vd_batch_destroy(vd_batch* batch);
 size_t vd_autotune_bytes(const vd_grid* grid);
 vd_status vd_autotune(const vd_grid* grid, int precisions, void* scratch, size_t bytes, vd_stream stream);
 /* entries of the table, 6 ints each (kind 0 y/z pass or 1 x pass, type 0 double / 1 float /
- * 2 float-pair, length, axis, direction or x-pass form, choice: 0 register kernel, > 0 lines per
- * block); writes at most max entries to out (may be null) and returns the total count */
+ * 2 float-pair, length, axis, direction or x-pass form, choice: 0 register kernel, 1..64 lines
+ * per block, 128 the register kernel with TMA-staged tiles (float y/z passes of length 128 and
+ * 256), 256 the Stockham engine on unpacked float pairs (float-pair passes; the default packed
+ * engine gives the same bits); writes at most max entries to out (may be null) and returns the
+ * total count */
 int vd_autotune_table(int* out, int max);
 /* set one entry by hand (choice < 0 erases it); INVALID_ARG on a bad key or choice */
 vd_status vd_autotune_set(int kind, int type, int n, int axis, int dir, int choice);

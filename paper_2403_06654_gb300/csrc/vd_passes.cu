@@ -5,6 +5,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include "vd_dd.cuh"
+#include "vd_pdd.cuh"
 #include "vd_prof.h"
 
 #include <cmath>
@@ -101,7 +102,10 @@ static inline int lines_per_cta(int m, int ept) {
 // strided axis pass
 // ---------------------------------------------------------------------------------------
 
-template <typename T, int S, bool CV>
+// PK (float pairs, radices 2 / 4 / 8 only): the shared-memory transform runs on packed
+// complex float pairs (vd_pdd.cuh), bit-identical to the unpacked engine; its twiddle table
+// holds two entries per twiddle.
+template <typename T, int S, bool CV, bool PK = false>
 __global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 : (std::is_same<T, dd>::value ? 4 : 3))) k_axis(const AxisProg P, const GridDesc g,
                                                    const cpx<T>* __restrict__ twg, int lw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -110,11 +114,16 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 
   const FftPlan& pl = (axis == 2) ? g.pz : g.py;
   const int n = pl.n;
   const int W = 1 << lw;
-  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* A = tw + n;
-  cpx<T>* B = A + W * n;
+  using E = typename std::conditional<PK, pdd, cpx<T>>::type;
+  E* tw = reinterpret_cast<E*>(smem_raw);
+  E* tw2 = tw + n;   // PK: the second table
+  E* A = tw + (PK ? 2 : 1) * n;
+  E* B = A + W * n;
   const int tid = threadIdx.x;
-  for (int j = tid; j < n; j += kThreads) tw[j] = twg[pl.tw_off + j];
+  for (int j = tid; j < n; j += kThreads) {
+    if constexpr (PK) p_tw_entry<S>(twg[pl.tw_off + j], &tw[j], &tw2[j]);
+    else tw[j] = twg[pl.tw_off + j];
+  }
 
   // field offsets fit in 32 bits (ncplx < 2^31 is checked when the grid is created)
   int line_stride, inner_n, outer_stride;
@@ -201,15 +210,20 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 
         v = scal(v, mult(xf.pre, i, go, T(1)));
         if (xf.pre & MUL_IK) v = mul_i(v);
       }
-      A[i * W + w] = v;
+      if constexpr (PK) A[i * W + w] = pdd_of(v);
+      else A[i * W + w] = v;
     }
-    cpx<T>* res = fft_lines<T, S>(A, B, W, w, ib, istep, pl, tw);
+    E* res;
+    if constexpr (PK) res = p_fft_lines<S>(A, B, W, w, ib, istep, pl, tw, tw2);
+    else res = fft_lines<T, S>(A, B, W, w, ib, istep, pl, tw);
     if (colok) {
 #pragma unroll 4
       for (int q = 0; q < nq; ++q) {
         const int i = ib + q * istep;
         const int go = g0 + q * gstep;
-        cpx<T> v = res[i * W + w];
+        cpx<T> v;
+        if constexpr (PK) v = cpx_of(res[i * W + w]);
+        else v = res[i * W + w];
         if (xf.post) {
           v = scal(v, mult(xf.post, i, go, scale));
           if (xf.post & MUL_IK) v = mul_i(v);
@@ -725,8 +739,11 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
 // ---------------------------------------------------------------------------------------
 
 // float pairs: three blocks per SM (80 registers, no spills); the tuned 16 lines per block
-// take 70 KB of shared memory each, so a fourth block would not fit anyway
-template <typename T, bool CV>
+// take 70-73 KB of shared memory each, so a fourth block would not fit anyway.
+// PK (float pairs, radices 2 / 4 / 8 only): the transforms run on packed complex float pairs
+// (vd_pdd.cuh), bit-identical to the unpacked engine, with the twiddle tables of both
+// directions; the (un)packing of the real transform and the multipliers stay unpacked.
+template <typename T, bool CV, bool PK = false>
 __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)) k_xpass(const XProg P, const GridDesc g,
                                                     const cpx<T>* __restrict__ twg, int llpc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -735,12 +752,22 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)
   const int h0 = g.h0;
   const int ls = m + 1;
   const int LPC = 1 << llpc;
+  using E = typename std::conditional<PK, pdd, cpx<T>>::type;
   cpx<T>* twm = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* pk = twm + m;
-  cpx<T>* A = pk + (m + 2);   // keep 16-byte alignment (m even)
-  cpx<T>* B = A + LPC * ls;
+  E* twx = reinterpret_cast<E*>(pk + (m + 2));   // PK: the packed tables (wr, wi forward, wi inverse)
+  E* A = twx + (PK ? 3 * m : 0);   // keep 16-byte alignment (m even)
+  E* B = A + LPC * ls;
+  cpx<T>* Bc = reinterpret_cast<cpx<T>*>(B);   // the loaded half spectrum (elements of the same size)
   const int tid = threadIdx.x;
-  for (int j = tid; j < m; j += kThreads) twm[j] = twg[g.px.tw_off + j];
+  for (int j = tid; j < m; j += kThreads) {
+    twm[j] = twg[g.px.tw_off + j];
+    if constexpr (PK) {
+      p_tw_entry<-1>(twm[j], &twx[j], &twx[m + j]);
+      pdd wr;
+      p_tw_entry<+1>(twm[j], &wr, &twx[2 * m + j]);
+    }
+  }
   for (int j = tid; j <= m; j += kThreads) pk[j] = twg[g.pk_off + j];
 
   const long long nlines = (long long)g.n1 * g.n2;
@@ -756,22 +783,39 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)
   const T kfx = kfac_t<T>(g, 0);
   const T scale = scale_t<T>(P.scale, P.scale_hi, P.scale_lo);
   const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr) + (line0 + line) * h0;
+  // the transforms and element conversions of the engine in use
+  auto fft_fwd = [&](E* a, E* b) -> E* {
+    if constexpr (PK) return p_fft_lines<-1>(a, b, 1, lofs, t0, TPL, g.px, twx, twx + m);
+    else return fft_lines<T, -1>(a, b, 1, lofs, t0, TPL, g.px, twm);
+  };
+  auto fft_inv = [&](E* a, E* b) -> E* {
+    if constexpr (PK) return p_fft_lines<+1>(a, b, 1, lofs, t0, TPL, g.px, twx, twx + 2 * m);
+    else return fft_lines<T, +1>(a, b, 1, lofs, t0, TPL, g.px, twm);
+  };
+  auto to_e = [](cpx<T> v) -> E {
+    if constexpr (PK) return pdd_of(v);
+    else return v;
+  };
+  auto of_e = [](E v) -> cpx<T> {
+    if constexpr (PK) return cpx_of(v);
+    else return v;
+  };
 
   // c = -1: the inverse-only transform of component 0 into aux_out (mode 0 programs only)
   for (int c = P.aux_out ? -1 : 0; c < P.ncomp; ++c) {
     const bool aux = c < 0;
     const int ci = aux ? 0 : c;
     const int mode = aux ? 2 : P.mode;
-    cpx<T>* res;
+    E* res;
     __syncthreads();
     if (mode == 1) {
       const int cin = (P.conv_in >> c) & 1;
       const int rbase = (int)((line0 + line) * m);
       if (lok) {
 #pragma unroll 4
-        for (int j = t0; j < m; j += TPL) A[lofs + j] = ld_el<T, CV>(P.in[c], cin, rbase + j);
+        for (int j = t0; j < m; j += TPL) A[lofs + j] = to_e(ld_el<T, CV>(P.in[c], cin, rbase + j));
       }
-      res = fft_lines<T, -1>(A, B, 1, lofs, t0, TPL, g.px, twm);
+      res = fft_fwd(A, B);
     } else {
       const int cin = (P.conv_in >> ci) & 1;
       const int lbase = (int)((line0 + line) * h0);
@@ -789,31 +833,37 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)
             v = scal(v, cc);
             if (pre & MUL_IK) v = mul_i(v);
           }
-          B[lofs + k] = v;
+          Bc[lofs + k] = v;
         }
       }
       __syncthreads();
       // pack the half spectrum into a length-m complex spectrum (inverse real transform)
       if (lok) {
         for (int k = t0; k < m; k += TPL) {
-          const cpx<T> X = B[lofs + k];
-          const cpx<T> Xc = conjg(B[lofs + (m - k)]);
-          A[lofs + k] = (X + Xc) + mul_i(cmulc(X - Xc, pk[k]));
+          const cpx<T> X = Bc[lofs + k];
+          const cpx<T> Xc = conjg(Bc[lofs + (m - k)]);
+          A[lofs + k] = to_e((X + Xc) + mul_i(cmulc(X - Xc, pk[k])));
         }
       }
-      res = fft_lines<T, +1>(A, B, 1, lofs, t0, TPL, g.px, twm);
+      res = fft_inv(A, B);
       if (mode == 2) {
         void* o = aux ? P.aux_out : P.out[c];
         const int cout = aux ? P.aux_conv : ((P.conv_out >> c) & 1);
         const T sc = aux ? scale_t<T>(P.aux_scale, P.aux_scale_hi, P.aux_scale_lo) : scale;
         const int rbase = (int)((line0 + line) * m);
         if (lok)
-          for (int j = t0; j < m; j += TPL) st_el<T, CV>(o, cout, rbase + j, scal(res[lofs + j], sc), true);
+          for (int j = t0; j < m; j += TPL) st_el<T, CV>(o, cout, rbase + j, scal(of_e(res[lofs + j]), sc), true);
         continue;
       }
       if (P.wfield && lok) {
         bool done_pair = false;
-        if constexpr (std::is_same<T, float>::value) {
+        if constexpr (PK) {
+          // lane by lane the float-pair products z.x wv.x and z.y wv.y
+          const cpx<T>* __restrict__ wf = reinterpret_cast<const cpx<T>*>(P.wfield) + (line0 + line) * m;
+#pragma unroll 4
+          for (int j = t0; j < m; j += TPL) res[lofs + j] = p_scal(res[lofs + j], pdd_of(wf[j]));
+          done_pair = true;
+        } else if constexpr (std::is_same<T, float>::value) {
           if (P.wf_dd) {
             const float4* __restrict__ wf4 = reinterpret_cast<const float4*>(P.wfield) + (line0 + line) * m;
 #pragma unroll 4
@@ -825,18 +875,20 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)
             done_pair = true;
           }
         }
-        if (!done_pair) {
-          const cpx<T>* __restrict__ wf = reinterpret_cast<const cpx<T>*>(P.wfield) + (line0 + line) * m;
+        if constexpr (!PK) {
+          if (!done_pair) {
+            const cpx<T>* __restrict__ wf = reinterpret_cast<const cpx<T>*>(P.wfield) + (line0 + line) * m;
 #pragma unroll 4
-          for (int j = t0; j < m; j += TPL) {
-            const cpx<T> z = res[lofs + j];
-            const cpx<T> wv = wf[j];
-            res[lofs + j] = mk<T>(z.x * wv.x, z.y * wv.y);
+            for (int j = t0; j < m; j += TPL) {
+              const cpx<T> z = res[lofs + j];
+              const cpx<T> wv = wf[j];
+              res[lofs + j] = mk<T>(z.x * wv.x, z.y * wv.y);
+            }
           }
         }
       }
-      cpx<T>* other = (res == A) ? B : A;
-      res = fft_lines<T, -1>(res, other, 1, lofs, t0, TPL, g.px, twm);
+      E* other = (res == A) ? B : A;
+      res = fft_fwd(res, other);
     }
     // unpack the length-m spectrum into the half spectrum of the real line
     const int cout = (P.conv_out >> c) & 1;
@@ -844,8 +896,8 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)
     const int post = P.post[c];
     if (lok) {
       for (int k = t0; k < h0; k += TPL) {
-        const cpx<T> Z = res[lofs + (k == m ? 0 : k)];
-        const cpx<T> Zc = conjg(res[lofs + (k == 0 ? 0 : m - k)]);
+        const cpx<T> Z = of_e(res[lofs + (k == m ? 0 : k)]);
+        const cpx<T> Zc = conjg(of_e(res[lofs + (k == 0 ? 0 : m - k)]));
         cpx<T> X = (Z + Zc) - mul_i(cmul(Z - Zc, pk[k]));
         T cc = scale;
         const T kx = kfx * (T)freq_tilde(k, g.n0);
@@ -1398,9 +1450,11 @@ size_t xpass_smem_bytes(const GridDesc& g) {
   return sizeof(cpx<T>) * (size_t)(m + (m + 2) + 2 * L * (m + 1));
 }
 
-template <typename T, int S, bool CV>
-static void set_axis_attr(size_t smem) {
-  ensure_smem(reinterpret_cast<const void*>(k_axis<T, S, CV>), smem);
+template <typename T, int S, bool CV, bool PK>
+static void launch_k_axis(const AxisProg& P, const GridDesc& g, const cpx<T>* tw, int W, long long blocks,
+                          size_t smem, cudaStream_t st) {
+  ensure_smem(reinterpret_cast<const void*>(k_axis<T, S, CV, PK>), smem);
+  k_axis<T, S, CV, PK><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, tw, ilog2(W));
 }
 
 template <typename T, int S, int N1, int N2>
@@ -1573,19 +1627,27 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
     }
   }
   const bool cv = (P.conv_in | P.conv_out) != 0;
-  if (dir < 0 && cv) {
-    set_axis_attr<T, -1, true>(smem);
-    k_axis<T, -1, true><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, ilog2(W));
-  } else if (dir < 0) {
-    set_axis_attr<T, -1, false>(smem);
-    k_axis<T, -1, false><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, ilog2(W));
-  } else if (cv) {
-    set_axis_attr<T, +1, true>(smem);
-    k_axis<T, +1, true><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, ilog2(W));
-  } else {
-    set_axis_attr<T, +1, false>(smem);
-    k_axis<T, +1, false><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, twp, ilog2(W));
+  if constexpr (std::is_same<T, dd>::value) {
+    if (choice != kChoiceUnpacked && p_plan_ok(P.axis == 2 ? g.pz : g.py)) {
+      const size_t psmem = smem + sizeof(pdd) * (size_t)n;   // the second twiddle table
+      if (dir < 0 && cv) launch_k_axis<T, -1, true, true>(P, g, twp, W, blocks, psmem, st);
+      else if (dir < 0) launch_k_axis<T, -1, false, true>(P, g, twp, W, blocks, psmem, st);
+      else if (cv) launch_k_axis<T, +1, true, true>(P, g, twp, W, blocks, psmem, st);
+      else launch_k_axis<T, +1, false, true>(P, g, twp, W, blocks, psmem, st);
+      return;
+    }
   }
+  if (dir < 0 && cv) launch_k_axis<T, -1, true, false>(P, g, twp, W, blocks, smem, st);
+  else if (dir < 0) launch_k_axis<T, -1, false, false>(P, g, twp, W, blocks, smem, st);
+  else if (cv) launch_k_axis<T, +1, true, false>(P, g, twp, W, blocks, smem, st);
+  else launch_k_axis<T, +1, false, false>(P, g, twp, W, blocks, smem, st);
+}
+
+template <typename T, bool CV, bool PK>
+static void launch_k_xpass(const XProg& P, const GridDesc& g, const cpx<T>* tw, int L, long long blocks, size_t smem,
+                           cudaStream_t st) {
+  ensure_smem(reinterpret_cast<const void*>(k_xpass<T, CV, PK>), smem);
+  k_xpass<T, CV, PK><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, tw, ilog2(L));
 }
 
 template <typename T>
@@ -1618,8 +1680,6 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
   const long long blocks = (nlines + L - 1) / L;
   const size_t smem = sizeof(cpx<T>) * (size_t)(m + (m + 2) + 2 * L * (m + 1));
   const bool cv = (P.conv_in | P.conv_out | (P.aux_out ? P.aux_conv : 0)) != 0;
-  ensure_smem(cv ? reinterpret_cast<const void*>(k_xpass<T, true>) : reinterpret_cast<const void*>(k_xpass<T, false>),
-              smem);
   const double fc = (double)g.ncplx * sizeof(cpx<T>), fr = (double)g.nreal * sizeof(T);
   double bytes = 0, flops = 0;
   const double real_fft = (double)g.nreal * 2.5 * std::log2((double)g.n0);   // one real transform of every line
@@ -1664,8 +1724,17 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
       return;
     }
   }
-  if (cv) k_xpass<T, true><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, reinterpret_cast<const cpx<T>*>(tw), ilog2(L));
-  else k_xpass<T, false><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, reinterpret_cast<const cpx<T>*>(tw), ilog2(L));
+  const cpx<T>* twp = reinterpret_cast<const cpx<T>*>(tw);
+  if constexpr (std::is_same<T, dd>::value) {
+    if (choice != kChoiceUnpacked && p_plan_ok(g.px)) {
+      const size_t psmem = smem + sizeof(pdd) * (size_t)(3 * m);   // the packed twiddle tables
+      if (cv) launch_k_xpass<T, true, true>(P, g, twp, L, blocks, psmem, st);
+      else launch_k_xpass<T, false, true>(P, g, twp, L, blocks, psmem, st);
+      return;
+    }
+  }
+  if (cv) launch_k_xpass<T, true, false>(P, g, twp, L, blocks, smem, st);
+  else launch_k_xpass<T, false, false>(P, g, twp, L, blocks, smem, st);
 }
 
 template void launch_axis<dd>(const AxisProg&, int, const GridDesc&, const void*, cudaStream_t);

@@ -94,8 +94,11 @@ void launch_xpass(const XProg& P, const GridDesc& g, const void* tw, cudaStream_
 // kind 1: x pass (key: type, n0/2, axis 0, mode).  type: 0 double, 1 float, 2 float-pair.
 // choice: 0 register four-step kernel, > 0 lines per block, < 0 (get) absent / (set) erase.
 // kind 0 choice kChoiceStaged: the register kernel with TMA-staged input (float y/z passes of
-// length 128 / 256)
+// length 128 / 256).  Type 2 choice kChoiceUnpacked (either kind): the Stockham engine on
+// unpacked float pairs with the default lines per block, instead of the packed engine that the
+// float-pair passes use for lengths whose radices are 2, 4 and 8 (same results, bit for bit).
 constexpr int kChoiceStaged = 128;
+constexpr int kChoiceUnpacked = 256;
 int tune_get(int kind, int type, int n, int axis, int dir);
 void tune_set(int kind, int type, int n, int axis, int dir, int choice);
 int tune_table(int* out, int max);   // 6 ints per entry; returns the entry count

@@ -194,7 +194,8 @@ int vd_autotune_table(int* out, int max) { return vd::tune_table(out, max); }
 
 vd_status vd_autotune_set(int kind, int type, int n, int axis, int dir, int choice) {
   if (kind < 0 || kind > 1 || type < 0 || type > 2 || n <= 0) return vd::fail(VD_ERR_INVALID_ARG, "bad tuning key");
-  if (choice != vd::kChoiceStaged && (choice > 64 || (choice > 0 && (choice & (choice - 1)))))
+  if (choice != vd::kChoiceStaged && !(choice == vd::kChoiceUnpacked && type == 2) &&
+      (choice > 64 || (choice > 0 && (choice & (choice - 1)))))
     return vd::fail(VD_ERR_INVALID_ARG, "bad choice");
   vd::tune_set(kind, type, n, axis, dir, choice);
   return VD_OK;
