@@ -738,13 +738,13 @@ __global__ void __launch_bounds__(kRLines * N2, (N2 == 16 ? 3 : 6))
 // contiguous x pass (real <-> half spectrum through a complex FFT of length n0/2)
 // ---------------------------------------------------------------------------------------
 
-// float pairs: three blocks per SM (80 registers, no spills); the tuned 16 lines per block
-// take 70-73 KB of shared memory each, so a fourth block would not fit anyway.
-// PK (float pairs, radices 2 / 4 / 8 only): the transforms run on packed complex float pairs
-// (vd_pdd.cuh), bit-identical to the unpacked engine, with the twiddle tables of both
-// directions; the (un)packing of the real transform and the multipliers stay unpacked.
-template <typename T, bool CV, bool PK = false>
-__global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)) k_xpass(const XProg P, const GridDesc g,
+// float pairs: MINB blocks per SM, 3 (80 registers, no spills) where shared memory admits no
+// more (16 lines per block take 70-77 KB), 4 (64 registers) for smaller blocks.
+// PK (float pairs, radices 2 / 4 / 8 only): the transforms and the (un)packing of the real
+// transform run on packed complex float pairs (vd_pdd.cuh), bit-identical to the unpacked
+// code, with packed twiddle tables for both directions and the packing twiddles W_{n0}^k.
+template <typename T, bool CV, bool PK = false, int MINB = (std::is_same<T, dd>::value ? 3 : 1)>
+__global__ void __launch_bounds__(kThreads, MINB) k_xpass(const XProg P, const GridDesc g,
                                                     const cpx<T>* __restrict__ twg, int llpc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (P.done && *P.done) return;
@@ -753,22 +753,30 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)
   const int ls = m + 1;
   const int LPC = 1 << llpc;
   using E = typename std::conditional<PK, pdd, cpx<T>>::type;
+  // unpacked: W_m^j (m), W_{n0}^k (m + 1, padded to m + 2: 16-byte alignment), two line buffers
+  // PK: wr, wi forward, wi inverse of W_m^j (m each), wr, wi forward of W_{n0}^k (m + 1 each),
+  // two line buffers
   cpx<T>* twm = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* pk = twm + m;
-  E* twx = reinterpret_cast<E*>(pk + (m + 2));   // PK: the packed tables (wr, wi forward, wi inverse)
-  E* A = twx + (PK ? 3 * m : 0);   // keep 16-byte alignment (m even)
+  E* twx = reinterpret_cast<E*>(smem_raw);
+  E* pkx = twx + 3 * m;
+  E* A = PK ? pkx + 2 * (m + 1) : reinterpret_cast<E*>(pk + (m + 2));
   E* B = A + LPC * ls;
-  cpx<T>* Bc = reinterpret_cast<cpx<T>*>(B);   // the loaded half spectrum (elements of the same size)
   const int tid = threadIdx.x;
   for (int j = tid; j < m; j += kThreads) {
-    twm[j] = twg[g.px.tw_off + j];
     if constexpr (PK) {
-      p_tw_entry<-1>(twm[j], &twx[j], &twx[m + j]);
+      const cpx<T> w = twg[g.px.tw_off + j];
+      p_tw_entry<-1>(w, &twx[j], &twx[m + j]);
       pdd wr;
-      p_tw_entry<+1>(twm[j], &wr, &twx[2 * m + j]);
+      p_tw_entry<+1>(w, &wr, &twx[2 * m + j]);
+    } else {
+      twm[j] = twg[g.px.tw_off + j];
     }
   }
-  for (int j = tid; j <= m; j += kThreads) pk[j] = twg[g.pk_off + j];
+  for (int j = tid; j <= m; j += kThreads) {
+    if constexpr (PK) p_tw_entry<-1>(twg[g.pk_off + j], &pkx[j], &pkx[m + 1 + j]);
+    else pk[j] = twg[g.pk_off + j];
+  }
 
   const long long nlines = (long long)g.n1 * g.n2;
   const long long line0 = (long long)blockIdx.x * LPC;
@@ -794,10 +802,6 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)
   };
   auto to_e = [](cpx<T> v) -> E {
     if constexpr (PK) return pdd_of(v);
-    else return v;
-  };
-  auto of_e = [](E v) -> cpx<T> {
-    if constexpr (PK) return cpx_of(v);
     else return v;
   };
 
@@ -833,16 +837,24 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)
             v = scal(v, cc);
             if (pre & MUL_IK) v = mul_i(v);
           }
-          Bc[lofs + k] = v;
+          B[lofs + k] = to_e(v);
         }
       }
       __syncthreads();
       // pack the half spectrum into a length-m complex spectrum (inverse real transform)
       if (lok) {
         for (int k = t0; k < m; k += TPL) {
-          const cpx<T> X = Bc[lofs + k];
-          const cpx<T> Xc = conjg(Bc[lofs + (m - k)]);
-          A[lofs + k] = to_e((X + Xc) + mul_i(cmulc(X - Xc, pk[k])));
+          if constexpr (PK) {
+            // (X + conj Xr) + i cmulc(X - conj Xr, w), with cmulc(t, w) = conj cmul(conj t, w)
+            // bit for bit, conj t = conj X - Xr and i conj C = (C.im, C.re)
+            const pdd X = B[lofs + k], Xr = B[lofs + (m - k)];
+            const pdd C = p_cmul(p_conj(X) - Xr, pkx[k], pkx[m + 1 + k]);
+            A[lofs + k] = (X + p_conj(Xr)) + p_swap(C);
+          } else {
+            const cpx<T> X = B[lofs + k];
+            const cpx<T> Xc = conjg(B[lofs + (m - k)]);
+            A[lofs + k] = (X + Xc) + mul_i(cmulc(X - Xc, pk[k]));
+          }
         }
       }
       res = fft_inv(A, B);
@@ -852,7 +864,10 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)
         const T sc = aux ? scale_t<T>(P.aux_scale, P.aux_scale_hi, P.aux_scale_lo) : scale;
         const int rbase = (int)((line0 + line) * m);
         if (lok)
-          for (int j = t0; j < m; j += TPL) st_el<T, CV>(o, cout, rbase + j, scal(of_e(res[lofs + j]), sc), true);
+          for (int j = t0; j < m; j += TPL) {
+            if constexpr (PK) st_el<T, CV>(o, cout, rbase + j, cpx_of(p_scal(res[lofs + j], pdd_bc(sc))), true);
+            else st_el<T, CV>(o, cout, rbase + j, scal(res[lofs + j], sc), true);
+          }
         continue;
       }
       if (P.wfield && lok) {
@@ -896,17 +911,27 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, dd>::value ? 3 : 1)
     const int post = P.post[c];
     if (lok) {
       for (int k = t0; k < h0; k += TPL) {
-        const cpx<T> Z = of_e(res[lofs + (k == m ? 0 : k)]);
-        const cpx<T> Zc = conjg(of_e(res[lofs + (k == 0 ? 0 : m - k)]));
-        cpx<T> X = (Z + Zc) - mul_i(cmul(Z - Zc, pk[k]));
         T cc = scale;
         const T kx = kfx * (T)freq_tilde(k, g.n0);
         if (post & MUL_IK) cc *= kx;
         if (post & MUL_SYM) cc *= symarr[k];
         if (post & (MUL_NEGK2 | MUL_IK2)) cc *= -kx * kx;
-        X = scal(X, cc);
-        if (post & MUL_IK) X = mul_i(X);
-        st_el<T, CV>(P.out[c], cout, obase + k, X, true);
+        if constexpr (PK) {
+          // (Z + Zc) - i cmul(Z - Zc, w), Zc = conj of the mirrored entry
+          const pdd Z = res[lofs + (k == m ? 0 : k)];
+          const pdd Zc = p_conj(res[lofs + (k == 0 ? 0 : m - k)]);
+          const pdd C = p_cmul(Z - Zc, pkx[k], pkx[m + 1 + k]);
+          pdd X = p_scal((Z + Zc) - p_mul_si<+1>(C), pdd_bc(cc));
+          if (post & MUL_IK) X = p_mul_si<+1>(X);
+          st_el<T, CV>(P.out[c], cout, obase + k, cpx_of(X), true);
+        } else {
+          const cpx<T> Z = res[lofs + (k == m ? 0 : k)];
+          const cpx<T> Zc = conjg(res[lofs + (k == 0 ? 0 : m - k)]);
+          cpx<T> X = (Z + Zc) - mul_i(cmul(Z - Zc, pk[k]));
+          X = scal(X, cc);
+          if (post & MUL_IK) X = mul_i(X);
+          st_el<T, CV>(P.out[c], cout, obase + k, X, true);
+        }
       }
     }
   }
@@ -1643,11 +1668,11 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
   else launch_k_axis<T, +1, false, false>(P, g, twp, W, blocks, smem, st);
 }
 
-template <typename T, bool CV, bool PK>
+template <typename T, bool CV, bool PK, int MINB = (std::is_same<T, dd>::value ? 3 : 1)>
 static void launch_k_xpass(const XProg& P, const GridDesc& g, const cpx<T>* tw, int L, long long blocks, size_t smem,
                            cudaStream_t st) {
-  ensure_smem(reinterpret_cast<const void*>(k_xpass<T, CV, PK>), smem);
-  k_xpass<T, CV, PK><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, tw, ilog2(L));
+  ensure_smem(reinterpret_cast<const void*>(k_xpass<T, CV, PK, MINB>), smem);
+  k_xpass<T, CV, PK, MINB><<<(unsigned)blocks, kThreads, smem, st>>>(P, g, tw, ilog2(L));
 }
 
 template <typename T>
@@ -1727,9 +1752,14 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
   const cpx<T>* twp = reinterpret_cast<const cpx<T>*>(tw);
   if constexpr (std::is_same<T, dd>::value) {
     if (choice != kChoiceUnpacked && p_plan_ok(g.px)) {
-      const size_t psmem = smem + sizeof(pdd) * (size_t)(3 * m);   // the packed twiddle tables
-      if (cv) launch_k_xpass<T, true, true>(P, g, twp, L, blocks, psmem, st);
-      else launch_k_xpass<T, false, true>(P, g, twp, L, blocks, psmem, st);
+      // the packed twiddle tables: 3 m + 2 (m + 1) entries against 2 m + 2
+      const size_t psmem = smem + sizeof(pdd) * (size_t)(3 * m);
+      // four blocks per SM (64 registers) where their shared memory fits, else three
+      const bool four = 4 * (psmem + 1024) <= 228 * 1024;
+      if (cv && four) launch_k_xpass<T, true, true, 4>(P, g, twp, L, blocks, psmem, st);
+      else if (cv) launch_k_xpass<T, true, true, 3>(P, g, twp, L, blocks, psmem, st);
+      else if (four) launch_k_xpass<T, false, true, 4>(P, g, twp, L, blocks, psmem, st);
+      else launch_k_xpass<T, false, true, 3>(P, g, twp, L, blocks, psmem, st);
       return;
     }
   }

@@ -112,6 +112,12 @@ __device__ __forceinline__ pdd p_scal(pdd v, pdd s) {
   e = f2_fma(v.lo, s.hi, e);
   return p_fast_two_sum(p, e);
 }
+// complex conjugate and the exchange of the two parts
+__device__ __forceinline__ pdd p_conj(pdd v) {
+  const f2r sg = f2_pack(1.0f, -1.0f);
+  return pdd{f2_mul(v.hi, sg), f2_mul(v.lo, sg)};
+}
+__device__ __forceinline__ pdd p_swap(pdd v) { return pdd{f2_swap(v.hi), f2_swap(v.lo)}; }
 // multiply by S i: forward (S < 0) (re, im) -> (im, -re), inverse (-im, re)
 template <int S>
 __device__ __forceinline__ pdd p_mul_si(pdd v) {
