@@ -793,11 +793,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_xpass(const XProg P, const G
   const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr) + (line0 + line) * h0;
   // the transforms and element conversions of the engine in use
   auto fft_fwd = [&](E* a, E* b) -> E* {
-    if constexpr (PK) return p_fft_lines<-1>(a, b, 1, lofs, t0, TPL, g.px, twx, twx + m);
+    if constexpr (PK) return p_fft_lines<-1, 1>(a, b, 1, lofs, t0, TPL, g.px, twx, twx + m);
     else return fft_lines<T, -1>(a, b, 1, lofs, t0, TPL, g.px, twm);
   };
   auto fft_inv = [&](E* a, E* b) -> E* {
-    if constexpr (PK) return p_fft_lines<+1>(a, b, 1, lofs, t0, TPL, g.px, twx, twx + 2 * m);
+    if constexpr (PK) return p_fft_lines<+1, 1>(a, b, 1, lofs, t0, TPL, g.px, twx, twx + 2 * m);
     else return fft_lines<T, +1>(a, b, 1, lofs, t0, TPL, g.px, twm);
   };
   auto to_e = [](cpx<T> v) -> E {
@@ -1653,7 +1653,7 @@ void launch_axis(const AxisProg& P0, int dir, const GridDesc& g, const void* tw,
   }
   const bool cv = (P.conv_in | P.conv_out) != 0;
   if constexpr (std::is_same<T, dd>::value) {
-    if (choice != kChoiceUnpacked && p_plan_ok(P.axis == 2 ? g.pz : g.py)) {
+    if (choice != kChoiceUnpacked && p_plan_ok(P.axis == 2 ? g.pz : g.py, kThreads / W)) {
       const size_t psmem = smem + sizeof(pdd) * (size_t)n;   // the second twiddle table
       if (dir < 0 && cv) launch_k_axis<T, -1, true, true>(P, g, twp, W, blocks, psmem, st);
       else if (dir < 0) launch_k_axis<T, -1, false, true>(P, g, twp, W, blocks, psmem, st);
@@ -1751,7 +1751,7 @@ void launch_xpass(const XProg& P0, const GridDesc& g, const void* tw, cudaStream
   }
   const cpx<T>* twp = reinterpret_cast<const cpx<T>*>(tw);
   if constexpr (std::is_same<T, dd>::value) {
-    if (choice != kChoiceUnpacked && p_plan_ok(g.px)) {
+    if (choice != kChoiceUnpacked && p_plan_ok(g.px, kThreads / L)) {
       // the packed twiddle tables: 3 m + 2 (m + 1) entries against 2 m + 2
       const size_t psmem = smem + sizeof(pdd) * (size_t)(3 * m);
       // four blocks per SM (64 registers) where their shared memory fits, else three

@@ -208,60 +208,85 @@ __device__ __forceinline__ void p_dftR(pdd* u) {
   else p_dft8<S>(u);
 }
 
-// One Stockham stage of the packed engine (stockham_stage of vd_fft.cuh, radix 2 / 4 / 8).
+// The packed engine runs the stage sequence of a power-of-two length with the stage
+// parameters as compile-time constants (strides, twiddle steps and butterfly counts become
+// immediates): radix-8 stages, then one radix-4 or radix-2 stage for the remaining factor --
+// the order of the plans, which p_plan_ok checks.
+__host__ __device__ constexpr int p_log2(int n) { return n <= 1 ? 0 : 1 + p_log2(n / 2); }
+__host__ __device__ constexpr int p_nst(int n) { return p_log2(n) / 3 + (p_log2(n) % 3 ? 1 : 0); }
+__host__ __device__ constexpr int p_rad(int n, int s) {
+  return s < p_log2(n) / 3 ? 8 : (p_log2(n) % 3 == 2 ? 4 : 2);
+}
+
+// plans the packed engine takes: lengths 64, 128, 256, 512 in the stage order above, with at
+// most 8 elements of a line per thread (istep threads share a line)
+__host__ __device__ inline bool p_plan_ok(const FftPlan& pl, int istep) {
+  if (pl.n != 64 && pl.n != 128 && pl.n != 256 && pl.n != 512) return false;
+  if (pl.n > 8 * istep || pl.nst != p_nst(pl.n)) return false;
+  for (int s = 0; s < pl.nst; ++s)
+    if (pl.rad[s] != p_rad(pl.n, s)) return false;
+  return true;
+}
+
+// One Stockham stage of the packed engine (stockham_stage of vd_fft.cuh, radix 2 / 4 / 8) for
+// a line of N elements with span P; a thread has at most 8 / R butterflies (N <= 8 istep).
+// Element stride ES > 0 is a compile-time stride, 0 takes es.
 // twr, twi: the twiddle table in the form p_cmul takes for this direction (p_tw_entry).
-template <int S, int R>
-__device__ __forceinline__ void p_stage(const pdd* __restrict__ src, pdd* __restrict__ dst, int es, int lofs, int i0,
-                                        int istep, int n, int p, const pdd* __restrict__ twr,
+template <int S, int R, int N, int P, int ES>
+__device__ __forceinline__ void p_stage(const pdd* __restrict__ src, pdd* __restrict__ dst, int es_rt, int lofs,
+                                        int i0, int istep, const pdd* __restrict__ twr,
                                         const pdd* __restrict__ twi) {
-  const int nb = n / R;
-  const int tws = n / (p * R);
-  const int pmask = p - 1;   // p is a power of two here
-#pragma unroll 1
-  for (int i = i0; i < nb; i += istep) {
-    const int k = i & pmask;
-    const pdd* s = src + lofs;
-    pdd u[R];
+  constexpr int NB = N / R, TWS = N / (P * R), MB = 8 / R;
+  const int es = ES > 0 ? ES : es_rt;
 #pragma unroll
-    for (int r = 0; r < R; ++r) u[r] = s[(i + r * nb) * es];
-    if (p > 1) {
+  for (int b = 0; b < MB; ++b) {
+    const int i = i0 + b * istep;
+    if (i < NB) {
+      const int k = i & (P - 1);
+      const pdd* s = src + lofs + i * es;
+      pdd u[R];
 #pragma unroll
-      for (int r = 1; r < R; ++r) u[r] = p_cmul(u[r], twr[r * k * tws], twi[r * k * tws]);
+      for (int r = 0; r < R; ++r) u[r] = s[r * NB * es];
+      if constexpr (P > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = p_cmul(u[r], twr[r * k * TWS], twi[r * k * TWS]);
+      }
+      p_dftR<S, R>(u);
+      pdd* d = dst + lofs + ((i - k) * R + k) * es;
+#pragma unroll
+      for (int r = 0; r < R; ++r) d[r * P * es] = u[r];
     }
-    p_dftR<S, R>(u);
-    pdd* d = dst + lofs + ((i - k) * R + k) * es;
-#pragma unroll
-    for (int r = 0; r < R; ++r) d[r * p * es] = u[r];
   }
 }
 
-// plans whose radices are all 2, 4 or 8 (the packed engine's codelets)
-__host__ __device__ inline bool p_plan_ok(const FftPlan& pl) {
-  for (int s = 0; s < pl.nst; ++s)
-    if (pl.rad[s] != 2 && pl.rad[s] != 4 && pl.rad[s] != 8) return false;
-  return pl.nst > 0;
+template <int S, int N, int ST, int P, int ES>
+__device__ __forceinline__ pdd* p_stages(pdd* a, pdd* b, int es, int lofs, int i0, int istep, const pdd* twr,
+                                         const pdd* twi) {
+  if constexpr (ST < p_nst(N)) {
+    constexpr int R = p_rad(N, ST);
+    __syncthreads();
+    p_stage<S, R, N, P, ES>(a, b, es, lofs, i0, istep, twr, twi);
+    return p_stages<S, N, ST + 1, P * R, ES>(b, a, es, lofs, i0, istep, twr, twi);
+  } else {
+    return a;
+  }
 }
 
-// full transform of every line of the block (fft_lines), packed
-template <int S>
-__device__ pdd* p_fft_lines(pdd* a, pdd* b, int es, int lofs, int i0, int istep, const FftPlan& pl, const pdd* twr,
-                            const pdd* twi) {
-  pdd* src = a;
-  pdd* dst = b;
-  int p = 1;
-  for (int s = 0; s < pl.nst; ++s) {
-    const int R = pl.rad[s];
-    __syncthreads();
-    if (R == 2) p_stage<S, 2>(src, dst, es, lofs, i0, istep, pl.n, p, twr, twi);
-    else if (R == 4) p_stage<S, 4>(src, dst, es, lofs, i0, istep, pl.n, p, twr, twi);
-    else p_stage<S, 8>(src, dst, es, lofs, i0, istep, pl.n, p, twr, twi);
-    p *= R;
-    pdd* t = src;
-    src = dst;
-    dst = t;
+// full transform of every line of the block (fft_lines), packed, for a plan that p_plan_ok
+// accepts; input in a, returns the buffer holding the result.  Must be called by all threads
+// of the block (barriers before every stage and at the end).
+template <int S, int ES = 0>
+__device__ __forceinline__ pdd* p_fft_lines(pdd* a, pdd* b, int es, int lofs, int i0, int istep, const FftPlan& pl,
+                                            const pdd* twr, const pdd* twi) {
+  pdd* res;
+  switch (pl.n) {
+    case 64: res = p_stages<S, 64, 0, 1, ES>(a, b, es, lofs, i0, istep, twr, twi); break;
+    case 128: res = p_stages<S, 128, 0, 1, ES>(a, b, es, lofs, i0, istep, twr, twi); break;
+    case 256: res = p_stages<S, 256, 0, 1, ES>(a, b, es, lofs, i0, istep, twr, twi); break;
+    default: res = p_stages<S, 512, 0, 1, ES>(a, b, es, lofs, i0, istep, twr, twi); break;
   }
   __syncthreads();
-  return src;
+  return res;
 }
 
 }  // namespace vd
