@@ -21,7 +21,10 @@ from paper_2403_06654_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 UNPACKED = 256
-GRIDS = [((256,), (2 * math.pi,)), ((128, 64), (2 * math.pi, 2.0)), ((64, 32, 16), (2 * math.pi,) * 3),
+# packed lengths: x pass n0/2 = 128, 64, 512; y 64, 512; z 256 (the 64 x 32 x 16 and 48 x 40 x 32
+# grids keep the unpacked engine on their short or radix-3/5 axes)
+GRIDS = [((256,), (2 * math.pi,)), ((1024,), (2 * math.pi,)), ((128, 64), (2 * math.pi, 2.0)),
+         ((64, 512), (2 * math.pi, 4.0)), ((64, 32, 16), (2 * math.pi,) * 3), ((32, 16, 256), (2 * math.pi,) * 3),
          ((48, 40, 32), (2 * math.pi,) * 3)]
 
 
