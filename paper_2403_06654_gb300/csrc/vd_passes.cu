@@ -78,6 +78,15 @@ __device__ __forceinline__ float mul_pair(float z, float wh, float wl) {
   return p + fmaf(z, wl, e);
 }
 
+// Hint: bring [p, p + bytes) into L2 (p and bytes multiples of 16), in pieces of at most 32 KB.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  const size_t ga = __cvta_generic_to_global(p);
+  for (unsigned o = 0; o < bytes; o += 32768u) {
+    const unsigned len = (bytes - o < 32768u) ? bytes - o : 32768u;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ga + o), "r"(len) : "memory");
+  }
+}
+
 constexpr int kThreads = 256;
 template <typename T>
 constexpr int kEPT = (sizeof(T) == 4) ? 16 : 8;   // tile elements per thread (float: 16; double, dd: 8)
@@ -791,6 +800,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_xpass(const XProg P, const G
   const T kfx = kfac_t<T>(g, 0);
   const T scale = scale_t<T>(P.scale, P.scale_hi, P.scale_lo);
   const T* __restrict__ symarr = reinterpret_cast<const T*>(P.symarr) + (line0 + line) * h0;
+  // float pairs: the block's lines of a component are one contiguous chunk (16 bytes per
+  // element, float pairs and doubles alike); the weights and each next component's input are
+  // prefetched into L2 while the current component is transformed
+  constexpr bool kPrefetch = std::is_same<T, dd>::value;
+  if (kPrefetch && tid == 0 && P.mode == 0 && P.wfield)
+    prefetch_l2(reinterpret_cast<const cpx<T>*>(P.wfield) + line0 * m, (unsigned)(nl * m) * 16u);
   // the transforms and element conversions of the engine in use
   auto fft_fwd = [&](E* a, E* b) -> E* {
     if constexpr (PK) return p_fft_lines<-1, 1>(a, b, 1, lofs, t0, TPL, g.px, twx, twx + m);
@@ -812,6 +827,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_xpass(const XProg P, const G
     const int mode = aux ? 2 : P.mode;
     E* res;
     __syncthreads();
+    if (kPrefetch && tid == 0 && c + 1 < P.ncomp) {
+      const int per = (P.mode == 1) ? m : h0;   // elements per line of the next input
+      prefetch_l2(reinterpret_cast<const cpx<T>*>(P.in[c + 1]) + line0 * per, (unsigned)(nl * per) * 16u);
+    }
     if (mode == 1) {
       const int cin = (P.conv_in >> c) & 1;
       const int rbase = (int)((line0 + line) * m);
