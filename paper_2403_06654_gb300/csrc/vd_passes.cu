@@ -87,6 +87,11 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   }
 }
 
+// Hint: bring the 128-byte line holding p into L2.
+__device__ __forceinline__ void prefetch_line_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
+
 constexpr int kThreads = 256;
 template <typename T>
 constexpr int kEPT = (sizeof(T) == 4) ? 16 : 8;   // tile elements per thread (float: 16; double, dd: 8)
@@ -221,6 +226,14 @@ __global__ void __launch_bounds__(kThreads, (std::is_same<T, double>::value ? 2 
       }
       if constexpr (PK) A[i * W + w] = pdd_of(v);
       else A[i * W + w] = v;
+    }
+    // PK: the rows of the next transform's input tile are prefetched into L2 (one thread per
+    // row: a row of the tile is W elements of 16 bytes) while this one is transformed
+    if constexpr (PK) {
+      if (w == 0 && t + 1 < P.nxf && !P.xf[t + 1].nofft) {
+        const cpx<T>* nsrc = reinterpret_cast<const cpx<T>*>(P.in[P.xf[t + 1].src]);   // 16-byte elements
+        for (int q = 0; q < nq; ++q) prefetch_line_l2(nsrc + g0 + q * gstep);
+      }
     }
     E* res;
     if constexpr (PK) res = p_fft_lines<S>(A, B, W, w, ib, istep, pl, tw, tw2);
